@@ -1,0 +1,189 @@
+/*
+ * repro.h -- C ABI of the reproducible grouped SUM library (librepro.so).
+ *
+ * The library computes SQL's SUM ... GROUP BY over floating-point values so
+ * that the bits of every group's result are the same for any order of the
+ * rows, any split of the input into calls, and any GPU schedule.  It
+ * implements the repro<T,L> aggregate of Mueller, Arteaga, Hoefler, Alonso,
+ * "Reproducible Floating-Point Aggregation in RDBMSs" (arXiv 1802.09883):
+ * each value is cut into L digits on a grid fixed by the group's largest
+ * |value| (Sec. III-C, Algorithm 2), digits are summed exactly, and the
+ * result is the per-level sum rounded to T and folded from the lowest level
+ * (eq. (1)).  Reproducibility comes from exact integer bins, not from a
+ * fixed order, so atomics and any launch configuration give the same bits.
+ *
+ * Conventions for every entry point:
+ *  - Arrays are DEVICE pointers owned by the caller; the library never frees
+ *    them.  `stream` is a cudaStream_t (NULL = the legacy default stream).
+ *  - Calls are stream-ordered and asynchronous: they enqueue kernels on
+ *    `stream` and return.  Argument errors are returned synchronously, before
+ *    anything is enqueued.  Errors found in the data (a key outside
+ *    [0, num_groups)) are recorded in the state's header and reported by
+ *    repro_state_check().
+ *  - Scratch memory is taken stream-ordered from the device's default memory
+ *    pool (cudaMallocAsync) and returned on the same stream; REPRO_ENOMEM if
+ *    it cannot be had.
+ *  - L (levels) is 1..4; num_groups is 1 .. 2^31 - 1; keys are dense int32
+ *    group ids in [0, num_groups) (the paper's IdentityHashing, Sec. VI-A).
+ */
+#ifndef REPRO_H
+#define REPRO_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    REPRO_OK = 0,
+    REPRO_EINVAL = 1,   /* bad argument (NULL pointer, L, num_groups, n, dtype) */
+    REPRO_EKEY = 2,     /* a key outside [0, num_groups) was seen (row skipped) */
+    REPRO_ERANGE = 3,   /* reserved: size beyond a documented maximum */
+    REPRO_ENOMEM = 4,   /* scratch memory could not be allocated */
+    REPRO_ECUDA = 5,    /* a CUDA call failed (launch, copy, allocation) */
+    REPRO_ETIMEOUT = 6, /* a bounded device-side wait gave up */
+    REPRO_ELAYOUT = 7   /* the state header does not match dtype / L / num_groups */
+} repro_status;
+
+typedef enum {
+    REPRO_F64 = 0, /* double: W = 40 bits per level, grid unit 2^(-1074 + 40 k) */
+    REPRO_F32 = 1  /* float:  W = 18 bits per level, grid unit 2^(-149 + 18 k)  */
+} repro_dtype;
+
+/* Per-group flags (state layout below). */
+#define REPRO_FLAG_NAN 1u     /* a NaN was summed: result is NaN */
+#define REPRO_FLAG_POS_INF 2u /* +Inf summed (with -Inf too: NaN) */
+#define REPRO_FLAG_NEG_INF 4u /* -Inf summed */
+#define REPRO_FLAG_RANGE 8u   /* a finite value >= 2^1005 (double) / 2^120 (float)
+                                 was summed: its window would overflow the
+                                 running sum of Algorithm 2; result is NaN */
+
+/* Header error bits (repro_state_header.errors). */
+#define REPRO_ERR_KEY 1u
+#define REPRO_ERR_TIMEOUT 2u
+#define REPRO_ERR_LAYOUT 4u
+
+#define REPRO_STATE_MAGIC 0x4f525052u /* "RPRO" */
+
+/*
+ * State layout (device memory, canonical: equal sums give equal bytes).
+ *
+ *   repro_state_header                         64 bytes
+ *   group g at 64 + g * (8 + 16 L):
+ *     int32_t  K;        grid index of level 0 (level j has unit
+ *                        u(K - j) = 2^(g_min + (K - j) W)); the smallest K
+ *                        with max |value| < 2^(W-1) u(K) (Algorithm 2's
+ *                        raise condition)
+ *     uint32_t flags;    REPRO_FLAG_*
+ *     { int64_t lo; int64_t hi; } bin[L];
+ *                        the exact integer T_j = hi * 2^64 + lo of level j
+ *                        (both halves signed), the sum of the digits of the
+ *                        group's values at that level; level 0 is the top.
+ * An empty group has K = 0, flags = 0 and zero bins.  T_j * u(K - j) is the
+ * level's exact value, i.e. (S - 1.5 ufp(S)) + 0.25 ufp(S) C of the paper's
+ * <S, C> pair.
+ */
+typedef struct {
+    uint32_t magic;      /* REPRO_STATE_MAGIC */
+    uint32_t dtype;      /* repro_dtype */
+    uint32_t L;
+    uint32_t errors;     /* REPRO_ERR_* bits, OR-ed by kernels */
+    int64_t num_groups;
+    uint8_t reserved[40];
+} repro_state_header;
+
+/* Bytes of a state for num_groups groups: 64 + num_groups * (8 + 16 L).
+   Returns 0 for invalid arguments. */
+size_t repro_state_bytes(repro_dtype dtype, int L, int64_t num_groups);
+
+/* Write an empty state (header + all groups empty) into `state`, which must
+   hold repro_state_bytes() bytes and be 16-byte aligned. */
+repro_status repro_state_init(void* state, repro_dtype dtype, int L, int64_t num_groups,
+                              void* stream);
+
+/*
+ * Grouped reproducible SUM: for each row i, add values[i] to group keys[i]
+ * of `state` (accumulating: the state may already hold earlier calls' rows,
+ * which is how the paper's resumable summation state is used, Sec. III-C).
+ *
+ * keys:   int32[n] device array, group ids in [0, num_groups).  Rows with a
+ *         key outside that range are skipped and set REPRO_ERR_KEY.
+ * values: double[n] (REPRO_F64) or float[n] (REPRO_F32) device array.
+ *         NaN / +-Inf / out-of-range values set the group's flags and add
+ *         nothing to its bins.
+ * n:      rows; 0 is allowed (no-op).  keys and values must be 4- and
+ *         8/4-byte aligned.
+ * state:  in-out, initialised by repro_state_init with the same dtype / L /
+ *         num_groups.
+ * Steps (paper sections): per-group window from max |value| (Algorithm 2,
+ * check extractor validity); L-digit extraction against the window
+ * (Algorithm 2, transform; constant extractor so ties round to even);
+ * exact accumulation (the carry-bit counts of Algorithm 2 become wide
+ * integer bins); per-call partial states merged into `state` with
+ * operator+=(repro) (Sec. V-B, Algorithm 4).
+ */
+repro_status repro_groupby_sum(const int32_t* keys, const void* values, int64_t n,
+                               repro_dtype dtype, int L, int64_t num_groups, void* state,
+                               void* stream);
+
+/* dst += src, group by group (operator+=(repro), Sec. V-B; eq. (2)/(3) for
+   equal windows): both are aligned to the larger window, levels that fall
+   below it are dropped, bins are added exactly and flags OR-ed.  Exact, so
+   any merge order or tree gives the same bytes.  dst and src may not
+   overlap. */
+repro_status repro_merge(void* dst, const void* src, repro_dtype dtype, int L,
+                         int64_t num_groups, void* stream);
+
+/* out[g] = the group's reproducible sum (eq. (1)): V_j = T_j * u(K - j)
+   rounded to nearest even in T (gradual underflow, overflow to +-Inf), then
+   Q = (((V_{L-1} + V_{L-2}) + ...) + V_0) in T arithmetic.  A group with
+   NaN or RANGE flags, or both infinities, gives the quiet NaN
+   0x7ff8000000000000 / 0x7fc00000; +Inf or -Inf alone gives that infinity;
+   an empty group gives +0.0.  out is double[num_groups] or float[num_groups]. */
+repro_status repro_finalize(const void* state, repro_dtype dtype, int L, int64_t num_groups,
+                            void* out, void* stream);
+
+/* Synchronise `stream` and report the state's error bits: REPRO_EKEY,
+   REPRO_ETIMEOUT or REPRO_ELAYOUT (first one set, in that order), else
+   REPRO_OK.  If errors_out is not NULL it receives the raw bits.  The bits
+   stay set until repro_state_init. */
+repro_status repro_state_check(const void* state, uint32_t* errors_out, void* stream);
+
+/* Conventional, NON-reproducible grouped SUM: out[g] = sum of values[i]
+   with keys[i] == g, added with floating-point atomics in whatever order
+   the GPU runs them (the "built-in" baseline the paper compares against,
+   Sec. VI-D).  out (double[num_groups]) is overwritten.  Rows with a key
+   outside [0, num_groups) are skipped. */
+repro_status groupby_sum_fp64(const int32_t* keys, const double* values, int64_t n,
+                              int64_t num_groups, double* out, void* stream);
+
+/* Float variant of the conventional baseline (float accumulators). */
+repro_status groupby_sum_fp32(const int32_t* keys, const float* values, int64_t n,
+                              int64_t num_groups, float* out, void* stream);
+
+/* Human-readable text for a status code (static storage). */
+const char* repro_strerror(repro_status status);
+
+/* Version of the state layout and the library (major * 100 + minor). */
+int repro_version(void);
+
+/* Profiling aid (not part of the computation).  While enabled, the library
+   records a pair of CUDA events on the caller's stream around every launch
+   of its row-pass kernels, keyed by kernel name ("window", "accum",
+   "fused", "partition", "merge", "finalize", "fp64", "fp32").
+   repro_profile_read() waits for the recorded events of that name, returns
+   their summed duration in milliseconds and their count, and forgets them.
+   Unknown names give REPRO_EINVAL. */
+void repro_profile_enable(int on);
+repro_status repro_profile_read(const char* kernel, double* total_ms, int64_t* launches);
+
+/* Number of kernel launches the library has made since it was loaded. */
+int64_t repro_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* REPRO_H */

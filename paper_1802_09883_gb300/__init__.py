@@ -1,1 +1,232 @@
-"""Reproducible grouped SUM (repro<T,L>) on GB300: Python binding placeholder."""
+"""Reproducible grouped SUM (repro<T,L>) on GB300.
+
+Python binding of librepro.so (C ABI in include/repro.h).  This module only
+marshals arguments -- device pointers from torch tensors and the current
+CUDA stream -- and every step of the computation runs in the library's CUDA
+kernels.  There is no CPU fallback: without a CUDA device or without the
+compiled library the calls raise.
+
+    import torch, paper_1802_09883_gb300 as repro
+    out = repro.groupby_sum(keys, values, num_groups=1024, L=3)   # float64[G]
+
+    st = repro.State(num_groups=1024, L=3)                        # resumable
+    st.add(keys_part1, values_part1); st.add(keys_part2, values_part2)
+    st.merge(other_state); out = st.finalize()
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+from typing import Optional
+
+import numpy as np
+import torch
+
+from . import build as _build
+
+REPRO_F64 = 0
+REPRO_F32 = 1
+FLAG_NAN, FLAG_POS_INF, FLAG_NEG_INF, FLAG_RANGE = 1, 2, 4, 8
+ERR_KEY, ERR_TIMEOUT, ERR_LAYOUT = 1, 2, 4
+HEADER_BYTES = 64
+
+STATUS = {0: "REPRO_OK", 1: "REPRO_EINVAL", 2: "REPRO_EKEY", 3: "REPRO_ERANGE", 4: "REPRO_ENOMEM",
+          5: "REPRO_ECUDA", 6: "REPRO_ETIMEOUT", 7: "REPRO_ELAYOUT"}
+
+_lib = None
+
+
+class ReproError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        msg = lib().repro_strerror(status).decode() if _lib is not None else STATUS.get(status, "?")
+        super().__init__(f"{where}: {STATUS.get(status, status)} ({msg})")
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def declared_functions():
+    """Names of the functions declared in include/repro.h."""
+    with open(os.path.join(_build.INCLUDE, "repro.h")) as fh:
+        text = fh.read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"^[A-Za-z_][\w\s\*]*?\b(\w+)\s*\(", text, flags=re.M)) - {"if", "defined"})
+
+
+def lib(build_if_stale: bool = True):
+    """Load librepro.so (building it first when missing or stale)."""
+    global _lib
+    if _lib is None:
+        if build_if_stale:
+            _build.build()
+        if not os.path.exists(_build.LIB):
+            raise RuntimeError("librepro.so is not built; run paper_1802_09883_gb300.build.build()")
+        L = ctypes.CDLL(_build.LIB)
+        vp, i64, i32, u32p = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.POINTER(ctypes.c_uint32)
+        L.repro_state_bytes.argtypes = [i32, i32, i64]
+        L.repro_state_bytes.restype = ctypes.c_size_t
+        L.repro_state_init.argtypes = [vp, i32, i32, i64, vp]
+        L.repro_groupby_sum.argtypes = [vp, vp, i64, i32, i32, i64, vp, vp]
+        L.repro_merge.argtypes = [vp, vp, i32, i32, i64, vp]
+        L.repro_finalize.argtypes = [vp, i32, i32, i64, vp, vp]
+        L.repro_state_check.argtypes = [vp, u32p, vp]
+        L.groupby_sum_fp64.argtypes = [vp, vp, i64, i64, vp, vp]
+        L.groupby_sum_fp32.argtypes = [vp, vp, i64, i64, vp, vp]
+        L.repro_strerror.argtypes = [i32]
+        L.repro_strerror.restype = ctypes.c_char_p
+        L.repro_version.restype = i32
+        for name in ("repro_state_init", "repro_groupby_sum", "repro_merge", "repro_finalize",
+                     "repro_state_check", "groupby_sum_fp64", "groupby_sum_fp32"):
+            getattr(L, name).restype = i32
+        _lib = L
+    return _lib
+
+
+def _require_cuda(t: torch.Tensor, name: str):
+    if not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor (this library has no CPU path)")
+
+
+def _stream(device) -> int:
+    return torch.cuda.current_stream(device).cuda_stream
+
+
+def _dtype_code(dtype) -> int:
+    if dtype == torch.float64:
+        return REPRO_F64
+    if dtype == torch.float32:
+        return REPRO_F32
+    raise ValueError("values must be float64 or float32")
+
+
+def _check(status: int, where: str):
+    if status != 0:
+        raise ReproError(status, where)
+
+
+def state_bytes(dtype, L: int, num_groups: int) -> int:
+    return int(lib().repro_state_bytes(_dtype_code(dtype), L, num_groups))
+
+
+class State:
+    """G reproducible accumulators repro<T,L> in device memory (the library's
+    canonical state layout: header + per group K, flags, L 128-bit bins)."""
+
+    def __init__(self, num_groups: int, L: int = 3, dtype=torch.float64, device=None,
+                 tensor: Optional[torch.Tensor] = None):
+        if not torch.cuda.is_available():
+            raise RuntimeError("paper_1802_09883_gb300 needs a CUDA device")
+        self.G = int(num_groups)
+        self.L = int(L)
+        self.dtype = dtype
+        self.code = _dtype_code(dtype)
+        nbytes = state_bytes(dtype, self.L, self.G)
+        if nbytes == 0:
+            raise ValueError("invalid L or num_groups")
+        if tensor is not None:
+            if tensor.numel() != nbytes or tensor.dtype != torch.uint8:
+                raise ValueError("state tensor has the wrong size or dtype")
+            self.tensor = tensor
+        else:
+            dev = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+            self.tensor = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+            self.reset()
+
+    @property
+    def device(self):
+        return self.tensor.device
+
+    def reset(self):
+        _check(lib().repro_state_init(self.tensor.data_ptr(), self.code, self.L, self.G,
+                                      _stream(self.device)), "repro_state_init")
+        return self
+
+    def add(self, keys: torch.Tensor, values: torch.Tensor):
+        """Accumulate rows (keys int32[n], values of the state's dtype)."""
+        _require_cuda(keys, "keys")
+        _require_cuda(values, "values")
+        if keys.dtype != torch.int32:
+            raise ValueError("keys must be int32")
+        if values.dtype != self.dtype:
+            raise ValueError(f"values must be {self.dtype}")
+        if keys.numel() != values.numel():
+            raise ValueError("keys and values differ in length")
+        keys = keys.contiguous()
+        values = values.contiguous()
+        _check(lib().repro_groupby_sum(keys.data_ptr(), values.data_ptr(), keys.numel(), self.code, self.L,
+                                       self.G, self.tensor.data_ptr(), _stream(self.device)),
+               "repro_groupby_sum")
+        return self
+
+    def merge(self, other: "State"):
+        if (other.G, other.L, other.dtype) != (self.G, self.L, self.dtype):
+            raise ValueError("states differ in num_groups, L or dtype")
+        _check(lib().repro_merge(self.tensor.data_ptr(), other.tensor.data_ptr(), self.code, self.L, self.G,
+                                 _stream(self.device)), "repro_merge")
+        return self
+
+    def finalize(self, out: Optional[torch.Tensor] = None) -> torch.Tensor:
+        if out is None:
+            out = torch.empty(self.G, dtype=self.dtype, device=self.device)
+        _check(lib().repro_finalize(self.tensor.data_ptr(), self.code, self.L, self.G, out.data_ptr(),
+                                    _stream(self.device)), "repro_finalize")
+        return out
+
+    def check(self) -> int:
+        """Synchronise and raise ReproError if a data error was recorded."""
+        err = ctypes.c_uint32(0)
+        st = lib().repro_state_check(self.tensor.data_ptr(), ctypes.byref(err), _stream(self.device))
+        _check(st, "repro_state_check")
+        return err.value
+
+    def clone(self) -> "State":
+        return State(self.G, self.L, self.dtype, tensor=self.tensor.clone())
+
+    def host_view(self):
+        """(K[G], flags[G], lo[G, L], hi[G, L]) copied to the host."""
+        return parse_state(self.tensor.cpu().numpy(), self.L, self.G)
+
+
+def parse_state(raw: np.ndarray, L: int, G: int):
+    """Split raw state bytes into (K, flags, lo[G, L], hi[G, L])."""
+    rec = np.dtype([("K", "<i4"), ("flags", "<u4"), ("bins", "<i8", (L, 2))])
+    arr = np.frombuffer(raw[HEADER_BYTES:].tobytes(), dtype=rec, count=G)
+    return (arr["K"].copy(), arr["flags"].copy(), arr["bins"][:, :, 0].copy(), arr["bins"][:, :, 1].copy())
+
+
+def groupby_sum(keys: torch.Tensor, values: torch.Tensor, num_groups: int, L: int = 3,
+                check: bool = True) -> torch.Tensor:
+    """One-shot reproducible SUM ... GROUP BY key: returns values.dtype[num_groups]."""
+    st = State(num_groups, L, values.dtype, device=values.device)
+    st.add(keys, values)
+    out = st.finalize()
+    if check:
+        st.check()
+    return out
+
+
+def groupby_sum_fp64(keys: torch.Tensor, values: torch.Tensor, num_groups: int,
+                     out: Optional[torch.Tensor] = None) -> torch.Tensor:
+    """Conventional (non-reproducible) float64 atomic GroupBy baseline."""
+    _require_cuda(keys, "keys")
+    _require_cuda(values, "values")
+    if out is None:
+        out = torch.empty(num_groups, dtype=torch.float64, device=values.device)
+    _check(lib().groupby_sum_fp64(keys.data_ptr(), values.data_ptr(), keys.numel(), num_groups, out.data_ptr(),
+                                  _stream(values.device)), "groupby_sum_fp64")
+    return out
+
+
+def groupby_sum_fp32(keys: torch.Tensor, values: torch.Tensor, num_groups: int,
+                     out: Optional[torch.Tensor] = None) -> torch.Tensor:
+    """Conventional (non-reproducible) float32 atomic GroupBy baseline."""
+    _require_cuda(keys, "keys")
+    _require_cuda(values, "values")
+    if out is None:
+        out = torch.empty(num_groups, dtype=torch.float32, device=values.device)
+    _check(lib().groupby_sum_fp32(keys.data_ptr(), values.data_ptr(), keys.numel(), num_groups, out.data_ptr(),
+                                  _stream(values.device)), "groupby_sum_fp32")
+    return out

@@ -1,0 +1,149 @@
+// repro_api.cu -- the C ABI of librepro.so (declared in include/repro.h).
+//
+// Each entry point validates its arguments on the host, takes stream-ordered
+// scratch from the device's default memory pool when it needs any, and
+// enqueues the kernels of repro_kernels.cu on the caller's stream.
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <mutex>
+
+#include "repro.h"
+#include "repro_internal.h"
+
+namespace rp {
+
+const DeviceInfo& device_info() {
+    static DeviceInfo cache[64];
+    static bool have[64] = {};
+    static std::mutex mu;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64) dev = 0;
+    std::lock_guard<std::mutex> lock(mu);
+    if (!have[dev]) {
+        DeviceInfo d{dev, 1, 48 * 1024};
+        int v = 0;
+        if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && v > 0) d.sms = v;
+        if (cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) == cudaSuccess && v > 0)
+            d.smem_optin = (size_t)v;
+        cache[dev] = d;
+        have[dev] = true;
+    }
+    return cache[dev];
+}
+
+static bool valid_dtype(int t) { return t == REPRO_F64 || t == REPRO_F32; }
+static bool valid_shape(int L, int64_t G) { return L >= 1 && L <= 4 && G >= 1 && G <= INT32_MAX; }
+
+static repro_status from_cuda(cudaError_t e) {
+    if (e == cudaSuccess) return REPRO_OK;
+    if (e == cudaErrorMemoryAllocation) return REPRO_ENOMEM;
+    return REPRO_ECUDA;
+}
+
+// Stream-ordered scratch from the default memory pool, freed on scope exit.
+struct Scratch {
+    void* p = nullptr;
+    cudaStream_t s;
+    cudaError_t err = cudaSuccess;
+    Scratch(size_t bytes, cudaStream_t st) : s(st) {
+        if (bytes) err = cudaMallocAsync(&p, bytes, s);
+    }
+    ~Scratch() {
+        if (p) cudaFreeAsync(p, s);
+    }
+};
+
+}  // namespace rp
+
+using namespace rp;
+
+extern "C" {
+
+size_t repro_state_bytes(repro_dtype dtype, int L, int64_t num_groups) {
+    if (!valid_dtype(dtype) || !valid_shape(L, num_groups)) return 0;
+    return sizeof(repro_state_header) + (size_t)num_groups * (8 + 16 * (size_t)L);
+}
+
+repro_status repro_state_init(void* state, repro_dtype dtype, int L, int64_t num_groups, void* stream) {
+    if (!state || !valid_dtype(dtype) || !valid_shape(L, num_groups)) return REPRO_EINVAL;
+    if ((uintptr_t)state % 16) return REPRO_EINVAL;
+    return from_cuda(launch_init_state(state, dtype, L, num_groups, (cudaStream_t)stream));
+}
+
+repro_status repro_groupby_sum(const int32_t* keys, const void* values, int64_t n, repro_dtype dtype, int L,
+                               int64_t num_groups, void* state, void* stream) {
+    if (!state || !valid_dtype(dtype) || !valid_shape(L, num_groups) || n < 0) return REPRO_EINVAL;
+    if (n > 0 && (!keys || !values)) return REPRO_EINVAL;
+    if ((uintptr_t)state % 16 || (uintptr_t)keys % 4 || (uintptr_t)values % (dtype == REPRO_F64 ? 8 : 4))
+        return REPRO_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    Scratch scratch(two_pass_scratch_bytes(num_groups), s);
+    if (scratch.err != cudaSuccess) return from_cuda(scratch.err);
+    return from_cuda(launch_groupby_two_pass(keys, values, n, dtype, L, num_groups, state, scratch.p, s));
+}
+
+repro_status repro_merge(void* dst, const void* src, repro_dtype dtype, int L, int64_t num_groups, void* stream) {
+    if (!dst || !src || !valid_dtype(dtype) || !valid_shape(L, num_groups)) return REPRO_EINVAL;
+    if (dst == src || (uintptr_t)dst % 16 || (uintptr_t)src % 16) return REPRO_EINVAL;
+    const size_t bytes = repro_state_bytes(dtype, L, num_groups);
+    const char* a = (const char*)dst;
+    const char* b = (const char*)src;
+    if (a < b + bytes && b < a + bytes) return REPRO_EINVAL;
+    return from_cuda(launch_merge(dst, src, dtype, L, num_groups, (cudaStream_t)stream));
+}
+
+repro_status repro_finalize(const void* state, repro_dtype dtype, int L, int64_t num_groups, void* out,
+                            void* stream) {
+    if (!state || !out || !valid_dtype(dtype) || !valid_shape(L, num_groups)) return REPRO_EINVAL;
+    if ((uintptr_t)state % 16 || (uintptr_t)out % (dtype == REPRO_F64 ? 8 : 4)) return REPRO_EINVAL;
+    return from_cuda(launch_finalize(state, dtype, L, num_groups, out, (cudaStream_t)stream));
+}
+
+repro_status repro_state_check(const void* state, uint32_t* errors_out, void* stream) {
+    if (!state) return REPRO_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    uint32_t err = 0;
+    cudaError_t e = cudaMemcpyAsync(&err, &((const repro_state_header*)state)->errors, sizeof(err),
+                                    cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return from_cuda(e);
+    if (errors_out) *errors_out = err;
+    if (err & REPRO_ERR_KEY) return REPRO_EKEY;
+    if (err & REPRO_ERR_TIMEOUT) return REPRO_ETIMEOUT;
+    if (err & REPRO_ERR_LAYOUT) return REPRO_ELAYOUT;
+    return REPRO_OK;
+}
+
+repro_status groupby_sum_fp64(const int32_t* keys, const double* values, int64_t n, int64_t num_groups,
+                              double* out, void* stream) {
+    if (!out || n < 0 || num_groups < 1 || num_groups > INT32_MAX) return REPRO_EINVAL;
+    if (n > 0 && (!keys || !values)) return REPRO_EINVAL;
+    return from_cuda(launch_groupby_fp64(keys, values, n, num_groups, out, (cudaStream_t)stream));
+}
+
+repro_status groupby_sum_fp32(const int32_t* keys, const float* values, int64_t n, int64_t num_groups,
+                              float* out, void* stream) {
+    if (!out || n < 0 || num_groups < 1 || num_groups > INT32_MAX) return REPRO_EINVAL;
+    if (n > 0 && (!keys || !values)) return REPRO_EINVAL;
+    return from_cuda(launch_groupby_fp32(keys, values, n, num_groups, out, (cudaStream_t)stream));
+}
+
+const char* repro_strerror(repro_status status) {
+    switch (status) {
+        case REPRO_OK: return "ok";
+        case REPRO_EINVAL: return "invalid argument";
+        case REPRO_EKEY: return "a key outside [0, num_groups) was seen";
+        case REPRO_ERANGE: return "size beyond the supported maximum";
+        case REPRO_ENOMEM: return "scratch memory could not be allocated";
+        case REPRO_ECUDA: return "CUDA error";
+        case REPRO_ETIMEOUT: return "a bounded device wait gave up";
+        case REPRO_ELAYOUT: return "state header does not match dtype / L / num_groups";
+    }
+    return "unknown status";
+}
+
+int repro_version(void) { return 100; }
+
+}  // extern "C"

@@ -1,0 +1,279 @@
+// repro_device.cuh -- device-side arithmetic of the reproducible grouped SUM.
+//
+// The paper's repro<T,L> (Sec. III-C, Sec. IV) keeps, per level, a running
+// sum S in [1.5, 1.75) ufp(S) and a carry count C; ulp(S) is the level's
+// unit.  Here each level is held directly as the exact integer
+// T = (S - 1.5 ufp(S)) / ulp(S) + C 2^(m-2): the same value, without the
+// floating-point container.  Everything in this file is integer arithmetic
+// except the final rounding to T (eq. (1)).
+//
+// The grid: level units are u(k) = 2^(g_min + k W), g_min = -1074 (double)
+// or -149 (float), so every finite value is an integer multiple of u(0).
+// A value b = mant * 2^p * u(0) needs the top grid index
+//   K(b) = min{K >= 0 : |b| < 2^(W-1) u(K)}          (Algorithm 2's raise test)
+// and its digit at grid index k is
+//   d_k(b) = RNE(b / u(k)) - 2^W RNE(b / u(k+1)),    |d_k| <= 2^(W-1),
+// which is the contribution q / u of Algorithm 2's transform against the
+// constant extractor 1.5 ufp(S) (ties to even).  d_k does not depend on the
+// window the value is extracted in, which is what lets partial states with
+// different windows merge exactly.
+#pragma once
+
+#include <cstdint>
+
+#include "repro.h"
+
+namespace rp {
+
+template <typename T>
+struct Traits;
+
+template <>
+struct Traits<double> {
+    static constexpr int W = 40;       // bits between levels (Sec. III-C)
+    static constexpr int M = 52;       // fraction bits
+    static constexpr int KMAX = 51;    // top grid index with a finite S
+    static constexpr int GMIN = -1074; // exponent of u(0)
+    static constexpr int BIAS = 1023;
+    static constexpr int EMIN = -1022;
+    static constexpr int EMAX = 1023;
+};
+
+template <>
+struct Traits<float> {
+    static constexpr int W = 18;
+    static constexpr int M = 23;
+    static constexpr int KMAX = 14;
+    static constexpr int GMIN = -149;
+    static constexpr int BIAS = 127;
+    static constexpr int EMIN = -126;
+    static constexpr int EMAX = 127;
+};
+
+// A value split into sign, integer significand and grid position.
+struct Split {
+    uint64_t mant;  // |b| = mant * 2^p * u(0)
+    int p;
+    int kb;         // K(b)
+    uint32_t flag;  // REPRO_FLAG_* for NaN / Inf / out of range; 0 otherwise
+    bool neg;
+};
+
+__device__ __forceinline__ Split split_value(double b) {
+    const uint64_t bits = (uint64_t)__double_as_longlong(b);
+    Split s;
+    s.neg = (bits >> 63) != 0;
+    const uint32_t E = (uint32_t)(bits >> 52) & 0x7ffu;
+    const uint64_t F = bits & ((1ull << 52) - 1);
+    s.flag = 0;
+    if (E == 0x7ffu) {
+        s.flag = F ? REPRO_FLAG_NAN : (s.neg ? REPRO_FLAG_NEG_INF : REPRO_FLAG_POS_INF);
+        s.mant = 0; s.p = 0; s.kb = 0;
+        return s;
+    }
+    if (E == 0) {  // subnormal or zero: top bit at t = 63 - clz, K = (t + 1) / W
+        s.mant = F;
+        s.p = 0;
+        s.kb = F ? (64 - __clzll((long long)F)) / 40 : 0;
+    } else {       // normal: top bit at t = E + 51, K = (t + 1) / W
+        s.mant = F | (1ull << 52);
+        s.p = (int)E - 1;
+        s.kb = ((int)E + 52) / 40;
+    }
+    if (s.kb > Traits<double>::KMAX) s.flag = REPRO_FLAG_RANGE;
+    return s;
+}
+
+__device__ __forceinline__ Split split_value(float b) {
+    const uint32_t bits = (uint32_t)__float_as_int(b);
+    Split s;
+    s.neg = (bits >> 31) != 0;
+    const uint32_t E = (bits >> 23) & 0xffu;
+    const uint32_t F = bits & ((1u << 23) - 1);
+    s.flag = 0;
+    if (E == 0xffu) {
+        s.flag = F ? REPRO_FLAG_NAN : (s.neg ? REPRO_FLAG_NEG_INF : REPRO_FLAG_POS_INF);
+        s.mant = 0; s.p = 0; s.kb = 0;
+        return s;
+    }
+    if (E == 0) {  // top bit at t = 31 - clz
+        s.mant = F;
+        s.p = 0;
+        s.kb = F ? (32 - __clz((int)F)) / 18 : 0;
+    } else {       // top bit at t = E + 22
+        s.mant = F | (1u << 23);
+        s.p = (int)E - 1;
+        s.kb = ((int)E + 23) / 18;
+    }
+    if (s.kb > Traits<float>::KMAX) s.flag = REPRO_FLAG_RANGE;
+    return s;
+}
+
+// Low 64 bits of RNE(mant * 2^s), ties to even; mant < 2^53.
+__device__ __forceinline__ uint64_t rne_scaled(uint64_t mant, int s) {
+    if (s >= 0) return s < 64 ? (mant << s) : 0ull;
+    const int r = -s;
+    if (r >= 64) return 0ull;
+    const uint64_t q = mant >> r;
+    const uint64_t rem = mant - (q << r);
+    const uint64_t half = 1ull << (r - 1);
+    return q + (uint64_t)((rem > half) | ((rem == half) & (uint32_t)(q & 1)));
+}
+
+// The (at most three) nonzero digits of a split value in the window with top
+// grid index K and L levels: grid indices max(K(b) - 2, K - L + 1, 0) ..
+// min(K(b), K).  A value's bits span at most three W-bit levels (53 bits
+// over W = 40, 24 bits over W = 18), so lower digits vanish.
+// Calls f(level, digit) for each, level j = K - k (0 = top of the window).
+template <typename T, typename F>
+__device__ __forceinline__ void for_each_digit(const Split& s, int K, int L, F&& f) {
+    constexpr int W = Traits<T>::W;
+    const int khi = min(s.kb, K);
+    const int klo = max(max(s.kb - 2, K - L + 1), 0);
+    if (s.mant == 0 || khi < klo) return;
+    uint64_t r_up = rne_scaled(s.mant, s.p - W * (khi + 1));
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        const int k = khi - i;
+        if (k >= klo) {
+            const uint64_t r = rne_scaled(s.mant, s.p - W * k);
+            const long long d = (long long)(r - (r_up << W));
+            if (d != 0) f(K - k, s.neg ? -d : d);
+            r_up = r;
+        }
+    }
+}
+
+// ---------------------------------------------------------------- state view
+
+struct StateView {
+    unsigned char* base;
+    int L;
+    long long G;
+
+    __device__ __forceinline__ repro_state_header* header() const {
+        return reinterpret_cast<repro_state_header*>(base);
+    }
+    __device__ __forceinline__ size_t stride() const { return 8 + 16 * (size_t)L; }
+    __device__ __forceinline__ int* K(long long g) const {
+        return reinterpret_cast<int*>(base + sizeof(repro_state_header) + (size_t)g * stride());
+    }
+    __device__ __forceinline__ unsigned* flags(long long g) const {
+        return reinterpret_cast<unsigned*>(K(g) + 1);
+    }
+    __device__ __forceinline__ long long* lo(long long g, int j) const {
+        return reinterpret_cast<long long*>(base + sizeof(repro_state_header) + (size_t)g * stride() + 8 +
+                                            16 * (size_t)j);
+    }
+    __device__ __forceinline__ long long* hi(long long g, int j) const { return lo(g, j) + 1; }
+};
+
+// Add a signed 64-bit amount to a 128-bit bin held as hi 2^64 + lo (both
+// halves signed): lo takes the add, and the rare signed overflow of lo,
+// detected from the value the atomic returns, moves one unit into hi.
+// Adds commute, so the final (lo, hi) do not depend on their order.
+__device__ __forceinline__ void add128_atomic(long long* lo, long long* hi, long long d) {
+    const unsigned long long old = atomicAdd(reinterpret_cast<unsigned long long*>(lo),
+                                             (unsigned long long)d);
+    const long long o = (long long)old;
+    const long long nw = (long long)(old + (unsigned long long)d);
+    if (((o >= 0) == (d >= 0)) && ((nw >= 0) != (d >= 0)))
+        atomicAdd(reinterpret_cast<unsigned long long*>(hi), d >= 0 ? 1ull : ~0ull);
+}
+
+__device__ __forceinline__ __int128 bin_read(const long long* lo, const long long* hi) {
+    return (((__int128)*hi) << 64) + (__int128)*lo;
+}
+
+__device__ __forceinline__ void bin_write(long long* lo, long long* hi, __int128 v) {
+    const long long l = (long long)(unsigned long long)v;
+    *lo = l;
+    *hi = (long long)((v - (__int128)l) >> 64);
+}
+
+// ----------------------------------------------------------------- finalize
+
+// RN_T(+-mag * 2^e2), round to nearest even, gradual underflow, overflow to
+// infinity; e2 >= g_min so results below the normal range are exact.
+template <typename T>
+__device__ __forceinline__ T round_scaled(bool neg, unsigned __int128 mag, int e2);
+
+template <>
+__device__ __forceinline__ double round_scaled<double>(bool neg, unsigned __int128 mag, int e2) {
+    if (mag == 0) return 0.0;
+    const uint64_t mh = (uint64_t)(mag >> 64), ml = (uint64_t)mag;
+    const int nb = mh ? 128 - __clzll((long long)mh) : 64 - __clzll((long long)ml);
+    int E = nb - 1 + e2;
+    uint64_t bits;
+    if (E < -1022) {
+        bits = (uint64_t)(mag << (e2 + 1074));  // exact: below 2^52 units of 2^-1074
+    } else {
+        const int sh = nb - 53;
+        uint64_t q;
+        if (sh <= 0) {
+            q = ml << (-sh);
+        } else {
+            q = (uint64_t)(mag >> sh);
+            const unsigned __int128 rem = mag - ((unsigned __int128)q << sh);
+            const unsigned __int128 half = (unsigned __int128)1 << (sh - 1);
+            if (rem > half || (rem == half && (q & 1))) ++q;
+            if (q == (1ull << 53)) { q >>= 1; ++E; }
+        }
+        if (E > 1023) return neg ? -__longlong_as_double(0x7ff0000000000000ll)
+                                 : __longlong_as_double(0x7ff0000000000000ll);
+        bits = ((uint64_t)(E + 1023) << 52) | (q & ((1ull << 52) - 1));
+    }
+    if (neg) bits |= 1ull << 63;
+    return __longlong_as_double((long long)bits);
+}
+
+template <>
+__device__ __forceinline__ float round_scaled<float>(bool neg, unsigned __int128 mag, int e2) {
+    if (mag == 0) return 0.0f;
+    const uint64_t mh = (uint64_t)(mag >> 64), ml = (uint64_t)mag;
+    const int nb = mh ? 128 - __clzll((long long)mh) : 64 - __clzll((long long)ml);
+    int E = nb - 1 + e2;
+    uint32_t bits;
+    if (E < -126) {
+        bits = (uint32_t)(mag << (e2 + 149));
+    } else {
+        const int sh = nb - 24;
+        uint64_t q;
+        if (sh <= 0) {
+            q = ml << (-sh);
+        } else {
+            q = (uint64_t)(mag >> sh);
+            const unsigned __int128 rem = mag - ((unsigned __int128)q << sh);
+            const unsigned __int128 half = (unsigned __int128)1 << (sh - 1);
+            if (rem > half || (rem == half && (q & 1))) ++q;
+            if (q == (1ull << 24)) { q >>= 1; ++E; }
+        }
+        if (E > 127) return neg ? -__int_as_float(0x7f800000) : __int_as_float(0x7f800000);
+        bits = ((uint32_t)(E + 127) << 23) | ((uint32_t)q & ((1u << 23) - 1));
+    }
+    if (neg) bits |= 1u << 31;
+    return __int_as_float((int)bits);
+}
+
+__device__ __forceinline__ double t_add(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ float t_add(float a, float b) { return __fadd_rn(a, b); }
+
+template <typename T>
+__device__ __forceinline__ T quiet_nan();
+template <>
+__device__ __forceinline__ double quiet_nan<double>() { return __longlong_as_double(0x7ff8000000000000ll); }
+template <>
+__device__ __forceinline__ float quiet_nan<float>() { return __int_as_float(0x7fc00000); }
+
+template <typename T>
+__device__ __forceinline__ T inf_of(bool neg);
+template <>
+__device__ __forceinline__ double inf_of<double>(bool neg) {
+    return __longlong_as_double(neg ? (long long)0xfff0000000000000ull : 0x7ff0000000000000ll);
+}
+template <>
+__device__ __forceinline__ float inf_of<float>(bool neg) {
+    return __int_as_float(neg ? (int)0xff800000u : 0x7f800000);
+}
+
+}  // namespace rp

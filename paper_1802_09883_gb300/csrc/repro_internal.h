@@ -1,0 +1,43 @@
+// repro_internal.h -- host-side interface between the C ABI (repro_api.cu)
+// and the kernel launchers (repro_kernels.cu).  Not installed.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+
+namespace rp {
+
+struct DeviceInfo {
+    int device;
+    int sms;            // multiprocessors
+    size_t smem_optin;  // opt-in shared memory per block, bytes
+};
+
+// Properties of the current device (queried once per device).
+const DeviceInfo& device_info();
+
+// Profiling hooks (repro_profile_enable / repro_profile_read) and the launch
+// counter (repro_launch_count).
+enum ProfKernel { PROF_WINDOW, PROF_ACCUM, PROF_FUSED, PROF_PARTITION, PROF_MERGE, PROF_FINALIZE, PROF_FP64,
+                  PROF_FP32, PROF_COUNT };
+void prof_begin(ProfKernel k, cudaStream_t s);
+void prof_end(ProfKernel k, cudaStream_t s);
+void count_launches(int k);
+
+cudaError_t launch_init_state(void* state, int dtype, int L, long long G, cudaStream_t s);
+
+size_t two_pass_scratch_bytes(long long G);
+cudaError_t launch_groupby_two_pass(const int32_t* keys, const void* vals, long long n, int dtype, int L,
+                                    long long G, void* state, void* scratch, cudaStream_t s);
+
+cudaError_t launch_merge(void* dst, const void* src, int dtype, int L, long long G, cudaStream_t s);
+cudaError_t launch_finalize(const void* state, int dtype, int L, long long G, void* out, cudaStream_t s);
+
+cudaError_t launch_groupby_fp64(const int32_t* keys, const double* vals, long long n, long long G, double* out,
+                                cudaStream_t s);
+cudaError_t launch_groupby_fp32(const int32_t* keys, const float* vals, long long n, long long G, float* out,
+                                cudaStream_t s);
+
+}  // namespace rp

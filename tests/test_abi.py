@@ -1,0 +1,69 @@
+"""The C ABI library loads and exports what include/repro.h declares (CPU)."""
+import ctypes
+import subprocess
+
+import pytest
+
+import paper_1802_09883_gb300 as R
+from paper_1802_09883_gb300 import build as B
+
+
+def test_library_builds_and_exports_every_declared_symbol():
+    path = B.build()
+    lib = ctypes.CDLL(path)
+    names = R.declared_functions()
+    assert {"repro_groupby_sum", "repro_merge", "repro_finalize", "groupby_sum_fp64"} <= set(names)
+    for name in names:
+        assert hasattr(lib, name), name
+    out = subprocess.run(["nm", "-D", "--defined-only", path], capture_output=True, text=True).stdout
+    exported = {ln.split()[-1] for ln in out.splitlines() if " T " in ln}
+    assert set(names) <= exported
+
+
+def test_state_bytes_layout():
+    lib = R.lib()
+    for L in (1, 2, 3, 4):
+        for G in (1, 1024, 1 << 24):
+            assert lib.repro_state_bytes(R.REPRO_F64, L, G) == 64 + G * (8 + 16 * L)
+            assert lib.repro_state_bytes(R.REPRO_F32, L, G) == 64 + G * (8 + 16 * L)
+    assert lib.repro_state_bytes(R.REPRO_F64, 0, 10) == 0
+    assert lib.repro_state_bytes(R.REPRO_F64, 5, 10) == 0
+    assert lib.repro_state_bytes(R.REPRO_F64, 2, 0) == 0
+    assert lib.repro_state_bytes(R.REPRO_F64, 2, 1 << 31) == 0
+    assert lib.repro_state_bytes(7, 2, 10) == 0
+
+
+def test_argument_errors_are_synchronous_and_need_no_gpu():
+    lib = R.lib()
+    EINVAL = 1
+    fake = 0x1000  # never dereferenced: every call below fails validation first
+    assert lib.repro_state_init(None, 0, 3, 10, None) == EINVAL
+    assert lib.repro_state_init(fake, 0, 0, 10, None) == EINVAL
+    assert lib.repro_state_init(fake + 8, 0, 3, 10, None) == EINVAL  # misaligned
+    assert lib.repro_groupby_sum(fake, fake, -1, 0, 3, 10, fake, None) == EINVAL
+    assert lib.repro_groupby_sum(None, None, 5, 0, 3, 10, fake, None) == EINVAL
+    assert lib.repro_groupby_sum(fake, fake, 5, 2, 3, 10, fake, None) == EINVAL  # dtype
+    assert lib.repro_groupby_sum(fake, fake, 5, 0, 3, 0, fake, None) == EINVAL  # G
+    assert lib.repro_merge(fake, fake, 0, 3, 10, None) == EINVAL  # same buffer
+    assert lib.repro_merge(fake, fake + 16, 0, 3, 10, None) == EINVAL  # overlap
+    assert lib.repro_finalize(fake, 0, 3, 10, None, None) == EINVAL
+    assert lib.repro_state_check(None, None, None) == EINVAL
+    assert lib.groupby_sum_fp64(fake, fake, 4, 0, fake, None) == EINVAL
+
+
+def test_strerror_covers_every_status():
+    lib = R.lib()
+    for code in range(8):
+        s = lib.repro_strerror(code).decode()
+        assert s and s != "unknown status"
+    assert lib.repro_strerror(99).decode() == "unknown status"
+
+
+def test_no_cpu_fallback():
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("CPU-only check")
+    with pytest.raises(RuntimeError):
+        R.State(16, 3)
+    with pytest.raises(ValueError):
+        R.groupby_sum_fp64(torch.zeros(4, dtype=torch.int32), torch.zeros(4, dtype=torch.float64), 4)

@@ -1,0 +1,232 @@
+"""GPU path vs the CPU oracle, bit for bit (states and results).
+
+Every test calls the CUDA kernels through the C ABI (via the thin binding)
+and compares with oracle/repro_oracle.c on the same seeded inputs.
+"""
+import numpy as np
+import pytest
+import torch
+
+import paper_1802_09883_gb300 as R
+from paper_1802_09883_gb300 import workloads as WL
+from oracle import oracle as O
+
+pytestmark = pytest.mark.gpu
+
+DEV = "cuda"
+
+
+def _np(t):
+    return t.detach().cpu().numpy()
+
+
+def oracle_state(keys, vals, G, L, threads=4):
+    st = O.init(vals.dtype, L, G)
+    bad = O.groupby_sum(st, keys, vals, threads=threads)
+    return st, bad
+
+
+def assert_state_equal(gst: R.State, ost):
+    K, fl, lo, hi = gst.host_view()
+    oK, ofl, olo, ohi = O.to_bins(ost)
+    assert np.array_equal(K, oK), "K differs"
+    assert np.array_equal(fl, ofl), "flags differ"
+    assert np.array_equal(lo, olo), "bins (lo) differ"
+    assert np.array_equal(hi, ohi), "bins (hi) differ"
+
+
+def assert_bits_equal(a, b):
+    a, b = np.asarray(a), np.asarray(b)
+    assert a.dtype == b.dtype and a.shape == b.shape
+    ai = a.view(np.int64 if a.dtype == np.float64 else np.int32)
+    bi = b.view(np.int64 if b.dtype == np.float64 else np.int32)
+    mism = np.flatnonzero(ai != bi)
+    assert mism.size == 0, f"{mism.size} results differ, first at {mism[:5]}: {a[mism[:5]]} vs {b[mism[:5]]}"
+
+
+def run_gpu(keys_t, vals_t, G, L):
+    st = R.State(G, L, vals_t.dtype)
+    st.add(keys_t, vals_t)
+    out = st.finalize()
+    torch.cuda.synchronize()
+    return st, out
+
+
+# ----------------------------------------------------------------- config 0
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+def test_plain_1e6_rows_1024_groups_L3(dtype):
+    w = WL.plain(n=1_000_000, G=1024, L=3, seed=1, device=DEV, dtype=dtype)
+    st, out = run_gpu(w.keys, w.values, w.G, w.L)
+    assert st.check() == 0
+    ost, bad = oracle_state(_np(w.keys), _np(w.values), w.G, w.L)
+    assert bad == 0
+    assert_state_equal(st, ost)
+    assert_bits_equal(_np(out), O.finalize(ost))
+
+
+# ------------------------------------------------------- shapes and levels
+
+@pytest.mark.parametrize("L", [1, 2, 3, 4])
+@pytest.mark.parametrize("G", [1, 16, 1000, 3000, 7777, 70000])
+def test_group_counts_and_levels(G, L):
+    n = 200_003  # several tiles and a ragged tail
+    w = WL.plain(n=n, G=G, L=L, seed=G * 10 + L, device=DEV, e_lo=-60, e_hi=60)
+    st, out = run_gpu(w.keys, w.values, G, L)
+    ost, _ = oracle_state(_np(w.keys), _np(w.values), G, L)
+    assert_state_equal(st, ost)
+    assert_bits_equal(_np(out), O.finalize(ost))
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+@pytest.mark.parametrize("L", [1, 2, 4])
+def test_wide_exponent_range_and_subnormals(dtype, L):
+    g = torch.Generator(device=DEV)
+    g.manual_seed(5 + L)
+    n, G = 100_000, 37
+    lo_e, hi_e = (-1074, 1000) if dtype == torch.float64 else (-149, 118)
+    keys = WL.uniform_keys(n, G, g, DEV)
+    # exponents across the whole range (random_values takes biased-exponent
+    # offsets, so subnormals are drawn separately)
+    vals = WL.random_values(n, max(lo_e, -1022 if dtype == torch.float64 else -126), hi_e, g, DEV, dtype)
+    sub = torch.randint(1, 1 << (20 if dtype == torch.float64 else 12), (n // 10,), generator=g, device=DEV)
+    sub = sub.to(torch.int64 if dtype == torch.float64 else torch.int32).view(dtype)
+    vals[: n // 10] = sub
+    st, out = run_gpu(keys, vals, G, L)
+    ost, _ = oracle_state(_np(keys), _np(vals), G, L)
+    assert_state_equal(st, ost)
+    assert_bits_equal(_np(out), O.finalize(ost))
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+def test_special_values_and_empty_groups(dtype):
+    npd = np.float64 if dtype == torch.float64 else np.float32
+    lim = 2.0 ** 1005 if dtype == torch.float64 else 2.0 ** 120
+    keys = np.array([0, 0, 1, 1, 2, 3, 3, 4, 4, 5, 5, 6, 8, 8], np.int32)
+    vals = np.array([1.0, np.nan, np.inf, 2.0, -np.inf, np.inf, -np.inf, lim, 1.0, 0.0, -0.0, -np.inf,
+                     np.nextafter(npd(lim), npd(0)), -np.nextafter(npd(lim), npd(0))], npd)
+    kt, vt = torch.from_numpy(keys).to(DEV), torch.from_numpy(vals).to(DEV)
+    for L in (1, 3, 4):
+        st, out = run_gpu(kt, vt, 10, L)
+        ost, _ = oracle_state(keys, vals, 10, L, threads=1)
+        assert_state_equal(st, ost)
+        assert_bits_equal(_np(out), O.finalize(ost))
+        o = _np(out)
+        assert o.view(np.int64 if npd == np.float64 else np.int32)[0] == \
+            (0x7FF8000000000000 if npd == np.float64 else 0x7FC00000)
+        assert o[7] == 0 and not np.signbit(o[7]) and o[9] == 0 and not np.signbit(o[9])
+
+
+def test_bad_keys_are_reported_and_skipped():
+    keys = torch.tensor([0, 5, -1, 2, 1 << 30], dtype=torch.int32, device=DEV)
+    vals = torch.tensor([1.0, 2.0, 3.0, 4.0, 5.0], dtype=torch.float64, device=DEV)
+    st = R.State(5, 2)
+    st.add(keys, vals)
+    out = st.finalize()
+    with pytest.raises(R.ReproError) as ei:
+        st.check()
+    assert ei.value.status == 2  # REPRO_EKEY
+    assert _np(out).tolist() == [1.0, 0.0, 4.0, 0.0, 0.0]
+
+
+def test_empty_input():
+    st = R.State(8, 3)
+    st.add(torch.empty(0, dtype=torch.int32, device=DEV), torch.empty(0, dtype=torch.float64, device=DEV))
+    out = st.finalize()
+    assert st.check() == 0
+    assert (_np(out) == 0).all() and not np.signbit(_np(out)).any()
+
+
+def test_layout_mismatch_is_detected():
+    """A state initialised for L = 3 but passed with L = 4 is refused on the
+    device (REPRO_ELAYOUT) and left untouched."""
+    st = R.State(8, 3)
+    with pytest.raises(ValueError):
+        R.State(16, 3).merge(st)
+    lib = R.lib()
+    keys = torch.zeros(4, dtype=torch.int32, device=DEV)
+    vals = torch.ones(4, dtype=torch.float64, device=DEV)
+    buf = torch.zeros(R.state_bytes(torch.float64, 4, 8), dtype=torch.uint8, device=DEV)
+    buf[: st.tensor.numel()] = st.tensor
+    before = _np(buf).copy()
+    s = torch.cuda.current_stream().cuda_stream
+    assert lib.repro_groupby_sum(keys.data_ptr(), vals.data_ptr(), 4, 0, 4, 8, buf.data_ptr(), s) == 0
+    assert lib.repro_state_check(buf.data_ptr(), None, s) == 7  # REPRO_ELAYOUT
+    after = _np(buf)
+    assert np.array_equal(after[64:], before[64:])
+
+
+# ------------------------------------------------------------ invariants
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+def test_shuffles_splits_and_merges_give_identical_bytes(dtype):
+    w = WL.sweep_cell(G=1 << 10, dist="zipf", L=3, n=1 << 20, seed=7, device=DEV, dtype=dtype)
+    ref, ref_out = run_gpu(w.keys, w.values, w.G, w.L)
+    ref_bytes = _np(ref.tensor)
+    g = torch.Generator(device=DEV)
+    g.manual_seed(3)
+    for trial in range(3):
+        p = torch.randperm(w.n, generator=g, device=DEV)
+        k, v = w.keys[p], w.values[p]
+        st, out = run_gpu(k, v, w.G, w.L)
+        assert np.array_equal(_np(st.tensor), ref_bytes)
+        # split into calls on one state
+        cuts = sorted(torch.randint(1, w.n, (5,), generator=g, device=DEV).tolist())
+        edges = [0] + cuts + [w.n]
+        acc = R.State(w.G, w.L, dtype)
+        parts = []
+        for a, b in zip(edges[:-1], edges[1:]):
+            acc.add(k[a:b], v[a:b])
+            s = R.State(w.G, w.L, dtype)
+            s.add(k[a:b], v[a:b])
+            parts.append(s)
+        assert np.array_equal(_np(acc.tensor), ref_bytes)
+        # separate states merged in a shuffled order
+        order = torch.randperm(len(parts), generator=g, device=DEV).tolist()
+        m = parts[order[0]]
+        for i in order[1:]:
+            m.merge(parts[i])
+        torch.cuda.synchronize()
+        assert np.array_equal(_np(m.tensor), ref_bytes)
+    ost, _ = oracle_state(_np(w.keys), _np(w.values), w.G, w.L)
+    assert_state_equal(ref, ost)
+    assert_bits_equal(_np(ref_out), O.finalize(ost))
+
+
+def test_merge_with_different_windows_matches_oracle():
+    g = torch.Generator(device=DEV)
+    g.manual_seed(11)
+    G, L = 300, 3
+    ka, kb = WL.uniform_keys(50_000, G, g, DEV), WL.uniform_keys(50_000, G, g, DEV)
+    va = WL.random_values(50_000, -90, -20, g, DEV)
+    vb = WL.random_values(50_000, -30, 70, g, DEV)
+    A, B = R.State(G, L), R.State(G, L)
+    A.add(ka, va)
+    B.add(kb, vb)
+    A.merge(B)
+    oa, _ = oracle_state(_np(ka), _np(va), G, L)
+    ob, _ = oracle_state(_np(kb), _np(vb), G, L)
+    O.merge(oa, ob)
+    assert_state_equal(A, oa)
+    assert_bits_equal(_np(A.finalize()), O.finalize(oa))
+
+
+# -------------------------------------------------------------- baselines
+
+def test_fp64_baseline_close_to_exact():
+    w = WL.plain(n=1_000_000, G=1024, L=3, seed=1, device=DEV)
+    out = _np(R.groupby_sum_fp64(w.keys, w.values, w.G))
+    ref = O.groupby_sum_values(_np(w.keys), _np(w.values), w.G, 4)  # L = 4 holds every bit here
+    absum = np.bincount(_np(w.keys), weights=np.abs(_np(w.values)), minlength=w.G)
+    cnt = np.bincount(_np(w.keys), minlength=w.G)
+    # eq. (5): (n - 1) eps sum |b|
+    assert np.all(np.abs(out - ref) <= (cnt - 1).clip(min=0) * 2.0 ** -53 * absum + 1e-300)
+
+
+def test_fp32_baseline_runs():
+    w = WL.plain(n=100_000, G=100, L=3, seed=4, device=DEV, dtype=torch.float32)
+    out = _np(R.groupby_sum_fp32(w.keys, w.values, w.G)).astype(np.float64)
+    ref = np.bincount(_np(w.keys), weights=_np(w.values).astype(np.float64), minlength=w.G)
+    absum = np.bincount(_np(w.keys), weights=np.abs(_np(w.values)).astype(np.float64), minlength=w.G)
+    cnt = np.bincount(_np(w.keys), minlength=w.G)
+    assert np.all(np.abs(out - ref) <= cnt * 2.0 ** -24 * absum + 1e-30)
