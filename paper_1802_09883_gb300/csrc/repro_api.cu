@@ -22,8 +22,10 @@ const DeviceInfo& device_info() {
     if (dev < 0 || dev >= 64) dev = 0;
     std::lock_guard<std::mutex> lock(mu);
     if (!have[dev]) {
-        DeviceInfo d{dev, 1, 48 * 1024};
+        DeviceInfo d{dev, 1, 48 * 1024, 48 * 1024};
         int v = 0;
+        if (cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) == cudaSuccess && v > 0)
+            d.smem_per_sm = (size_t)v;
         if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && v > 0) d.sms = v;
         if (cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) == cudaSuccess && v > 0)
             d.smem_optin = (size_t)v;
@@ -79,6 +81,11 @@ repro_status repro_groupby_sum(const int32_t* keys, const void* values, int64_t 
     if ((uintptr_t)state % 16 || (uintptr_t)keys % 4 || (uintptr_t)values % (dtype == REPRO_F64 ? 8 : 4))
         return REPRO_EINVAL;
     cudaStream_t s = (cudaStream_t)stream;
+    if (n > 0 && fused_supported(dtype, L, num_groups, keys, values)) {
+        Scratch scratch(fused_scratch_bytes(dtype, L, num_groups, n), s);
+        if (scratch.err != cudaSuccess) return from_cuda(scratch.err);
+        return from_cuda(launch_groupby_fused(keys, values, n, dtype, L, num_groups, state, scratch.p, s));
+    }
     Scratch scratch(two_pass_scratch_bytes(num_groups), s);
     if (scratch.err != cudaSuccess) return from_cuda(scratch.err);
     return from_cuda(launch_groupby_two_pass(keys, values, n, dtype, L, num_groups, state, scratch.p, s));

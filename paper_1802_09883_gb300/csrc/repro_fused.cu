@@ -1,0 +1,707 @@
+// repro_fused.cu -- single-pass reproducible grouped SUM for group tables
+// that fit in shared memory.
+//
+// One read of the rows.  Each persistent CTA owns a contiguous range of
+// tiles; a producer warp streams key/value tiles into a ring of shared-memory
+// stages with 1-D TMA bulk copies (cp.async.bulk + mbarrier), and the
+// consumer warps turn every row into at most three integer digits added with
+// shared-memory atomics into a CTA-private table repro<T,L>[G].
+//
+// Windows are CTA-local (Algorithm 2's level raising, done per tile): a row
+// whose top grid index K(b) exceeds its group's current CTA window is
+// deferred; after the tile the CTA raises the windows of those groups
+// (shifting their bins, dropping levels that fall off the bottom) and adds
+// the deferred rows.  Digits are the same in every window that can hold the
+// value, so rows added before a raise stay correct.  At the end each CTA
+// writes its table as a partial state; k_merge_partials aligns and adds the
+// partials into the caller's state (operator+=(repro), Algorithm 4's merge).
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <cstdio>
+#include <cstdlib>
+
+#include "ptx.cuh"
+#include "repro_device.cuh"
+#include "repro_internal.h"
+
+namespace rp {
+
+namespace {
+
+constexpr uint64_t kWaitNs = 2000000000ull;  // every mbarrier wait gives up after 2 s
+
+struct FusedSmem {
+    // byte offsets into dynamic shared memory
+    size_t bars, ctl, keys, vals, bins, K, Kp, F, dlist, rlist, total;
+};
+
+__host__ __device__ inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+template <typename T>
+__host__ __device__ inline FusedSmem fused_layout(int S, int R, int G, int L, int C) {
+    FusedSmem m;
+    size_t o = 0;
+    m.bars = o;
+    o += 16 * (size_t)S;  // full[S], empty[S]
+    m.ctl = o;
+    o += 64;  // counters[3][2], abort, pad
+    o = align_up(o, 128);
+    m.keys = o;
+    o += (size_t)S * R * 4;
+    o = align_up(o, 128);
+    m.vals = o;
+    o += (size_t)S * R * sizeof(T);
+    o = align_up(o, 16);
+    m.bins = o;  // LO[G][L][C] (uint32) then HI[G][L][C] (int32)
+    o += (size_t)G * L * C * 8;
+    m.K = o;
+    o += (size_t)G * 4;
+    m.Kp = o;
+    o += (size_t)G * 4;
+    m.F = o;
+    o += (size_t)G * 4;
+    m.dlist = o;
+    o += (size_t)R * 2;
+    o = align_up(o, 4);
+    m.rlist = o;
+    o += (size_t)(R < G ? R : G) * 4;
+    m.total = align_up(o, 16);
+    return m;
+}
+
+struct FusedArgs {
+    const int32_t* keys;
+    const void* vals;
+    long long n;
+    int G;
+    int R;             // rows per tile
+    int S;             // stages
+    int C;             // copies of the table (1, or 32 for lane-private copies)
+    long long ntiles;  // full tiles (n / R)
+    int tiles_per_cta;
+    long long flush_rows;     // flush the int64 table into the partial before this many rows
+    unsigned char* partials;  // [gridDim.x][G] records of 8 + 16 L bytes
+    unsigned* errors;         // state header error word
+};
+
+}  // namespace
+
+// The CTA table holds each bin of each group as a 64-bit value
+// HI * 2^32 + LO with LO unsigned and HI signed, both 32-bit words in shared
+// memory: 32-bit shared atomics run far faster than 64-bit ones.  A digit d
+// is added to LO as its low 32 bits; the value LO held before (returned by
+// the atomic) tells whether LO wrapped, and HI takes d's high part plus that
+// carry, skipped when zero.  Every add is exact and adds commute, so the
+// result is independent of their order.  With C copies, lane l uses copy
+// l mod C (C = 32: conflict-free, and skewed keys never collide in a warp).
+struct Table {
+    unsigned* lo;
+    int* hi;
+    int L, C;
+    __device__ __forceinline__ size_t at(int g, int j, int copy) const {
+        return ((size_t)g * L + j) * C + copy;
+    }
+};
+
+__device__ __forceinline__ void add_digit(const Table& t, size_t i, long long d) {
+    const unsigned lo = (unsigned)(unsigned long long)d;
+    const unsigned old = atomicAdd(&t.lo[i], lo);
+    const int carry = (unsigned)(old + lo) < old;
+    const int hi = (int)(d >> 32) + carry;
+    if (hi != 0) atomicAdd(&t.hi[i], hi);
+}
+
+__device__ __forceinline__ long long table_value(const Table& t, size_t i) {
+    return (long long)(((unsigned long long)(long long)t.hi[i] << 32) + (unsigned long long)t.lo[i]);
+}
+
+// Add one row's digits into the CTA table (its window must hold the value).
+template <typename T, int L>
+__device__ __forceinline__ void add_row(const Split& s, int K, const Table& t, int g, int copy) {
+    long long top, mid, low;
+    digits3<T>(s, top, mid, low);
+    const int j = K - s.kb;  // level of the value's top digit
+    if (j < L && top != 0) add_digit(t, t.at(g, j, copy), top);
+    if (j + 1 < L && s.kb >= 1 && mid != 0) add_digit(t, t.at(g, j + 1, copy), mid);
+    if (j + 2 < L && s.kb >= 2 && low != 0) add_digit(t, t.at(g, j + 2, copy), low);
+}
+
+// Phase A for one row: add it, flag it, or defer it until its group's window
+// is raised.
+template <typename T, int L>
+__device__ __forceinline__ void consume_row(int g, T b, int idx, int G, const Table& t, int copy, int* sK,
+                                            int* sKp, unsigned* sF, unsigned short* dlist, int* rlist, int* cnt,
+                                            bool& bad_key) {
+    if ((unsigned)g >= (unsigned)G) {
+        bad_key = true;
+        return;
+    }
+    const Split s = split_value(b);
+    if (s.flag) {
+        atomicOr(&sF[g], s.flag);
+        return;
+    }
+    if (s.mant == 0) return;
+    const int K = sK[g];
+    if (s.kb <= K) {
+        add_row<T, L>(s, K, t, g, copy);
+        return;
+    }
+    dlist[atomicAdd(&cnt[0], 1)] = (unsigned short)idx;
+    if (atomicMax(&sKp[g], s.kb) == K) rlist[atomicAdd(&cnt[1], 1)] = g;  // first raiser of g in this tile
+}
+
+// Shared-window addresses of the hot loop's arrays.
+struct SAddr {
+    uint32_t keys, vals;  // stage s starts at keys + 4 R s, vals + sizeof(T) R s
+    uint32_t K;           // int K[G]
+    uint32_t lo, hi;      // table words [(g L + j) C + copy]
+};
+
+// Value bit-words of four consecutive rows: (hi, lo) per row for double,
+// the single word for float.
+template <typename T>
+struct QuadWords;
+template <>
+struct QuadWords<double> {
+    static __device__ __forceinline__ void load(uint32_t a, uint32_t hi[4], uint32_t lo[4]) {
+        const uint4 p = lds_v4(a), q = lds_v4(a + 16);
+        lo[0] = p.x; hi[0] = p.y; lo[1] = p.z; hi[1] = p.w;
+        lo[2] = q.x; hi[2] = q.y; lo[3] = q.z; hi[3] = q.w;
+    }
+};
+template <>
+struct QuadWords<float> {
+    static __device__ __forceinline__ void load(uint32_t a, uint32_t hi[4], uint32_t lo[4]) {
+        const uint4 p = lds_v4(a);
+        hi[0] = p.x; hi[1] = p.y; hi[2] = p.z; hi[3] = p.w;
+        lo[0] = lo[1] = lo[2] = lo[3] = 0u;
+    }
+};
+
+template <typename T>
+__device__ __forceinline__ T words_value(uint32_t hi, uint32_t lo);
+template <>
+__device__ __forceinline__ double words_value<double>(uint32_t hi, uint32_t lo) {
+    return __longlong_as_double((long long)(((unsigned long long)hi << 32) | lo));
+}
+template <>
+__device__ __forceinline__ float words_value<float>(uint32_t hi, uint32_t) {
+    return __uint_as_float(hi);
+}
+
+// Phase A for four consecutive rows of a staged tile (r0 a multiple of 4):
+// vector loads, then -- when all four rows are ordinary (good key, normal
+// value inside its group's window) -- straight-line digits for the four rows
+// and predicated 32-bit atomics; otherwise the rows go one by one through
+// consume_row.
+template <typename T, int L>
+__device__ __forceinline__ void consume_quad(const SAddr& sa, const int32_t* tk, const T* tv, int r0, int G,
+                                             const Table& t, int copy, int* sK, int* sKp, unsigned* sF,
+                                             unsigned short* dlist, int* rlist, int* cnt, bool& bad_key) {
+    const uint4 k4 = lds_v4(sa.keys + 4u * (uint32_t)r0);
+    const int gq[4] = {(int)k4.x, (int)k4.y, (int)k4.z, (int)k4.w};
+    uint32_t vhi[4], vlo[4];
+    QuadWords<T>::load(sa.vals + (uint32_t)sizeof(T) * (uint32_t)r0, vhi, vlo);
+    int kb[4], K[4];
+    bool fast = true;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const bool ok_key = (unsigned)gq[q] < (unsigned)G;
+        const bool ok_val = Lean<T>::decode_words(vhi[q], kb[q]);
+        K[q] = (int)lds_u32(sa.K + 4u * (uint32_t)(ok_key ? gq[q] : 0));
+        fast = fast && ok_key && ok_val && kb[q] <= K[q];
+    }
+    if (!fast) {  // some row is special, has a bad key, or must wait for a raise
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+            consume_row<T, L>(gq[q], words_value<T>(vhi[q], vlo[q]), r0 + q, G, t, copy, sK, sKp, sF, dlist,
+                              rlist, cnt, bad_key);
+        return;
+    }
+    // common case, straight-line: four rows' digits, then predicated atomics
+    unsigned lo[12];
+    int hi[12];
+    uint32_t at[12];
+    bool on[12];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        Lean<T>::digits(vhi[q], vlo[q], kb[q], &lo[3 * q], &hi[3 * q]);
+        const int j = K[q] - kb[q];  // window level of the value's top digit
+        const uint32_t row = (uint32_t)gq[q] * (uint32_t)(L * t.C) + (uint32_t)copy;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            on[3 * q + k] = (j + k < L) && ((lo[3 * q + k] | (unsigned)hi[3 * q + k]) != 0u);
+            at[3 * q + k] = 4u * (row + (uint32_t)(min(j + k, L - 1) * t.C));
+        }
+    }
+    unsigned old[12];
+#pragma unroll
+    for (int i = 0; i < 12; ++i) old[i] = atom_add_if(on[i], sa.lo + at[i], lo[i]);
+#pragma unroll
+    for (int i = 0; i < 12; ++i) {
+        const int h = hi[i] + (int)((unsigned)(old[i] + lo[i]) < old[i]);
+        red_add_if(on[i] && h != 0, sa.hi + at[i], h);
+    }
+}
+
+// After phase A: raise the windows collected in rlist (dropping low levels)
+// and add the deferred rows.  Consumer-uniform; uses named barrier 1.
+template <typename T, int L>
+__device__ __forceinline__ void raise_and_add(int nr, int nd, const int32_t* tk, const T* tv, const Table& t,
+                                              int* sK, const int* sKp, const unsigned short* dlist,
+                                              const int* rlist, int ctid, int NC) {
+    for (int i = ctid; i < nr * t.C; i += NC) {
+        const int g = rlist[i / t.C];
+        const int copy = i % t.C;
+        const int d = sKp[g] - sK[g];
+#pragma unroll
+        for (int j = L - 1; j >= 0; --j) {
+            const size_t dst = t.at(g, j, copy);
+            if (j - d >= 0) {
+                const size_t src = t.at(g, j - d, copy);
+                t.lo[dst] = t.lo[src];
+                t.hi[dst] = t.hi[src];
+            } else {
+                t.lo[dst] = 0;
+                t.hi[dst] = 0;
+            }
+        }
+    }
+    named_bar_sync(1, NC);
+    for (int i = ctid; i < nr; i += NC) sK[rlist[i]] = sKp[rlist[i]];
+    named_bar_sync(1, NC);
+    for (int i = ctid; i < nd; i += NC) {
+        const int r = dlist[i];
+        const int g = tk[r];
+        const Split s = split_value(tv[r]);
+        add_row<T, L>(s, sK[g], t, g, (ctid & 31) & (t.C - 1));
+    }
+}
+
+// Write (first) or add (later) the CTA table into this CTA's partial record
+// array, then clear the table's bins.  Consumer threads only.
+template <int L>
+__device__ void flush_partial(unsigned char* part, int G, const Table& t, const int* sK, const unsigned* sF,
+                              bool first, int ctid, int NC) {
+    constexpr size_t rec = 8 + 16 * L;
+    for (int g = ctid; g < G; g += NC) {
+        unsigned char* r = part + (size_t)g * rec;
+        int* pK = reinterpret_cast<int*>(r);
+        unsigned* pF = reinterpret_cast<unsigned*>(r + 4);
+        long long* pb = reinterpret_cast<long long*>(r + 8);
+        const int K = sK[g];
+        __int128 acc[L];
+#pragma unroll
+        for (int j = 0; j < L; ++j) {
+            acc[j] = 0;
+            for (int c = 0; c < t.C; ++c) {
+                const size_t i = t.at(g, j, c);
+                acc[j] += (__int128)table_value(t, i);
+                t.lo[i] = 0;
+                t.hi[i] = 0;
+            }
+        }
+        if (first) {
+            *pK = K;
+            *pF = sF[g];
+        } else {
+            const int d = K - *pK;  // the CTA window only rises
+#pragma unroll
+            for (int j = L - 1; j >= 0; --j)
+                if (j - d >= 0) acc[j] += bin_read(&pb[2 * (j - d)], &pb[2 * (j - d) + 1]);
+            *pK = K;
+            *pF |= sF[g];
+        }
+#pragma unroll
+        for (int j = 0; j < L; ++j) bin_write(&pb[2 * j], &pb[2 * j + 1], acc[j]);
+    }
+}
+
+template <typename T, int L, int NCW>
+__global__ void __launch_bounds__(32 * (NCW + 1)) k_fused(FusedArgs a) {
+    constexpr int NC = 32 * NCW;
+    extern __shared__ __align__(128) unsigned char smem[];
+    const FusedSmem m = fused_layout<T>(a.S, a.R, a.G, L, a.C);
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem + m.bars);
+    uint64_t* empty = full + a.S;
+    int* ctl = reinterpret_cast<int*>(smem + m.ctl);  // cnt[3][2] at 0..5, abort at 6
+    int32_t* skeys = reinterpret_cast<int32_t*>(smem + m.keys);
+    T* svals = reinterpret_cast<T*>(smem + m.vals);
+    Table tab;
+    tab.lo = reinterpret_cast<unsigned*>(smem + m.bins);
+    tab.hi = reinterpret_cast<int*>(tab.lo + (size_t)a.G * L * a.C);
+    tab.L = L;
+    tab.C = a.C;
+    int* sK = reinterpret_cast<int*>(smem + m.K);
+    int* sKp = reinterpret_cast<int*>(smem + m.Kp);
+    unsigned* sF = reinterpret_cast<unsigned*>(smem + m.F);
+    unsigned short* dlist = reinterpret_cast<unsigned short*>(smem + m.dlist);
+    int* rlist = reinterpret_cast<int*>(smem + m.rlist);
+    volatile int* abort_flag = &ctl[6];  // consumers only
+
+    const int tid = threadIdx.x;
+    const int G = a.G, R = a.R, S = a.S;
+    for (int i = tid; i < G * L * a.C; i += blockDim.x) {
+        tab.lo[i] = 0;
+        tab.hi[i] = 0;
+    }
+    for (int g = tid; g < G; g += blockDim.x) {
+        sK[g] = 0;
+        sKp[g] = 0;
+        sF[g] = 0;
+    }
+    if (tid < 16) ctl[tid] = 0;
+    if (tid == 0) {
+        for (int s = 0; s < S; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], NCW);
+        }
+        fence_barrier_init();
+    }
+    __syncthreads();
+
+    const long long t0 = (long long)blockIdx.x * a.tiles_per_cta;
+    const long long t1 = min(a.ntiles, t0 + a.tiles_per_cta);
+    const int ntile = (int)max(0ll, t1 - t0);
+    const T* vals = reinterpret_cast<const T*>(a.vals);
+
+    if (tid >= NC) {
+        // ---------------------------------------------------------- producer
+        if (tid == NC) {
+            const uint32_t kb = (uint32_t)R * 4, vb = (uint32_t)R * sizeof(T);
+            int issued = 0;
+            for (int i = 0; i < ntile; ++i) {
+                const int s = i % S;
+                if (i >= S && !mbar_wait_bounded(&empty[s], ((i / S) - 1) & 1, kWaitNs)) {
+                    // consumers will time out on the stages never filled
+                    atomicOr(a.errors, REPRO_ERR_TIMEOUT);
+                    break;
+                }
+                const long long row0 = (t0 + i) * (long long)R;
+                mbar_arrive_expect_tx(&full[s], kb + vb);
+                bulk_g2s(skeys + (size_t)s * R, a.keys + row0, kb, &full[s]);
+                bulk_g2s(svals + (size_t)s * R, vals + row0, vb, &full[s]);
+                ++issued;
+            }
+            // never leave with a copy in flight
+            for (int i = max(0, issued - S); i < issued; ++i)
+                if (!mbar_wait_bounded(&full[i % S], (i / S) & 1, kWaitNs)) break;
+        }
+        return;
+    }
+
+    // -------------------------------------------------------------- consumers
+    const int ctid = tid;
+    const int copy = (ctid & 31) & (a.C - 1);
+    SAddr sa;
+    sa.K = smem_addr(sK);
+    sa.lo = smem_addr(tab.lo);
+    sa.hi = smem_addr(tab.hi);
+    bool bad_key = false;
+    bool first_flush = true;
+    long long rows_since_flush = 0;
+    int tcount = 0;  // tiles processed (counter buffer index)
+    for (int i = 0; i < ntile; ++i) {
+        const int s = i % S;
+        if (rows_since_flush + R > a.flush_rows) {
+            named_bar_sync(1, NC);
+            flush_partial<L>(a.partials + (size_t)blockIdx.x * G * (8 + 16 * L), G, tab, sK, sF, first_flush,
+                             ctid, NC);
+            first_flush = false;
+            rows_since_flush = 0;
+            named_bar_sync(1, NC);
+        }
+        const bool ok = mbar_wait_bounded(&full[s], (i / S) & 1, kWaitNs);
+        int* cnt = &ctl[2 * (tcount % 3)];
+        const int32_t* tk = skeys + (size_t)s * R;
+        const T* tv = svals + (size_t)s * R;
+        if (ok) {
+            sa.keys = smem_addr(tk);
+            sa.vals = smem_addr(tv);
+            for (int r = 4 * ctid; r < R; r += 4 * NC)
+                consume_quad<T, L>(sa, tk, tv, r, G, tab, copy, sK, sKp, sF, dlist, rlist, cnt, bad_key);
+        } else {
+            *abort_flag = 1;  // written before the barrier, read after it: uniform
+            atomicOr(a.errors, REPRO_ERR_TIMEOUT);
+        }
+        named_bar_sync(1, NC);
+        if (ctid == 0) {  // the counters of two tiles ago are no longer read
+            int* old = &ctl[2 * ((tcount + 2) % 3)];
+            old[0] = 0;
+            old[1] = 0;
+        }
+        if (*abort_flag) break;
+        const int nd = cnt[0], nr = cnt[1];
+        if (nr > 0) {
+            raise_and_add<T, L>(nr, nd, tk, tv, tab, sK, sKp, dlist, rlist, ctid, NC);
+            named_bar_sync(1, NC);
+        }
+        __syncwarp();
+        if ((ctid & 31) == 0) mbar_arrive(&empty[s]);
+        rows_since_flush += R;
+        ++tcount;
+    }
+
+    // ragged tail (n mod R rows), read straight from global memory by the last CTA
+    const long long tail0 = a.ntiles * (long long)R;
+    if (!*abort_flag && blockIdx.x == gridDim.x - 1 && tail0 < a.n) {
+        const int rows = (int)(a.n - tail0);
+        if (rows_since_flush + rows > a.flush_rows) {
+            named_bar_sync(1, NC);
+            flush_partial<L>(a.partials + (size_t)blockIdx.x * G * (8 + 16 * L), G, tab, sK, sF, first_flush,
+                             ctid, NC);
+            first_flush = false;
+            named_bar_sync(1, NC);
+        }
+        int* cnt = &ctl[2 * (tcount % 3)];
+        const int32_t* tk = a.keys + tail0;
+        const T* tv = vals + tail0;
+        for (int r = ctid; r < rows; r += NC)
+            consume_row<T, L>(tk[r], tv[r], r, G, tab, copy, sK, sKp, sF, dlist, rlist, cnt, bad_key);
+        named_bar_sync(1, NC);
+        const int nd = cnt[0], nr = cnt[1];
+        if (nr > 0) {
+            raise_and_add<T, L>(nr, nd, tk, tv, tab, sK, sKp, dlist, rlist, ctid, NC);
+        }
+    }
+    if (__any_sync(0xffffffffu, bad_key) && (ctid & 31) == 0) atomicOr(a.errors, REPRO_ERR_KEY);
+    named_bar_sync(1, NC);
+    if (*abort_flag) return;
+    flush_partial<L>(a.partials + (size_t)blockIdx.x * G * (8 + 16 * L), G, tab, sK, sF, first_flush, ctid, NC);
+}
+
+// state += sum of C partial tables (one record per group each), aligned to
+// the largest window.  Block = 32 groups x NW warps; warps split the partials.
+template <int L>
+__global__ void __launch_bounds__(256) k_merge_partials(const unsigned char* __restrict__ parts, int C, int G,
+                                                        unsigned char* base, int dtype) {
+    constexpr int NW = 8;
+    constexpr size_t rec = 8 + 16 * L;
+    StateView st{base, L, G};
+    __shared__ int s_ok;
+    __shared__ int sKw[NW][32];
+    __shared__ unsigned sFw[NW][32];
+    __shared__ long long sAcc[NW][32][L][2];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (threadIdx.x == 0) {
+        const repro_state_header* h = st.header();
+        s_ok = h->magic == REPRO_STATE_MAGIC && h->dtype == (uint32_t)dtype && h->L == (uint32_t)L &&
+               h->num_groups == G;
+        if (!s_ok) atomicOr(&st.header()->errors, REPRO_ERR_LAYOUT);
+    }
+    __syncthreads();
+    if (!s_ok) return;
+    const long long g = (long long)blockIdx.x * 32 + lane;
+    const bool valid = g < G;
+    int K = 0;
+    unsigned fl = 0;
+    if (valid)
+        for (int c = w; c < C; c += NW) {
+            const unsigned char* r = parts + ((size_t)c * G + g) * rec;
+            K = max(K, *reinterpret_cast<const int*>(r));
+            fl |= *reinterpret_cast<const unsigned*>(r + 4);
+        }
+    sKw[w][lane] = K;
+    sFw[w][lane] = fl;
+    __syncthreads();
+    int Kg = valid ? *st.K(g) : 0;
+#pragma unroll
+    for (int i = 0; i < NW; ++i) Kg = max(Kg, sKw[i][lane]);
+    __int128 acc[L];
+#pragma unroll
+    for (int j = 0; j < L; ++j) acc[j] = 0;
+    if (valid)
+        for (int c = w; c < C; c += NW) {
+            const unsigned char* r = parts + ((size_t)c * G + g) * rec;
+            const int d = Kg - *reinterpret_cast<const int*>(r);
+            const long long* b = reinterpret_cast<const long long*>(r + 8);
+#pragma unroll
+            for (int j = 0; j < L; ++j)
+                if (j - d >= 0) acc[j] += bin_read(&b[2 * (j - d)], &b[2 * (j - d) + 1]);
+        }
+#pragma unroll
+    for (int j = 0; j < L; ++j) {
+        sAcc[w][lane][j][0] = (long long)(unsigned long long)acc[j];
+        sAcc[w][lane][j][1] = (long long)(acc[j] >> 64);
+    }
+    __syncthreads();
+    if (w == 0 && valid) {
+        const int d = Kg - *st.K(g);
+        __int128 tot[L];
+#pragma unroll
+        for (int j = 0; j < L; ++j) {
+            tot[j] = (j - d >= 0) ? bin_read(st.lo(g, j - d), st.hi(g, j - d)) : 0;
+#pragma unroll
+            for (int i = 0; i < NW; ++i)
+                tot[j] += (((__int128)sAcc[i][lane][j][1]) << 64) + (__int128)(unsigned long long)sAcc[i][lane][j][0];
+        }
+        unsigned f = *st.flags(g);
+#pragma unroll
+        for (int i = 0; i < NW; ++i) f |= sFw[i][lane];
+#pragma unroll
+        for (int j = 0; j < L; ++j) bin_write(st.lo(g, j), st.hi(g, j), tot[j]);
+        *st.K(g) = Kg;
+        *st.flags(g) = f;
+    }
+}
+
+// ------------------------------------------------------------------ launcher
+
+namespace {
+
+struct FusedConfig {
+    int S, R, ncw, ctas_per_sm, copies;
+};
+
+template <typename T>
+bool pick_config(int G, int L, const DeviceInfo& di, FusedConfig& cfg) {
+    static FusedConfig forced{0, 0, 0, 0, 0};
+    static bool env_read = false;
+    if (!env_read) {  // tuning aid: REPRO_FUSED_CFG="S,R,ncw,ctas_per_sm[,copies]"
+        const char* e = getenv("REPRO_FUSED_CFG");
+        if (e) {
+            forced.copies = 0;
+            sscanf(e, "%d,%d,%d,%d,%d", &forced.S, &forced.R, &forced.ncw, &forced.ctas_per_sm, &forced.copies);
+        }
+        env_read = true;
+    }
+    // Prefer two CTAs per SM (barrier bubbles of one hide behind the other),
+    // then one CTA with deeper staging; lane-private table copies when the
+    // 32 copies fit next to the stages.
+    const FusedConfig cands[] = {{3, 2048, 8, 2, 0}, {4, 1024, 8, 2, 0}, {2, 2048, 8, 2, 0}, {4, 2048, 16, 1, 0},
+                                 {3, 2048, 16, 1, 0}, {2, 2048, 16, 1, 0}, {2, 1024, 16, 1, 0}};
+    auto fits = [&](FusedConfig c) {
+        if (c.S < 2 || c.R < 256 || c.R % (128 * c.ncw) || (c.ncw != 8 && c.ncw != 16) || c.ctas_per_sm < 1)
+            return false;
+        if (c.copies != 1 && c.copies != 32) return false;
+        const size_t bytes = fused_layout<T>(c.S, c.R, G, L, c.copies).total;
+        return bytes * c.ctas_per_sm + 1024 * c.ctas_per_sm <= di.smem_per_sm && bytes <= di.smem_optin;
+    };
+    if (forced.S) {
+        FusedConfig c = forced;
+        if (c.copies == 0) c.copies = 1;
+        if (fits(c)) {
+            cfg = c;
+            return true;
+        }
+    }
+    for (int copies : {32, 1}) {
+        if (copies == 32 && G > 256) continue;
+        for (FusedConfig c : cands) {
+            c.copies = copies;
+            if (fits(c)) {
+                cfg = c;
+                return true;
+            }
+        }
+    }
+    return false;
+}
+
+long long env_flush_rows() {
+    static long long v = -2;
+    if (v == -2) {
+        const char* e = getenv("REPRO_FLUSH_ROWS");
+        v = e ? atoll(e) : -1;
+    }
+    return v;
+}
+
+template <typename T, int L, int NCW>
+cudaError_t launch_fused_t(const FusedArgs& a0, int ctas, size_t smem, cudaStream_t s) {
+    auto kern = k_fused<T, L, NCW>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    prof_begin(PROF_FUSED, s);
+    kern<<<ctas, 32 * (NCW + 1), smem, s>>>(a0);
+    prof_end(PROF_FUSED, s);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+template <typename T, int L>
+cudaError_t dispatch_ncw(int ncw, const FusedArgs& a, int ctas, size_t smem, cudaStream_t s) {
+    if (ncw == 8) return launch_fused_t<T, L, 8>(a, ctas, smem, s);
+    return launch_fused_t<T, L, 16>(a, ctas, smem, s);
+}
+
+template <typename T>
+cudaError_t dispatch_L(int L, int ncw, const FusedArgs& a, int ctas, size_t smem, cudaStream_t s) {
+    switch (L) {
+        case 1: return dispatch_ncw<T, 1>(ncw, a, ctas, smem, s);
+        case 2: return dispatch_ncw<T, 2>(ncw, a, ctas, smem, s);
+        case 3: return dispatch_ncw<T, 3>(ncw, a, ctas, smem, s);
+        default: return dispatch_ncw<T, 4>(ncw, a, ctas, smem, s);
+    }
+}
+
+}  // namespace
+
+bool fused_supported(int dtype, int L, long long G, const void* keys, const void* vals) {
+    if (G > 65535) return false;
+    if ((uintptr_t)keys % 16 || (uintptr_t)vals % 16) return false;
+    FusedConfig cfg;
+    return dtype == REPRO_F64 ? pick_config<double>((int)G, L, device_info(), cfg)
+                              : pick_config<float>((int)G, L, device_info(), cfg);
+}
+
+static int fused_ctas(long long ntiles, const FusedConfig& cfg, const DeviceInfo& di) {
+    // at least ~16 tiles per CTA keeps the partial tables small next to the input
+    long long c = (long long)di.sms * cfg.ctas_per_sm;
+    const long long by_work = (ntiles + 15) / 16;
+    if (by_work < c) c = by_work;
+    if (c < 1) c = 1;
+    return (int)c;
+}
+
+size_t fused_scratch_bytes(int dtype, int L, long long G, long long n) {
+    FusedConfig cfg;
+    const DeviceInfo& di = device_info();
+    const bool ok = dtype == REPRO_F64 ? pick_config<double>((int)G, L, di, cfg) : pick_config<float>((int)G, L, di, cfg);
+    if (!ok) return 0;
+    const long long ntiles = n / cfg.R;
+    return (size_t)fused_ctas(ntiles, cfg, di) * (size_t)G * (8 + 16 * (size_t)L);
+}
+
+cudaError_t launch_groupby_fused(const int32_t* keys, const void* vals, long long n, int dtype, int L, long long G,
+                                 void* state, void* scratch, cudaStream_t s) {
+    const DeviceInfo& di = device_info();
+    FusedConfig cfg;
+    const bool ok = dtype == REPRO_F64 ? pick_config<double>((int)G, L, di, cfg) : pick_config<float>((int)G, L, di, cfg);
+    if (!ok) return cudaErrorInvalidValue;
+    FusedArgs a;
+    a.keys = keys;
+    a.vals = vals;
+    a.n = n;
+    a.G = (int)G;
+    a.R = cfg.R;
+    a.S = cfg.S;
+    a.C = cfg.copies;
+    a.ntiles = n / cfg.R;
+    const int ctas = fused_ctas(a.ntiles, cfg, di);
+    a.tiles_per_cta = (int)((a.ntiles + ctas - 1) / ctas);
+    const long long fr = env_flush_rows();
+    a.flush_rows = fr > 0 ? fr : (1ll << 23);
+    a.partials = (unsigned char*)scratch;
+    a.errors = &reinterpret_cast<repro_state_header*>(state)->errors;
+    const size_t smem = dtype == REPRO_F64 ? fused_layout<double>(cfg.S, cfg.R, (int)G, L, cfg.copies).total
+                                           : fused_layout<float>(cfg.S, cfg.R, (int)G, L, cfg.copies).total;
+    cudaError_t e = dtype == REPRO_F64 ? dispatch_L<double>(L, cfg.ncw, a, ctas, smem, s)
+                                       : dispatch_L<float>(L, cfg.ncw, a, ctas, smem, s);
+    if (e != cudaSuccess) return e;
+    const int blocks = (int)((G + 31) / 32);
+    prof_begin(PROF_MERGE, s);
+    switch (L) {
+        case 1: k_merge_partials<1><<<blocks, 256, 0, s>>>(a.partials, ctas, (int)G, (unsigned char*)state, dtype); break;
+        case 2: k_merge_partials<2><<<blocks, 256, 0, s>>>(a.partials, ctas, (int)G, (unsigned char*)state, dtype); break;
+        case 3: k_merge_partials<3><<<blocks, 256, 0, s>>>(a.partials, ctas, (int)G, (unsigned char*)state, dtype); break;
+        default: k_merge_partials<4><<<blocks, 256, 0, s>>>(a.partials, ctas, (int)G, (unsigned char*)state, dtype); break;
+    }
+    prof_end(PROF_MERGE, s);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+}  // namespace rp

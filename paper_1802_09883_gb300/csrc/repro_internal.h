@@ -13,6 +13,7 @@ struct DeviceInfo {
     int device;
     int sms;            // multiprocessors
     size_t smem_optin;  // opt-in shared memory per block, bytes
+    size_t smem_per_sm; // shared memory per multiprocessor, bytes
 };
 
 // Properties of the current device (queried once per device).
@@ -31,6 +32,12 @@ cudaError_t launch_init_state(void* state, int dtype, int L, long long G, cudaSt
 size_t two_pass_scratch_bytes(long long G);
 cudaError_t launch_groupby_two_pass(const int32_t* keys, const void* vals, long long n, int dtype, int L,
                                     long long G, void* state, void* scratch, cudaStream_t s);
+
+// Single-pass fused path (shared-memory group tables, TMA-staged tiles).
+bool fused_supported(int dtype, int L, long long G, const void* keys, const void* vals);
+size_t fused_scratch_bytes(int dtype, int L, long long G, long long n);
+cudaError_t launch_groupby_fused(const int32_t* keys, const void* vals, long long n, int dtype, int L, long long G,
+                                 void* state, void* scratch, cudaStream_t s);
 
 cudaError_t launch_merge(void* dst, const void* src, int dtype, int L, long long G, cudaStream_t s);
 cudaError_t launch_finalize(const void* state, int dtype, int L, long long G, void* out, cudaStream_t s);

@@ -230,3 +230,77 @@ def test_fp32_baseline_runs():
     absum = np.bincount(_np(w.keys), weights=np.abs(_np(w.values)).astype(np.float64), minlength=w.G)
     cnt = np.bincount(_np(w.keys), minlength=w.G)
     assert np.all(np.abs(out - ref) <= cnt * 2.0 ** -24 * absum + 1e-30)
+
+
+# ----------------------------------------------------- single-pass fused path
+
+def test_raise_heavy_input_sorted_by_magnitude():
+    """Rows sorted by |value|: nearly every tile raises some group's window
+    (the deferred-row path of the single-pass kernel)."""
+    g = torch.Generator(device=DEV)
+    g.manual_seed(21)
+    n, G, L = 400_000, 200, 3
+    keys = WL.uniform_keys(n, G, g, DEV)
+    vals = WL.random_values(n, -300, 300, g, DEV)
+    order = torch.argsort(vals.abs())
+    vals = vals[order].contiguous()
+    st, out = run_gpu(keys, vals, G, L)
+    ost, _ = oracle_state(_np(keys), _np(vals), G, L)
+    assert_state_equal(st, ost)
+    assert_bits_equal(_np(out), O.finalize(ost))
+
+
+@pytest.mark.parametrize("n", [1, 100, 2047, 2048, 2049, 6000])
+def test_small_and_ragged_row_counts(n):
+    w = WL.plain(n=n, G=64, L=4, seed=n, device=DEV, e_lo=-50, e_hi=50)
+    st, out = run_gpu(w.keys, w.values, w.G, w.L)
+    ost, _ = oracle_state(_np(w.keys), _np(w.values), w.G, w.L, threads=1)
+    assert_state_equal(st, ost)
+    assert_bits_equal(_np(out), O.finalize(ost))
+
+
+def test_unaligned_inputs_take_the_two_pass_path():
+    w = WL.plain(n=50_001, G=300, L=3, seed=9, device=DEV)
+    k, v = w.keys[1:], w.values[1:]  # 4- and 8-byte aligned, not 16
+    st, out = run_gpu(k, v, w.G, w.L)
+    ost, _ = oracle_state(_np(k), _np(v), w.G, w.L)
+    assert_state_equal(st, ost)
+    assert_bits_equal(_np(out), O.finalize(ost))
+
+
+_SUB = r"""
+import sys, numpy as np, torch
+sys.path.insert(0, {root!r})
+import paper_1802_09883_gb300 as R
+from paper_1802_09883_gb300 import workloads as WL
+from oracle import oracle as O
+for G, L, dtype in ((16, 2, torch.float64), (1024, 3, torch.float64), (777, 4, torch.float32), (3000, 3, torch.float64)):
+    w = WL.plain(n=300_001, G=G, L=L, seed=G + L, device="cuda", e_lo=-45, e_hi=45, dtype=dtype)
+    st = R.State(G, L, dtype)
+    st.add(w.keys, w.values)
+    out = st.finalize().cpu().numpy()
+    st.check()
+    ref = O.init(np.float64 if dtype == torch.float64 else np.float32, L, G)
+    O.groupby_sum(ref, w.keys.cpu().numpy(), w.values.cpu().numpy(), threads=4)
+    K, fl, lo, hi = st.host_view()
+    oK, ofl, olo, ohi = O.to_bins(ref)
+    assert (K == oK).all() and (fl == ofl).all() and (lo == olo).all() and (hi == ohi).all(), (G, L)
+    iv = np.int64 if out.dtype == np.float64 else np.int32
+    assert (out.view(iv) == O.finalize(ref).view(iv)).all(), (G, L)
+print("ok")
+"""
+
+
+@pytest.mark.parametrize("env", [{"REPRO_FLUSH_ROWS": "4096"}, {"REPRO_FUSED_CFG": "2,1024,16,1"},
+                                 {"REPRO_FUSED_CFG": "4,1024,8,2"}, {"REPRO_FUSED_CFG": "3,2048,16,1"},
+                                 {"REPRO_FUSED_CFG": "3,1024,8,2,32"}])
+def test_fused_variants_in_subprocess(env):
+    """Mid-kernel flushes of the int64 table into the 128-bit partial, and
+    other tile / stage / warp configurations, give the same bits."""
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    r = subprocess.run([sys.executable, "-c", _SUB.format(root=root)], env={**os.environ, **env},
+                       capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0 and "ok" in r.stdout, r.stdout + r.stderr
