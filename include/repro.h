@@ -128,6 +128,31 @@ repro_status repro_groupby_sum(const int32_t* keys, const void* values, int64_t 
                                repro_dtype dtype, int L, int64_t num_groups, void* state,
                                void* stream);
 
+/*
+ * repro_groupby_sum without any allocation.  The paper has no counterpart:
+ * this is a deployment variant of repro_groupby_sum for callers that cannot
+ * allocate device memory while they aggregate -- a host whose buffer
+ * manager has reserved the GPU's memory up front, a process whose allocator
+ * belongs to another runtime, or a request path that must not wait on, or
+ * fail in, an allocation.  Same arguments, same result bits as
+ * repro_groupby_sum.
+ *
+ * It runs the single-pass shared-memory path only, with its per-CTA partial
+ * tables in a fixed 16 MiB device array inside the library (held by every
+ * GPU that loads the library until the process exits), using fewer CTAs
+ * when needed so that they fit.  Limits: keys and values 16-byte aligned,
+ * and a group table that fits the single-pass path (num_groups up to a few
+ * thousand, depending on L and dtype) with num_groups * (8 + 16 L) <= 16 MiB;
+ * otherwise REPRO_ERANGE and nothing is enqueued.  The first call on a device
+ * looks the array's address up with cudaGetSymbolAddress, so make it before
+ * any stream capture.  Every call uses the same array: calls that overlap
+ * on the GPU race (serialise them on one stream).  Nothing needs clearing
+ * between calls.
+ */
+repro_status repro_groupby_sum_noalloc(const int32_t* keys, const void* values, int64_t n,
+                                       repro_dtype dtype, int L, int64_t num_groups, void* state,
+                                       void* stream);
+
 /* dst += src, group by group (operator+=(repro), Sec. V-B; eq. (2)/(3) for
    equal windows): both are aligned to the larger window, levels that fall
    below it are dropped, bins are added exactly and flags OR-ed.  Exact, so

@@ -70,6 +70,7 @@ def lib(build_if_stale: bool = True):
         L.repro_state_bytes.restype = ctypes.c_size_t
         L.repro_state_init.argtypes = [vp, i32, i32, i64, vp]
         L.repro_groupby_sum.argtypes = [vp, vp, i64, i32, i32, i64, vp, vp]
+        L.repro_groupby_sum_noalloc.argtypes = [vp, vp, i64, i32, i32, i64, vp, vp]
         L.repro_merge.argtypes = [vp, vp, i32, i32, i64, vp]
         L.repro_finalize.argtypes = [vp, i32, i32, i64, vp, vp]
         L.repro_state_check.argtypes = [vp, u32p, vp]
@@ -78,7 +79,8 @@ def lib(build_if_stale: bool = True):
         L.repro_strerror.argtypes = [i32]
         L.repro_strerror.restype = ctypes.c_char_p
         L.repro_version.restype = i32
-        for name in ("repro_state_init", "repro_groupby_sum", "repro_merge", "repro_finalize",
+        for name in ("repro_state_init", "repro_groupby_sum", "repro_groupby_sum_noalloc", "repro_merge",
+                     "repro_finalize",
                      "repro_state_check", "groupby_sum_fp64", "groupby_sum_fp32"):
             getattr(L, name).restype = i32
         _lib = L

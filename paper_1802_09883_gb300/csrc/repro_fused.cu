@@ -20,6 +20,7 @@
 #include <cstdint>
 #include <cstdio>
 #include <cstdlib>
+#include <mutex>
 
 #include "ptx.cuh"
 #include "repro_device.cuh"
@@ -666,7 +667,7 @@ size_t fused_scratch_bytes(int dtype, int L, long long G, long long n) {
 }
 
 cudaError_t launch_groupby_fused(const int32_t* keys, const void* vals, long long n, int dtype, int L, long long G,
-                                 void* state, void* scratch, cudaStream_t s) {
+                                 void* state, void* scratch, cudaStream_t s, int max_ctas) {
     const DeviceInfo& di = device_info();
     FusedConfig cfg;
     const bool ok = dtype == REPRO_F64 ? pick_config<double>((int)G, L, di, cfg) : pick_config<float>((int)G, L, di, cfg);
@@ -680,7 +681,8 @@ cudaError_t launch_groupby_fused(const int32_t* keys, const void* vals, long lon
     a.S = cfg.S;
     a.C = cfg.copies;
     a.ntiles = n / cfg.R;
-    const int ctas = fused_ctas(a.ntiles, cfg, di);
+    int ctas = fused_ctas(a.ntiles, cfg, di);
+    if (max_ctas > 0 && ctas > max_ctas) ctas = max_ctas;
     a.tiles_per_cta = (int)((a.ntiles + ctas - 1) / ctas);
     const long long fr = env_flush_rows();
     a.flush_rows = fr > 0 ? fr : (1ll << 23);
@@ -705,3 +707,70 @@ cudaError_t launch_groupby_fused(const int32_t* keys, const void* vals, long lon
 }
 
 }  // namespace rp
+
+// ------------------------------------------- entry point without allocation
+//
+// Some callers cannot allocate device memory while they aggregate: a host
+// that has reserved all of the GPU's memory for its own buffer manager, a
+// process whose allocator is owned by another runtime, or a latency-bound
+// request path that must never wait on (or fail in) an allocation.  For
+// them repro_groupby_sum_noalloc runs the single-pass fused path with its
+// per-CTA partial tables in the fixed array below instead of pool memory.
+// The array belongs to the library: every GPU that loads it keeps these
+// bytes until the process exits.  Calls share it, so calls that overlap on
+// the GPU (different streams, or the same array used from two threads)
+// race; each call fully rewrites the part it reads, so nothing needs
+// clearing between calls.
+
+namespace rp {
+
+constexpr size_t kStaticPartialBytes = 16u << 20;  // 16 MiB
+static __device__ __align__(256) unsigned char g_static_partials[kStaticPartialBytes];
+
+// Host-side device address of g_static_partials, looked up once per device
+// (with that device current) -- the symbol itself is only a host stand-in.
+static void* static_partials_address(cudaError_t& err) {
+    static void* addr[64] = {};
+    static std::mutex mu;
+    int dev = 0;
+    err = cudaGetDevice(&dev);
+    if (err != cudaSuccess) return nullptr;
+    if (dev < 0 || dev >= 64) {
+        err = cudaErrorInvalidDevice;
+        return nullptr;
+    }
+    std::lock_guard<std::mutex> lock(mu);
+    if (!addr[dev]) {
+        void* p = nullptr;
+        err = cudaGetSymbolAddress(&p, g_static_partials);
+        if (err != cudaSuccess) return nullptr;
+        addr[dev] = p;
+    }
+    err = cudaSuccess;
+    return addr[dev];
+}
+
+}  // namespace rp
+
+extern "C" repro_status repro_groupby_sum_noalloc(const int32_t* keys, const void* values, int64_t n,
+                                                  repro_dtype dtype, int L, int64_t num_groups, void* state,
+                                                  void* stream) {
+    using namespace rp;
+    if (!state || (dtype != REPRO_F64 && dtype != REPRO_F32) || L < 1 || L > 4 || num_groups < 1 ||
+        num_groups > INT32_MAX || n < 0)
+        return REPRO_EINVAL;
+    if (n > 0 && (!keys || !values)) return REPRO_EINVAL;
+    if ((uintptr_t)state % 16) return REPRO_EINVAL;
+    if (n == 0) return REPRO_OK;
+    // only the fused path runs here: aligned inputs and a table that fits
+    if (!fused_supported(dtype, L, num_groups, keys, values)) return REPRO_ERANGE;
+    const size_t per_cta = (size_t)num_groups * (8 + 16 * (size_t)L);
+    const long long max_ctas = (long long)(kStaticPartialBytes / per_cta);
+    if (max_ctas < 1) return REPRO_ERANGE;
+    cudaError_t e;
+    void* scratch = static_partials_address(e);
+    if (!scratch) return REPRO_ECUDA;
+    e = launch_groupby_fused(keys, values, n, dtype, L, num_groups, state, scratch, (cudaStream_t)stream,
+                             (int)(max_ctas < 65535 ? max_ctas : 65535));
+    return e == cudaSuccess ? REPRO_OK : REPRO_ECUDA;
+}

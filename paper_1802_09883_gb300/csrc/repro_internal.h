@@ -36,8 +36,9 @@ cudaError_t launch_groupby_two_pass(const int32_t* keys, const void* vals, long 
 // Single-pass fused path (shared-memory group tables, TMA-staged tiles).
 bool fused_supported(int dtype, int L, long long G, const void* keys, const void* vals);
 size_t fused_scratch_bytes(int dtype, int L, long long G, long long n);
+// max_ctas > 0 caps the number of CTAs (and so the partial tables in scratch).
 cudaError_t launch_groupby_fused(const int32_t* keys, const void* vals, long long n, int dtype, int L, long long G,
-                                 void* state, void* scratch, cudaStream_t s);
+                                 void* state, void* scratch, cudaStream_t s, int max_ctas = 0);
 
 cudaError_t launch_merge(void* dst, const void* src, int dtype, int L, long long G, cudaStream_t s);
 cudaError_t launch_finalize(const void* state, int dtype, int L, long long G, void* out, cudaStream_t s);
