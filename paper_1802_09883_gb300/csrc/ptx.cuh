@@ -89,14 +89,15 @@ __device__ __forceinline__ uint32_t lds_u32(uint32_t a) {
 }
 
 // Shared-memory atomic add, executed only when `pred` holds (a predicated
-// instruction, not a branch); returns the previous value, or 0 if skipped.
+// instruction, not a branch); returns the previous value, which is
+// unspecified when the add is skipped.
 __device__ __forceinline__ unsigned atom_add_if(bool pred, uint32_t addr, unsigned v) {
-    unsigned old = 0;
+    unsigned old;
     asm volatile(
         "{\n\t.reg .pred q;\n\t"
         "setp.ne.u32 q, %3, 0;\n\t"
         "@q atom.shared.add.u32 %0, [%1], %2;\n\t}"
-        : "+r"(old)
+        : "=r"(old)
         : "r"(addr), "r"(v), "r"((unsigned)pred)
         : "memory");
     return old;

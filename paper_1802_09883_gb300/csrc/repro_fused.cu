@@ -221,7 +221,9 @@ __device__ __forceinline__ void consume_quad(const SAddr& sa, const int32_t* tk,
                               rlist, cnt, bad_key);
         return;
     }
-    // common case, straight-line: four rows' digits, then predicated atomics
+    // common case, straight-line: four rows' digits, then predicated atomics.
+    // Top and middle digits are almost never zero (adding zero is harmless);
+    // the low digit is zero whenever the value starts above its boundary.
     unsigned lo[12];
     int hi[12];
     uint32_t at[12];
@@ -230,11 +232,11 @@ __device__ __forceinline__ void consume_quad(const SAddr& sa, const int32_t* tk,
     for (int q = 0; q < 4; ++q) {
         Lean<T>::digits(vhi[q], vlo[q], kb[q], &lo[3 * q], &hi[3 * q]);
         const int j = K[q] - kb[q];  // window level of the value's top digit
-        const uint32_t row = (uint32_t)gq[q] * (uint32_t)(L * t.C) + (uint32_t)copy;
+        const uint32_t row = 4u * ((uint32_t)gq[q] * (uint32_t)(L * t.C) + (uint32_t)copy);
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
-            on[3 * q + k] = (j + k < L) && ((lo[3 * q + k] | (unsigned)hi[3 * q + k]) != 0u);
-            at[3 * q + k] = 4u * (row + (uint32_t)(min(j + k, L - 1) * t.C));
+            on[3 * q + k] = (j + k < L) && (k < 2 || (lo[3 * q + k] | (unsigned)hi[3 * q + k]) != 0u);
+            at[3 * q + k] = row + 4u * (uint32_t)(min(j + k, L - 1) * t.C);
         }
     }
     unsigned old[12];
@@ -571,8 +573,8 @@ bool pick_config(int G, int L, const DeviceInfo& di, FusedConfig& cfg) {
     // Prefer two CTAs per SM (barrier bubbles of one hide behind the other),
     // then one CTA with deeper staging; lane-private table copies when the
     // 32 copies fit next to the stages.
-    const FusedConfig cands[] = {{3, 2048, 8, 2, 0}, {4, 1024, 8, 2, 0}, {2, 2048, 8, 2, 0}, {4, 2048, 16, 1, 0},
-                                 {3, 2048, 16, 1, 0}, {2, 2048, 16, 1, 0}, {2, 1024, 16, 1, 0}};
+    const FusedConfig cands[] = {{3, 2048, 8, 2, 0}, {2, 2048, 8, 2, 0}, {3, 4096, 16, 1, 0}, {4, 1024, 8, 2, 0},
+                                 {4, 2048, 16, 1, 0}, {3, 2048, 16, 1, 0}, {2, 2048, 16, 1, 0}, {2, 1024, 16, 1, 0}};
     auto fits = [&](FusedConfig c) {
         if (c.S < 2 || c.R < 256 || c.R % (128 * c.ncw) || (c.ncw != 8 && c.ncw != 16) || c.ctas_per_sm < 1)
             return false;
