@@ -153,6 +153,44 @@ repro_status repro_groupby_sum_noalloc(const int32_t* keys, const void* values, 
                                        repro_dtype dtype, int L, int64_t num_groups, void* state,
                                        void* stream);
 
+/*
+ * Batched grouped SUM: many independent aggregations (each with its own
+ * keys, values, group count and state) in one persistent launch.  Same
+ * result bits per task as repro_groupby_sum on that task alone.
+ *
+ * repro_batch_prepare builds a plan on the host (it allocates device memory
+ * with cudaMalloc and copies the task list and the work items to it; not
+ * capturable).  repro_batch_run enqueues the plan's kernels on `stream`
+ * without host copies or allocations, so it may be captured in a CUDA graph
+ * and replayed; every run adds the tasks' rows into their states again.
+ * repro_batch_destroy frees the plan (it synchronises the device).
+ * repro_groupby_sum_batched = prepare + run + stream synchronise + destroy.
+ *
+ * Tasks whose rows are 16-byte aligned and whose group table fits the
+ * single-pass path share the persistent launch: the plan cuts them into
+ * work items of whole tiles (the item size is tuned to the batch: about four
+ * items per CTA, at most 2^23 rows), largest first; an item that covers a
+ * whole task merges straight into its state.  Other tasks run through the
+ * two-pass path, one after the other, inside repro_batch_run.
+ * All tasks use the same dtype and L; states must not overlap.
+ */
+typedef struct {
+    const int32_t* keys;   /* device, int32[n] */
+    const void* values;    /* device, double[n] or float[n] */
+    int64_t n;             /* rows, >= 0 */
+    int64_t num_groups;    /* 1 .. 2^31 - 1 */
+    void* state;           /* device state (repro_state_init with the batch's dtype and L) */
+} repro_task;
+
+typedef struct repro_batch_plan_s* repro_batch_plan;
+
+repro_status repro_batch_prepare(const repro_task* tasks, int ntasks, repro_dtype dtype, int L,
+                                 repro_batch_plan* plan);
+repro_status repro_batch_run(repro_batch_plan plan, void* stream);
+repro_status repro_batch_destroy(repro_batch_plan plan);
+repro_status repro_groupby_sum_batched(const repro_task* tasks, int ntasks, repro_dtype dtype, int L,
+                                       void* stream);
+
 /* dst += src, group by group (operator+=(repro), Sec. V-B; eq. (2)/(3) for
    equal windows): both are aligned to the larger window, levels that fall
    below it are dropped, bins are added exactly and flags OR-ed.  Exact, so

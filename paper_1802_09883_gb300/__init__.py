@@ -76,11 +76,16 @@ def lib(build_if_stale: bool = True):
         L.repro_state_check.argtypes = [vp, u32p, vp]
         L.groupby_sum_fp64.argtypes = [vp, vp, i64, i64, vp, vp]
         L.groupby_sum_fp32.argtypes = [vp, vp, i64, i64, vp, vp]
+        L.repro_batch_prepare.argtypes = [vp, i32, i32, i32, ctypes.POINTER(vp)]
+        L.repro_batch_run.argtypes = [vp, vp]
+        L.repro_batch_destroy.argtypes = [vp]
+        L.repro_groupby_sum_batched.argtypes = [vp, i32, i32, i32, vp]
         L.repro_strerror.argtypes = [i32]
         L.repro_strerror.restype = ctypes.c_char_p
         L.repro_version.restype = i32
         for name in ("repro_state_init", "repro_groupby_sum", "repro_groupby_sum_noalloc", "repro_merge",
-                     "repro_finalize",
+                     "repro_finalize", "repro_batch_prepare", "repro_batch_run", "repro_batch_destroy",
+                     "repro_groupby_sum_batched",
                      "repro_state_check", "groupby_sum_fp64", "groupby_sum_fp32"):
             getattr(L, name).restype = i32
         _lib = L
@@ -232,3 +237,64 @@ def groupby_sum_fp32(keys: torch.Tensor, values: torch.Tensor, num_groups: int,
     _check(lib().groupby_sum_fp32(keys.data_ptr(), values.data_ptr(), keys.numel(), num_groups, out.data_ptr(),
                                   _stream(values.device)), "groupby_sum_fp32")
     return out
+
+
+class _Task(ctypes.Structure):
+    _fields_ = [("keys", ctypes.c_void_p), ("values", ctypes.c_void_p), ("n", ctypes.c_int64),
+                ("num_groups", ctypes.c_int64), ("state", ctypes.c_void_p)]
+
+
+class BatchPlan:
+    """Many independent grouped SUMs in one persistent launch.
+
+    tasks: list of (keys, values, State); all States share dtype and L.
+    run() enqueues the plan's kernels on the current stream (capturable in a
+    CUDA graph); every run adds the tasks' rows into their states again.
+    """
+
+    def __init__(self, tasks):
+        if not tasks:
+            raise ValueError("no tasks")
+        st0 = tasks[0][2]
+        self.dtype, self.L, self.code = st0.dtype, st0.L, st0.code
+        self._keep = []
+        arr = (_Task * len(tasks))()
+        for i, (k, v, st) in enumerate(tasks):
+            _require_cuda(k, "keys")
+            _require_cuda(v, "values")
+            if (st.dtype, st.L) != (self.dtype, self.L):
+                raise ValueError("all tasks must share dtype and L")
+            if k.dtype != torch.int32 or v.dtype != self.dtype or k.numel() != v.numel():
+                raise ValueError("task %d: keys int32 and values of the batch dtype, same length" % i)
+            k, v = k.contiguous(), v.contiguous()
+            self._keep.append((k, v, st))
+            arr[i] = _Task(k.data_ptr(), v.data_ptr(), k.numel(), st.G, st.tensor.data_ptr())
+        self._plan = ctypes.c_void_p()
+        _check(lib().repro_batch_prepare(ctypes.cast(arr, ctypes.c_void_p), len(tasks), self.code, self.L,
+                                         ctypes.byref(self._plan)), "repro_batch_prepare")
+        self.device = st0.device
+
+    def run(self):
+        _check(lib().repro_batch_run(self._plan, _stream(self.device)), "repro_batch_run")
+        return self
+
+    def close(self):
+        if self._plan:
+            lib().repro_batch_destroy(self._plan)
+            self._plan = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def groupby_sum_batched(tasks, L: int = 3):
+    """tasks: list of (keys, values, num_groups); returns one State per task."""
+    states = [State(G, L, v.dtype, device=v.device) for _, v, G in tasks]
+    plan = BatchPlan([(k, v, st) for (k, v, _), st in zip(tasks, states)])
+    plan.run()
+    torch.cuda.current_stream(plan.device).synchronize()
+    plan.close()
+    return states

@@ -1,0 +1,633 @@
+// repro_batch.cu -- many independent reproducible grouped SUMs in one
+// persistent launch.
+//
+// A plan (built once on the host, repro_batch_prepare) cuts every task into
+// work items of whole tiles; the persistent CTAs of k_fused_multi pull items
+// from a device counter, stream their tiles through the same TMA-staged
+// shared-memory pipeline as the single-pass kernel, and at the end of each
+// item either merge the CTA table straight into the task's state (the item
+// owns the whole task) or write it as a partial that k_merge_items folds in
+// afterwards (operator+=(repro), Algorithm 4's merge).  Tasks the single-pass
+// table cannot hold (large G) or whose rows are not 16-byte aligned run
+// through the two-pass path.  repro_batch_run only launches kernels and
+// copies nothing from the host, so it can be captured in a CUDA graph.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdint>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <vector>
+
+#include "fused_device.cuh"
+#include "repro.h"
+#include "repro_internal.h"
+
+namespace rp {
+
+namespace {
+
+struct MTask {
+    const int32_t* keys;
+    const void* vals;
+    long long n;
+    int G;
+    int pad;
+    unsigned char* hdr;   // the task's state (header + records)
+};
+
+struct MItem {
+    int task;
+    int excl;             // 1: the item covers the whole task -> merge into its state
+    long long row0, row1; // rows [row0, row1) of the task; row0 is a multiple of R
+    long long part;       // first record of this item's partial table (excl == 0)
+};
+
+struct MergeBlk {
+    int task;
+    int g0;               // first group of this block (32 groups per block)
+    int nparts;           // partial tables of the task
+    int pad;
+    long long part;       // first record of the task's first partial table
+};
+
+struct StageMeta {
+    int item;             // -1: no more work
+    int rows;             // rows of this tile
+    int rows_tma;         // rows delivered by TMA (a multiple of 4), the rest read from global
+    int last;             // last tile of the item
+    long long row0;       // first row of the tile within the task
+};
+
+struct MultiArgs {
+    const MTask* tasks;
+    const MItem* items;
+    int nitems;
+    int* counter;
+    int R, S, C, Gcap;
+    unsigned char* partials;
+};
+
+__host__ __device__ constexpr size_t rec_bytes(int L) { return 8 + 16 * (size_t)L; }
+
+__device__ __forceinline__ bool task_header_ok(const unsigned char* hdr, int dtype, int L, int G) {
+    const repro_state_header* h = reinterpret_cast<const repro_state_header*>(hdr);
+    return h->magic == REPRO_STATE_MAGIC && h->dtype == (uint32_t)dtype && h->L == (uint32_t)L &&
+           h->num_groups == G;
+}
+
+// Deferred rows after a raise; rows at or beyond rows_tma come from global memory.
+template <typename T, int L>
+__device__ __forceinline__ void raise_and_add_multi(int nr, int nd, const int32_t* tk, const T* tv,
+                                                    const int32_t* gk, const T* gv, int rows_tma, const Table& t,
+                                                    int* sK, const int* sKp, const unsigned short* dlist,
+                                                    const int* rlist, int ctid, int NC) {
+    for (int i = ctid; i < nr * t.C; i += NC) {
+        const int g = rlist[i / t.C];
+        const int copy = i % t.C;
+        const int d = sKp[g] - sK[g];
+#pragma unroll
+        for (int j = L - 1; j >= 0; --j) {
+            const size_t dst = t.at(g, j, copy);
+            if (j - d >= 0) {
+                const size_t src = t.at(g, j - d, copy);
+                t.lo[dst] = t.lo[src];
+                t.hi[dst] = t.hi[src];
+            } else {
+                t.lo[dst] = 0;
+                t.hi[dst] = 0;
+            }
+        }
+    }
+    named_bar_sync(1, NC);
+    for (int i = ctid; i < nr; i += NC) sK[rlist[i]] = sKp[rlist[i]];
+    named_bar_sync(1, NC);
+    for (int i = ctid; i < nd; i += NC) {
+        const int r = dlist[i];
+        const int g = r < rows_tma ? tk[r] : gk[r];
+        const Split s = split_value(r < rows_tma ? tv[r] : gv[r]);
+        add_row<T, L>(s, sK[g], t, g, (ctid & 31) & (t.C - 1));
+    }
+}
+
+// Fold the CTA table into a record array (a partial table, or the task's
+// state when the item owns the task): records are aligned to the larger
+// window and their low levels dropped (operator+=(repro)); with `overwrite`
+// the old content is ignored.  Clears the table for the next item.
+template <int L>
+__device__ void flush_table(unsigned char* recs, int G, const Table& t, int* sK, int* sKp, unsigned* sF,
+                            bool overwrite, int ctid, int NC) {
+    constexpr size_t rec = 8 + 16 * L;
+    for (int g = ctid; g < G; g += NC) {
+        unsigned char* r = recs + (size_t)g * rec;
+        int* pK = reinterpret_cast<int*>(r);
+        unsigned* pF = reinterpret_cast<unsigned*>(r + 4);
+        long long* pb = reinterpret_cast<long long*>(r + 8);
+        const int Kt = sK[g];
+        const int Ks = overwrite ? Kt : *pK;
+        const int K = max(Kt, Ks);
+        __int128 acc[L];
+#pragma unroll
+        for (int j = 0; j < L; ++j) acc[j] = 0;
+        // table levels, aligned to K
+        __int128 tab[L];
+#pragma unroll
+        for (int j = 0; j < L; ++j) {
+            tab[j] = 0;
+            for (int c = 0; c < t.C; ++c) {
+                const size_t i = t.at(g, j, c);
+                tab[j] += (__int128)table_value(t, i);
+                t.lo[i] = 0;
+                t.hi[i] = 0;
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < L; ++j) {
+            const int jt = j - (K - Kt);
+            if (jt >= 0) acc[j] += tab[jt];
+            if (!overwrite) {
+                const int js = j - (K - Ks);
+                if (js >= 0) acc[j] += bin_read(&pb[2 * js], &pb[2 * js + 1]);
+            }
+        }
+        const unsigned f = sF[g] | (overwrite ? 0u : *pF);
+#pragma unroll
+        for (int j = 0; j < L; ++j) bin_write(&pb[2 * j], &pb[2 * j + 1], acc[j]);
+        *pK = K;
+        *pF = f;
+        sK[g] = 0;
+        sKp[g] = 0;
+        sF[g] = 0;
+    }
+}
+
+// Clear the CTA table (an item whose state header does not match is dropped).
+template <int L>
+__device__ void clear_table(int G, const Table& t, int* sK, int* sKp, unsigned* sF, int ctid, int NC) {
+    for (int g = ctid; g < G; g += NC) {
+        for (int j = 0; j < L; ++j)
+            for (int c = 0; c < t.C; ++c) {
+                const size_t x = t.at(g, j, c);
+                t.lo[x] = 0;
+                t.hi[x] = 0;
+            }
+        sK[g] = 0;
+        sKp[g] = 0;
+        sF[g] = 0;
+    }
+}
+
+}  // namespace
+
+template <typename T, int L, int NCW>
+__global__ void __launch_bounds__(32 * (NCW + 1)) k_fused_multi(MultiArgs a, int dtype) {
+    constexpr int NC = 32 * NCW;
+    extern __shared__ __align__(128) unsigned char smem[];
+    const FusedSmem m = fused_layout<T>(a.S, a.R, a.Gcap, L, a.C);
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem + m.bars);
+    uint64_t* empty = full + a.S;
+    int* ctl = reinterpret_cast<int*>(smem + m.ctl);  // cnt[3][2] at 0..5, abort at 6
+    StageMeta* meta = reinterpret_cast<StageMeta*>(smem + m.total);  // S entries
+    int32_t* skeys = reinterpret_cast<int32_t*>(smem + m.keys);
+    T* svals = reinterpret_cast<T*>(smem + m.vals);
+    Table tab;
+    tab.lo = reinterpret_cast<unsigned*>(smem + m.bins);
+    tab.hi = reinterpret_cast<int*>(tab.lo + (size_t)a.Gcap * L * a.C);
+    tab.L = L;
+    tab.C = a.C;
+    int* sK = reinterpret_cast<int*>(smem + m.K);
+    int* sKp = reinterpret_cast<int*>(smem + m.Kp);
+    unsigned* sF = reinterpret_cast<unsigned*>(smem + m.F);
+    unsigned short* dlist = reinterpret_cast<unsigned short*>(smem + m.dlist);
+    int* rlist = reinterpret_cast<int*>(smem + m.rlist);
+    volatile int* abort_flag = &ctl[6];
+
+    const int tid = threadIdx.x;
+    const int R = a.R, S = a.S;
+    for (int i = tid; i < a.Gcap * L * a.C; i += blockDim.x) {
+        tab.lo[i] = 0;
+        tab.hi[i] = 0;
+    }
+    for (int g = tid; g < a.Gcap; g += blockDim.x) {
+        sK[g] = 0;
+        sKp[g] = 0;
+        sF[g] = 0;
+    }
+    if (tid < 16) ctl[tid] = 0;
+    if (tid == 0) {
+        for (int s = 0; s < S; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], NCW);
+        }
+        fence_barrier_init();
+    }
+    __syncthreads();
+
+    if (tid >= NC) {
+        // ------------------------------------------------------------ producer
+        if (tid == NC) {
+            long long i = 0;  // tiles issued by this CTA (ring position)
+            bool ok = true;
+            for (;;) {
+                const int w = atomicAdd(a.counter, 1);
+                const bool done = w >= a.nitems;
+                const MItem it = done ? MItem{0, 0, 0, 0, 0} : a.items[w];
+                const MTask tk = a.tasks[done ? 0 : it.task];
+                const long long nrows = it.row1 - it.row0;
+                const long long ntile = done ? 1 : (nrows + R - 1) / R;
+                for (long long t = 0; t < ntile; ++t, ++i) {
+                    const int s = (int)(i % S);
+                    if (i >= S && !mbar_wait_bounded(&empty[s], (uint32_t)(((i / S) - 1) & 1), kWaitNs)) {
+                        ok = false;
+                        break;
+                    }
+                    StageMeta sm;
+                    if (done) {
+                        sm.item = -1;
+                        sm.rows = sm.rows_tma = sm.last = 0;
+                        sm.row0 = 0;
+                    } else {
+                        sm.item = w;
+                        sm.row0 = it.row0 + t * R;
+                        sm.rows = (int)min((long long)R, it.row1 - sm.row0);
+                        sm.rows_tma = sm.rows & ~3;
+                        sm.last = t == ntile - 1;
+                    }
+                    meta[s] = sm;
+                    const uint32_t kb = (uint32_t)sm.rows_tma * 4, vb = (uint32_t)sm.rows_tma * sizeof(T);
+                    mbar_arrive_expect_tx(&full[s], kb + vb);
+                    if (sm.rows_tma > 0) {
+                        bulk_g2s(skeys + (size_t)s * R, tk.keys + sm.row0, kb, &full[s]);
+                        bulk_g2s(svals + (size_t)s * R, reinterpret_cast<const T*>(tk.vals) + sm.row0, vb, &full[s]);
+                    }
+                }
+                if (done || !ok) break;
+            }
+            // never leave with a copy in flight
+            for (long long k = max(0ll, i - S); k < i; ++k)
+                if (!mbar_wait_bounded(&full[k % S], (uint32_t)((k / S) & 1), kWaitNs)) break;
+        }
+        return;
+    }
+
+    // --------------------------------------------------------------- consumers
+    const int ctid = tid;
+    const int copy = (ctid & 31) & (a.C - 1);
+    SAddr sa;
+    sa.K = smem_addr(sK);
+    sa.lo = smem_addr(tab.lo);
+    sa.hi = smem_addr(tab.hi);
+    bool bad_key = false;
+    int tcount = 0;
+    for (long long i = 0;; ++i) {
+        const int s = (int)(i % S);
+        const bool ok = mbar_wait_bounded(&full[s], (uint32_t)((i / S) & 1), kWaitNs);
+        if (!ok) *abort_flag = 1;  // before the barrier, read after it
+        named_bar_sync(1, NC);
+        if (*abort_flag) break;
+        const StageMeta sm = meta[s];
+        if (sm.item < 0) break;
+        const MItem it = a.items[sm.item];
+        const MTask tk = a.tasks[it.task];
+        const int G = tk.G;
+        int* cnt = &ctl[2 * (tcount % 3)];
+        const int32_t* tk_s = skeys + (size_t)s * R;
+        const T* tv_s = svals + (size_t)s * R;
+        const int32_t* gk = tk.keys + sm.row0;
+        const T* gv = reinterpret_cast<const T*>(tk.vals) + sm.row0;
+        sa.keys = smem_addr(tk_s);
+        sa.vals = smem_addr(tv_s);
+        for (int r = 4 * ctid; r < sm.rows_tma; r += 4 * NC)
+            consume_quad<T, L>(sa, tk_s, tv_s, r, G, tab, copy, sK, sKp, sF, dlist, rlist, cnt, bad_key);
+        for (int r = sm.rows_tma + ctid; r < sm.rows; r += NC)
+            consume_row<T, L>(gk[r], gv[r], r, G, tab, copy, sK, sKp, sF, dlist, rlist, cnt, bad_key);
+        named_bar_sync(1, NC);
+        if (ctid == 0) {  // the counters of two tiles ago are no longer read
+            int* old = &ctl[2 * ((tcount + 2) % 3)];
+            old[0] = 0;
+            old[1] = 0;
+        }
+        const int nd = cnt[0], nr = cnt[1];
+        if (nr > 0) {
+            raise_and_add_multi<T, L>(nr, nd, tk_s, tv_s, gk, gv, sm.rows_tma, tab, sK, sKp, dlist, rlist, ctid,
+                                      NC);
+            named_bar_sync(1, NC);
+        }
+        __syncwarp();
+        if ((ctid & 31) == 0) mbar_arrive(&empty[s]);
+        ++tcount;
+        if (sm.last) {
+            unsigned* errors = &reinterpret_cast<repro_state_header*>(tk.hdr)->errors;
+            const bool hdr_ok = task_header_ok(tk.hdr, dtype, L, G);
+            if (__any_sync(0xffffffffu, bad_key) && (ctid & 31) == 0) atomicOr(errors, REPRO_ERR_KEY);
+            bad_key = false;
+            if (ctid == 0 && !hdr_ok) atomicOr(errors, REPRO_ERR_LAYOUT);
+            unsigned char* dst = it.excl ? tk.hdr + sizeof(repro_state_header)
+                                         : a.partials + (size_t)it.part * rec_bytes(L);
+            if (hdr_ok || !it.excl)
+                flush_table<L>(dst, G, tab, sK, sKp, sF, !it.excl, ctid, NC);
+            else
+                clear_table<L>(G, tab, sK, sKp, sF, ctid, NC);
+            named_bar_sync(1, NC);
+        }
+    }
+}
+
+// state += sum of a task's partial tables; one block = 32 groups of one task,
+// 8 warps splitting the partials.
+template <int L>
+__global__ void __launch_bounds__(256) k_merge_items(const MTask* __restrict__ tasks, const MergeBlk* __restrict__ blks,
+                                                     const unsigned char* __restrict__ parts, int dtype) {
+    constexpr int NW = 8;
+    constexpr size_t rec = 8 + 16 * L;
+    __shared__ int sKw[NW][32];
+    __shared__ unsigned sFw[NW][32];
+    __shared__ long long sAcc[NW][32][L][2];
+    const MergeBlk b = blks[blockIdx.x];
+    const MTask tk = tasks[b.task];
+    const int G = tk.G;
+    if (!task_header_ok(tk.hdr, dtype, L, G)) return;  // flagged by k_fused_multi
+    StateView st{tk.hdr, L, G};
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const long long g = (long long)b.g0 + lane;
+    const bool valid = g < G;
+    int K = 0;
+    unsigned fl = 0;
+    if (valid)
+        for (int c = w; c < b.nparts; c += NW) {
+            const unsigned char* r = parts + ((size_t)b.part + (size_t)c * G + g) * rec;
+            K = max(K, *reinterpret_cast<const int*>(r));
+            fl |= *reinterpret_cast<const unsigned*>(r + 4);
+        }
+    sKw[w][lane] = K;
+    sFw[w][lane] = fl;
+    __syncthreads();
+    int Kg = valid ? *st.K(g) : 0;
+#pragma unroll
+    for (int i = 0; i < NW; ++i) Kg = max(Kg, sKw[i][lane]);
+    __int128 acc[L];
+#pragma unroll
+    for (int j = 0; j < L; ++j) acc[j] = 0;
+    if (valid)
+        for (int c = w; c < b.nparts; c += NW) {
+            const unsigned char* r = parts + ((size_t)b.part + (size_t)c * G + g) * rec;
+            const int d = Kg - *reinterpret_cast<const int*>(r);
+            const long long* bb = reinterpret_cast<const long long*>(r + 8);
+#pragma unroll
+            for (int j = 0; j < L; ++j)
+                if (j - d >= 0) acc[j] += bin_read(&bb[2 * (j - d)], &bb[2 * (j - d) + 1]);
+        }
+#pragma unroll
+    for (int j = 0; j < L; ++j) {
+        sAcc[w][lane][j][0] = (long long)(unsigned long long)acc[j];
+        sAcc[w][lane][j][1] = (long long)(acc[j] >> 64);
+    }
+    __syncthreads();
+    if (w == 0 && valid) {
+        const int d = Kg - *st.K(g);
+        __int128 tot[L];
+#pragma unroll
+        for (int j = 0; j < L; ++j) {
+            tot[j] = (j - d >= 0) ? bin_read(st.lo(g, j - d), st.hi(g, j - d)) : 0;
+#pragma unroll
+            for (int i = 0; i < NW; ++i)
+                tot[j] += (((__int128)sAcc[i][lane][j][1]) << 64) + (__int128)(unsigned long long)sAcc[i][lane][j][0];
+        }
+        unsigned f = *st.flags(g);
+#pragma unroll
+        for (int i = 0; i < NW; ++i) f |= sFw[i][lane];
+#pragma unroll
+        for (int j = 0; j < L; ++j) bin_write(st.lo(g, j), st.hi(g, j), tot[j]);
+        *st.K(g) = Kg;
+        *st.flags(g) = f;
+    }
+}
+
+// ---------------------------------------------------------------------- plan
+
+namespace {
+
+template <typename T, int L, int NCW>
+cudaError_t launch_multi_t(const MultiArgs& a, int dtype, int ctas, size_t smem, cudaStream_t s) {
+    auto kern = k_fused_multi<T, L, NCW>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    prof_begin(PROF_FUSED, s);
+    kern<<<ctas, 32 * (NCW + 1), smem, s>>>(a, dtype);
+    prof_end(PROF_FUSED, s);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+template <typename T, int L>
+cudaError_t launch_multi_ncw(int ncw, const MultiArgs& a, int dtype, int ctas, size_t smem, cudaStream_t s) {
+    return ncw == 8 ? launch_multi_t<T, L, 8>(a, dtype, ctas, smem, s) : launch_multi_t<T, L, 16>(a, dtype, ctas, smem, s);
+}
+
+template <typename T>
+cudaError_t launch_multi_L(int L, int ncw, const MultiArgs& a, int dtype, int ctas, size_t smem, cudaStream_t s) {
+    switch (L) {
+        case 1: return launch_multi_ncw<T, 1>(ncw, a, dtype, ctas, smem, s);
+        case 2: return launch_multi_ncw<T, 2>(ncw, a, dtype, ctas, smem, s);
+        case 3: return launch_multi_ncw<T, 3>(ncw, a, dtype, ctas, smem, s);
+        default: return launch_multi_ncw<T, 4>(ncw, a, dtype, ctas, smem, s);
+    }
+}
+
+}  // namespace
+
+struct BatchPlan {
+    int dtype = 0, L = 0;
+    FusedPlanConfig cfg{};
+    int gcap_ = 1;
+    int ctas = 0;
+    size_t smem = 0;
+    int nitems = 0, nblks = 0;
+    MTask* d_tasks = nullptr;
+    MItem* d_items = nullptr;
+    MergeBlk* d_blks = nullptr;
+    unsigned char* d_partials = nullptr;
+    int* d_counter = nullptr;
+    // tasks outside the single-pass path: run one by one through the two-pass path
+    std::vector<repro_task> slow;
+    void* d_slow_scratch = nullptr;
+};
+
+}  // namespace rp
+
+using namespace rp;
+
+struct repro_batch_plan_s {
+    BatchPlan p;
+};
+
+extern "C" {
+
+repro_status repro_batch_prepare(const repro_task* tasks, int ntasks, repro_dtype dtype, int L,
+                                 repro_batch_plan* out) {
+    if (!out || ntasks < 0 || (ntasks > 0 && !tasks) || (dtype != REPRO_F64 && dtype != REPRO_F32) || L < 1 ||
+        L > 4)
+        return REPRO_EINVAL;
+    *out = nullptr;
+    for (int t = 0; t < ntasks; ++t) {
+        const repro_task& k = tasks[t];
+        if (!k.state || k.n < 0 || k.num_groups < 1 || k.num_groups > INT32_MAX || (k.n > 0 && (!k.keys || !k.values)))
+            return REPRO_EINVAL;
+        if ((uintptr_t)k.state % 16 || (uintptr_t)k.keys % 4 || (uintptr_t)k.values % (dtype == REPRO_F64 ? 8 : 4))
+            return REPRO_EINVAL;
+    }
+    repro_batch_plan_s* plan = new (std::nothrow) repro_batch_plan_s;
+    if (!plan) return REPRO_ENOMEM;
+    BatchPlan& P = plan->p;
+    P.dtype = dtype;
+    P.L = L;
+    // single-pass tasks: aligned rows and a table that fits
+    std::vector<int> fast;
+    long long gcap = 1, total_tiles = 0, slow_gmax = 0;
+    for (int t = 0; t < ntasks; ++t) {
+        const repro_task& k = tasks[t];
+        if (k.n == 0) continue;
+        if (fused_supported(dtype, L, k.num_groups, k.keys, k.values)) {
+            fast.push_back(t);
+            gcap = std::max(gcap, (long long)k.num_groups);
+        } else {
+            P.slow.push_back(k);
+            slow_gmax = std::max(slow_gmax, (long long)k.num_groups);
+        }
+    }
+    repro_status st = REPRO_OK;
+    if (!fast.empty()) {
+        if (!fused_plan_config(dtype, L, (int)gcap, sizeof(StageMeta) * 4, P.cfg)) {
+            delete plan;
+            return REPRO_ERANGE;
+        }
+        const int R = P.cfg.R;
+        for (int t : fast) total_tiles += (tasks[t].n + R - 1) / R;
+        P.ctas = device_info().sms * P.cfg.ctas_per_sm;
+        // autotuned item size: about four items per CTA, at least 8 tiles,
+        // at most 2^23 rows (no int64 table bin can overflow within an item)
+        long long tpi = (total_tiles + 4ll * P.ctas - 1) / (4ll * P.ctas);
+        tpi = std::max(8ll, std::min(tpi, (1ll << 23) / R));
+        std::vector<MTask> htasks(ntasks);
+        for (int t = 0; t < ntasks; ++t)
+            htasks[t] = MTask{tasks[t].keys, tasks[t].values, tasks[t].n, (int)tasks[t].num_groups, 0,
+                              (unsigned char*)tasks[t].state};
+        std::vector<MItem> items;
+        std::vector<MergeBlk> blks;
+        long long part = 0;
+        for (int t : fast) {
+            const long long ntile = (tasks[t].n + R - 1) / R;
+            const long long nit = (ntile + tpi - 1) / tpi;
+            const int G = (int)tasks[t].num_groups;
+            for (long long k = 0; k < nit; ++k) {
+                MItem it;
+                it.task = t;
+                it.excl = nit == 1;
+                it.row0 = k * tpi * R;
+                it.row1 = std::min<long long>(tasks[t].n, (k + 1) * tpi * R);
+                it.part = nit == 1 ? -1 : part + k * G;
+                items.push_back(it);
+            }
+            if (nit > 1) {
+                for (int g0 = 0; g0 < G; g0 += 32) blks.push_back(MergeBlk{t, g0, (int)nit, 0, part});
+                part += nit * G;
+            }
+        }
+        // largest items first: the dynamic schedule then balances the tail
+        std::stable_sort(items.begin(), items.end(),
+                         [](const MItem& x, const MItem& y) { return x.row1 - x.row0 > y.row1 - y.row0; });
+        P.nitems = (int)items.size();
+        P.nblks = (int)blks.size();
+        P.smem = fused_plan_smem(dtype, L, (int)gcap, P.cfg) + sizeof(StageMeta) * (size_t)P.cfg.S;
+        cudaError_t e = cudaMalloc(&P.d_tasks, sizeof(MTask) * std::max(1, ntasks));
+        if (e == cudaSuccess) e = cudaMalloc(&P.d_items, sizeof(MItem) * std::max(1, P.nitems));
+        if (e == cudaSuccess) e = cudaMalloc(&P.d_blks, sizeof(MergeBlk) * std::max(1, P.nblks));
+        if (e == cudaSuccess) e = cudaMalloc(&P.d_partials, std::max<size_t>(16, (size_t)part * (8 + 16 * (size_t)L)));
+        if (e == cudaSuccess) e = cudaMalloc(&P.d_counter, sizeof(int));
+        if (e == cudaSuccess) e = cudaMemcpy(P.d_tasks, htasks.data(), sizeof(MTask) * ntasks, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess && P.nitems)
+            e = cudaMemcpy(P.d_items, items.data(), sizeof(MItem) * P.nitems, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess && P.nblks)
+            e = cudaMemcpy(P.d_blks, blks.data(), sizeof(MergeBlk) * P.nblks, cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) st = e == cudaErrorMemoryAllocation ? REPRO_ENOMEM : REPRO_ECUDA;
+        P.gcap_ = (int)gcap;
+    }
+    if (st == REPRO_OK && !P.slow.empty()) {
+        if (cudaMalloc(&P.d_slow_scratch, two_pass_scratch_bytes(slow_gmax)) != cudaSuccess) st = REPRO_ENOMEM;
+    }
+    if (st != REPRO_OK) {
+        repro_batch_destroy(plan);
+        return st;
+    }
+    *out = plan;
+    return REPRO_OK;
+}
+
+repro_status repro_batch_run(repro_batch_plan plan, void* stream) {
+    if (!plan) return REPRO_EINVAL;
+    BatchPlan& P = plan->p;
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = cudaSuccess;
+    if (P.nitems > 0) {
+        e = cudaMemsetAsync(P.d_counter, 0, sizeof(int), s);
+        if (e != cudaSuccess) return REPRO_ECUDA;
+        MultiArgs a;
+        a.tasks = P.d_tasks;
+        a.items = P.d_items;
+        a.nitems = P.nitems;
+        a.counter = P.d_counter;
+        a.R = P.cfg.R;
+        a.S = P.cfg.S;
+        a.C = P.cfg.copies;
+        a.Gcap = P.gcap_;
+        a.partials = P.d_partials;
+        const int ctas = std::min(P.ctas, std::max(1, P.nitems));
+        e = P.dtype == REPRO_F64 ? launch_multi_L<double>(P.L, P.cfg.ncw, a, P.dtype, ctas, P.smem, s)
+                                 : launch_multi_L<float>(P.L, P.cfg.ncw, a, P.dtype, ctas, P.smem, s);
+        if (e != cudaSuccess) return REPRO_ECUDA;
+        if (P.nblks > 0) {
+            prof_begin(PROF_MERGE, s);
+            switch (P.L) {
+                case 1: k_merge_items<1><<<P.nblks, 256, 0, s>>>(P.d_tasks, P.d_blks, P.d_partials, P.dtype); break;
+                case 2: k_merge_items<2><<<P.nblks, 256, 0, s>>>(P.d_tasks, P.d_blks, P.d_partials, P.dtype); break;
+                case 3: k_merge_items<3><<<P.nblks, 256, 0, s>>>(P.d_tasks, P.d_blks, P.d_partials, P.dtype); break;
+                default: k_merge_items<4><<<P.nblks, 256, 0, s>>>(P.d_tasks, P.d_blks, P.d_partials, P.dtype); break;
+            }
+            prof_end(PROF_MERGE, s);
+            count_launches(1);
+            if ((e = cudaGetLastError()) != cudaSuccess) return REPRO_ECUDA;
+        }
+    }
+    for (const repro_task& k : P.slow) {
+        e = launch_groupby_two_pass(k.keys, k.values, k.n, P.dtype, P.L, k.num_groups, k.state, P.d_slow_scratch, s);
+        if (e != cudaSuccess) return REPRO_ECUDA;
+    }
+    return REPRO_OK;
+}
+
+repro_status repro_batch_destroy(repro_batch_plan plan) {
+    if (!plan) return REPRO_OK;
+    BatchPlan& P = plan->p;
+    cudaFree(P.d_tasks);
+    cudaFree(P.d_items);
+    cudaFree(P.d_blks);
+    cudaFree(P.d_partials);
+    cudaFree(P.d_counter);
+    cudaFree(P.d_slow_scratch);
+    delete plan;
+    return REPRO_OK;
+}
+
+repro_status repro_groupby_sum_batched(const repro_task* tasks, int ntasks, repro_dtype dtype, int L,
+                                       void* stream) {
+    repro_batch_plan plan = nullptr;
+    repro_status st = repro_batch_prepare(tasks, ntasks, dtype, L, &plan);
+    if (st != REPRO_OK) return st;
+    st = repro_batch_run(plan, stream);
+    if (cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess && st == REPRO_OK) st = REPRO_ECUDA;
+    repro_batch_destroy(plan);
+    return st;
+}
+
+}  // extern "C"

@@ -22,54 +22,12 @@
 #include <cstdlib>
 #include <mutex>
 
-#include "ptx.cuh"
-#include "repro_device.cuh"
+#include "fused_device.cuh"
 #include "repro_internal.h"
 
 namespace rp {
 
 namespace {
-
-constexpr uint64_t kWaitNs = 2000000000ull;  // every mbarrier wait gives up after 2 s
-
-struct FusedSmem {
-    // byte offsets into dynamic shared memory
-    size_t bars, ctl, keys, vals, bins, K, Kp, F, dlist, rlist, total;
-};
-
-__host__ __device__ inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
-
-template <typename T>
-__host__ __device__ inline FusedSmem fused_layout(int S, int R, int G, int L, int C) {
-    FusedSmem m;
-    size_t o = 0;
-    m.bars = o;
-    o += 16 * (size_t)S;  // full[S], empty[S]
-    m.ctl = o;
-    o += 64;  // counters[3][2], abort, pad
-    o = align_up(o, 128);
-    m.keys = o;
-    o += (size_t)S * R * 4;
-    o = align_up(o, 128);
-    m.vals = o;
-    o += (size_t)S * R * sizeof(T);
-    o = align_up(o, 16);
-    m.bins = o;  // LO[G][L][C] (uint32) then HI[G][L][C] (int32)
-    o += (size_t)G * L * C * 8;
-    m.K = o;
-    o += (size_t)G * 4;
-    m.Kp = o;
-    o += (size_t)G * 4;
-    m.F = o;
-    o += (size_t)G * 4;
-    m.dlist = o;
-    o += (size_t)R * 2;
-    o = align_up(o, 4);
-    m.rlist = o;
-    o += (size_t)(R < G ? R : G) * 4;
-    m.total = align_up(o, 16);
-    return m;
-}
 
 struct FusedArgs {
     const int32_t* keys;
@@ -87,240 +45,6 @@ struct FusedArgs {
 };
 
 }  // namespace
-
-// The CTA table holds each bin of each group as a 64-bit value
-// HI * 2^32 + LO with LO unsigned and HI signed, both 32-bit words in shared
-// memory: 32-bit shared atomics run far faster than 64-bit ones.  A digit d
-// is added to LO as its low 32 bits; the value LO held before (returned by
-// the atomic) tells whether LO wrapped, and HI takes d's high part plus that
-// carry, skipped when zero.  Every add is exact and adds commute, so the
-// result is independent of their order.  With C copies, lane l uses copy
-// l mod C (C = 32: conflict-free, and skewed keys never collide in a warp).
-struct Table {
-    unsigned* lo;
-    int* hi;
-    int L, C;
-    __device__ __forceinline__ size_t at(int g, int j, int copy) const {
-        return ((size_t)g * L + j) * C + copy;
-    }
-};
-
-__device__ __forceinline__ void add_digit(const Table& t, size_t i, long long d) {
-    const unsigned lo = (unsigned)(unsigned long long)d;
-    const unsigned old = atomicAdd(&t.lo[i], lo);
-    const int carry = (unsigned)(old + lo) < old;
-    const int hi = (int)(d >> 32) + carry;
-    if (hi != 0) atomicAdd(&t.hi[i], hi);
-}
-
-__device__ __forceinline__ long long table_value(const Table& t, size_t i) {
-    return (long long)(((unsigned long long)(long long)t.hi[i] << 32) + (unsigned long long)t.lo[i]);
-}
-
-// Add one row's digits into the CTA table (its window must hold the value).
-template <typename T, int L>
-__device__ __forceinline__ void add_row(const Split& s, int K, const Table& t, int g, int copy) {
-    long long top, mid, low;
-    digits3<T>(s, top, mid, low);
-    const int j = K - s.kb;  // level of the value's top digit
-    if (j < L && top != 0) add_digit(t, t.at(g, j, copy), top);
-    if (j + 1 < L && s.kb >= 1 && mid != 0) add_digit(t, t.at(g, j + 1, copy), mid);
-    if (j + 2 < L && s.kb >= 2 && low != 0) add_digit(t, t.at(g, j + 2, copy), low);
-}
-
-// Phase A for one row: add it, flag it, or defer it until its group's window
-// is raised.
-template <typename T, int L>
-__device__ __forceinline__ void consume_row(int g, T b, int idx, int G, const Table& t, int copy, int* sK,
-                                            int* sKp, unsigned* sF, unsigned short* dlist, int* rlist, int* cnt,
-                                            bool& bad_key) {
-    if ((unsigned)g >= (unsigned)G) {
-        bad_key = true;
-        return;
-    }
-    const Split s = split_value(b);
-    if (s.flag) {
-        atomicOr(&sF[g], s.flag);
-        return;
-    }
-    if (s.mant == 0) return;
-    const int K = sK[g];
-    if (s.kb <= K) {
-        add_row<T, L>(s, K, t, g, copy);
-        return;
-    }
-    dlist[atomicAdd(&cnt[0], 1)] = (unsigned short)idx;
-    if (atomicMax(&sKp[g], s.kb) == K) rlist[atomicAdd(&cnt[1], 1)] = g;  // first raiser of g in this tile
-}
-
-// Shared-window addresses of the hot loop's arrays.
-struct SAddr {
-    uint32_t keys, vals;  // stage s starts at keys + 4 R s, vals + sizeof(T) R s
-    uint32_t K;           // int K[G]
-    uint32_t lo, hi;      // table words [(g L + j) C + copy]
-};
-
-// Value bit-words of four consecutive rows: (hi, lo) per row for double,
-// the single word for float.
-template <typename T>
-struct QuadWords;
-template <>
-struct QuadWords<double> {
-    static __device__ __forceinline__ void load(uint32_t a, uint32_t hi[4], uint32_t lo[4]) {
-        const uint4 p = lds_v4(a), q = lds_v4(a + 16);
-        lo[0] = p.x; hi[0] = p.y; lo[1] = p.z; hi[1] = p.w;
-        lo[2] = q.x; hi[2] = q.y; lo[3] = q.z; hi[3] = q.w;
-    }
-};
-template <>
-struct QuadWords<float> {
-    static __device__ __forceinline__ void load(uint32_t a, uint32_t hi[4], uint32_t lo[4]) {
-        const uint4 p = lds_v4(a);
-        hi[0] = p.x; hi[1] = p.y; hi[2] = p.z; hi[3] = p.w;
-        lo[0] = lo[1] = lo[2] = lo[3] = 0u;
-    }
-};
-
-template <typename T>
-__device__ __forceinline__ T words_value(uint32_t hi, uint32_t lo);
-template <>
-__device__ __forceinline__ double words_value<double>(uint32_t hi, uint32_t lo) {
-    return __longlong_as_double((long long)(((unsigned long long)hi << 32) | lo));
-}
-template <>
-__device__ __forceinline__ float words_value<float>(uint32_t hi, uint32_t) {
-    return __uint_as_float(hi);
-}
-
-// Phase A for four consecutive rows of a staged tile (r0 a multiple of 4):
-// vector loads, then -- when all four rows are ordinary (good key, normal
-// value inside its group's window) -- straight-line digits for the four rows
-// and predicated 32-bit atomics; otherwise the rows go one by one through
-// consume_row.
-template <typename T, int L>
-__device__ __forceinline__ void consume_quad(const SAddr& sa, const int32_t* tk, const T* tv, int r0, int G,
-                                             const Table& t, int copy, int* sK, int* sKp, unsigned* sF,
-                                             unsigned short* dlist, int* rlist, int* cnt, bool& bad_key) {
-    const uint4 k4 = lds_v4(sa.keys + 4u * (uint32_t)r0);
-    const int gq[4] = {(int)k4.x, (int)k4.y, (int)k4.z, (int)k4.w};
-    uint32_t vhi[4], vlo[4];
-    QuadWords<T>::load(sa.vals + (uint32_t)sizeof(T) * (uint32_t)r0, vhi, vlo);
-    int kb[4], K[4];
-    bool fast = true;
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        const bool ok_key = (unsigned)gq[q] < (unsigned)G;
-        const bool ok_val = Lean<T>::decode_words(vhi[q], kb[q]);
-        K[q] = (int)lds_u32(sa.K + 4u * (uint32_t)(ok_key ? gq[q] : 0));
-        fast = fast && ok_key && ok_val && kb[q] <= K[q];
-    }
-    if (!fast) {  // some row is special, has a bad key, or must wait for a raise
-#pragma unroll
-        for (int q = 0; q < 4; ++q)
-            consume_row<T, L>(gq[q], words_value<T>(vhi[q], vlo[q]), r0 + q, G, t, copy, sK, sKp, sF, dlist,
-                              rlist, cnt, bad_key);
-        return;
-    }
-    // common case, straight-line: four rows' digits, then predicated atomics.
-    // Top and middle digits are almost never zero (adding zero is harmless);
-    // the low digit is zero whenever the value starts above its boundary.
-    unsigned lo[12];
-    int hi[12];
-    uint32_t at[12];
-    bool on[12];
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        Lean<T>::digits(vhi[q], vlo[q], kb[q], &lo[3 * q], &hi[3 * q]);
-        const int j = K[q] - kb[q];  // window level of the value's top digit
-        const uint32_t row = 4u * ((uint32_t)gq[q] * (uint32_t)(L * t.C) + (uint32_t)copy);
-#pragma unroll
-        for (int k = 0; k < 3; ++k) {
-            on[3 * q + k] = (j + k < L) && (k < 2 || (lo[3 * q + k] | (unsigned)hi[3 * q + k]) != 0u);
-            at[3 * q + k] = row + 4u * (uint32_t)(min(j + k, L - 1) * t.C);
-        }
-    }
-    unsigned old[12];
-#pragma unroll
-    for (int i = 0; i < 12; ++i) old[i] = atom_add_if(on[i], sa.lo + at[i], lo[i]);
-#pragma unroll
-    for (int i = 0; i < 12; ++i) {
-        const int h = hi[i] + (int)((unsigned)(old[i] + lo[i]) < old[i]);
-        red_add_if(on[i] && h != 0, sa.hi + at[i], h);
-    }
-}
-
-// After phase A: raise the windows collected in rlist (dropping low levels)
-// and add the deferred rows.  Consumer-uniform; uses named barrier 1.
-template <typename T, int L>
-__device__ __forceinline__ void raise_and_add(int nr, int nd, const int32_t* tk, const T* tv, const Table& t,
-                                              int* sK, const int* sKp, const unsigned short* dlist,
-                                              const int* rlist, int ctid, int NC) {
-    for (int i = ctid; i < nr * t.C; i += NC) {
-        const int g = rlist[i / t.C];
-        const int copy = i % t.C;
-        const int d = sKp[g] - sK[g];
-#pragma unroll
-        for (int j = L - 1; j >= 0; --j) {
-            const size_t dst = t.at(g, j, copy);
-            if (j - d >= 0) {
-                const size_t src = t.at(g, j - d, copy);
-                t.lo[dst] = t.lo[src];
-                t.hi[dst] = t.hi[src];
-            } else {
-                t.lo[dst] = 0;
-                t.hi[dst] = 0;
-            }
-        }
-    }
-    named_bar_sync(1, NC);
-    for (int i = ctid; i < nr; i += NC) sK[rlist[i]] = sKp[rlist[i]];
-    named_bar_sync(1, NC);
-    for (int i = ctid; i < nd; i += NC) {
-        const int r = dlist[i];
-        const int g = tk[r];
-        const Split s = split_value(tv[r]);
-        add_row<T, L>(s, sK[g], t, g, (ctid & 31) & (t.C - 1));
-    }
-}
-
-// Write (first) or add (later) the CTA table into this CTA's partial record
-// array, then clear the table's bins.  Consumer threads only.
-template <int L>
-__device__ void flush_partial(unsigned char* part, int G, const Table& t, const int* sK, const unsigned* sF,
-                              bool first, int ctid, int NC) {
-    constexpr size_t rec = 8 + 16 * L;
-    for (int g = ctid; g < G; g += NC) {
-        unsigned char* r = part + (size_t)g * rec;
-        int* pK = reinterpret_cast<int*>(r);
-        unsigned* pF = reinterpret_cast<unsigned*>(r + 4);
-        long long* pb = reinterpret_cast<long long*>(r + 8);
-        const int K = sK[g];
-        __int128 acc[L];
-#pragma unroll
-        for (int j = 0; j < L; ++j) {
-            acc[j] = 0;
-            for (int c = 0; c < t.C; ++c) {
-                const size_t i = t.at(g, j, c);
-                acc[j] += (__int128)table_value(t, i);
-                t.lo[i] = 0;
-                t.hi[i] = 0;
-            }
-        }
-        if (first) {
-            *pK = K;
-            *pF = sF[g];
-        } else {
-            const int d = K - *pK;  // the CTA window only rises
-#pragma unroll
-            for (int j = L - 1; j >= 0; --j)
-                if (j - d >= 0) acc[j] += bin_read(&pb[2 * (j - d)], &pb[2 * (j - d) + 1]);
-            *pK = K;
-            *pF |= sF[g];
-        }
-#pragma unroll
-        for (int j = 0; j < L; ++j) bin_write(&pb[2 * j], &pb[2 * j + 1], acc[j]);
-    }
-}
 
 template <typename T, int L, int NCW>
 __global__ void __launch_bounds__(32 * (NCW + 1)) k_fused(FusedArgs a) {
@@ -554,13 +278,9 @@ __global__ void __launch_bounds__(256) k_merge_partials(const unsigned char* __r
 
 namespace {
 
-struct FusedConfig {
-    int S, R, ncw, ctas_per_sm, copies;
-};
-
 template <typename T>
-bool pick_config(int G, int L, const DeviceInfo& di, FusedConfig& cfg) {
-    static FusedConfig forced{0, 0, 0, 0, 0};
+bool pick_config(int G, int L, const DeviceInfo& di, FusedPlanConfig& cfg, size_t extra = 0) {
+    static FusedPlanConfig forced{0, 0, 0, 0, 0};
     static bool env_read = false;
     if (!env_read) {  // tuning aid: REPRO_FUSED_CFG="S,R,ncw,ctas_per_sm[,copies]"
         const char* e = getenv("REPRO_FUSED_CFG");
@@ -573,17 +293,17 @@ bool pick_config(int G, int L, const DeviceInfo& di, FusedConfig& cfg) {
     // Prefer two CTAs per SM (barrier bubbles of one hide behind the other),
     // then one CTA with deeper staging; lane-private table copies when the
     // 32 copies fit next to the stages.
-    const FusedConfig cands[] = {{3, 2048, 8, 2, 0}, {2, 2048, 8, 2, 0}, {3, 4096, 16, 1, 0}, {4, 1024, 8, 2, 0},
+    const FusedPlanConfig cands[] = {{3, 2048, 8, 2, 0}, {2, 2048, 8, 2, 0}, {3, 4096, 16, 1, 0}, {4, 1024, 8, 2, 0},
                                  {4, 2048, 16, 1, 0}, {3, 2048, 16, 1, 0}, {2, 2048, 16, 1, 0}, {2, 1024, 16, 1, 0}};
-    auto fits = [&](FusedConfig c) {
+    auto fits = [&](FusedPlanConfig c) {
         if (c.S < 2 || c.R < 256 || c.R % (128 * c.ncw) || (c.ncw != 8 && c.ncw != 16) || c.ctas_per_sm < 1)
             return false;
         if (c.copies != 1 && c.copies != 32) return false;
-        const size_t bytes = fused_layout<T>(c.S, c.R, G, L, c.copies).total;
+        const size_t bytes = fused_layout<T>(c.S, c.R, G, L, c.copies).total + extra;
         return bytes * c.ctas_per_sm + 1024 * c.ctas_per_sm <= di.smem_per_sm && bytes <= di.smem_optin;
     };
     if (forced.S) {
-        FusedConfig c = forced;
+        FusedPlanConfig c = forced;
         if (c.copies == 0) c.copies = 1;
         if (fits(c)) {
             cfg = c;
@@ -592,7 +312,7 @@ bool pick_config(int G, int L, const DeviceInfo& di, FusedConfig& cfg) {
     }
     for (int copies : {32, 1}) {
         if (copies == 32 && G > 256) continue;
-        for (FusedConfig c : cands) {
+        for (FusedPlanConfig c : cands) {
             c.copies = copies;
             if (fits(c)) {
                 cfg = c;
@@ -642,15 +362,25 @@ cudaError_t dispatch_L(int L, int ncw, const FusedArgs& a, int ctas, size_t smem
 
 }  // namespace
 
+bool fused_plan_config(int dtype, int L, int G, size_t extra_smem, FusedPlanConfig& cfg) {
+    return dtype == REPRO_F64 ? pick_config<double>(G, L, device_info(), cfg, extra_smem)
+                              : pick_config<float>(G, L, device_info(), cfg, extra_smem);
+}
+
+size_t fused_plan_smem(int dtype, int L, int G, const FusedPlanConfig& c) {
+    return dtype == REPRO_F64 ? fused_layout<double>(c.S, c.R, G, L, c.copies).total
+                              : fused_layout<float>(c.S, c.R, G, L, c.copies).total;
+}
+
 bool fused_supported(int dtype, int L, long long G, const void* keys, const void* vals) {
     if (G > 65535) return false;
     if ((uintptr_t)keys % 16 || (uintptr_t)vals % 16) return false;
-    FusedConfig cfg;
+    FusedPlanConfig cfg;
     return dtype == REPRO_F64 ? pick_config<double>((int)G, L, device_info(), cfg)
                               : pick_config<float>((int)G, L, device_info(), cfg);
 }
 
-static int fused_ctas(long long ntiles, const FusedConfig& cfg, const DeviceInfo& di) {
+static int fused_ctas(long long ntiles, const FusedPlanConfig& cfg, const DeviceInfo& di) {
     // at least ~16 tiles per CTA keeps the partial tables small next to the input
     long long c = (long long)di.sms * cfg.ctas_per_sm;
     const long long by_work = (ntiles + 15) / 16;
@@ -660,7 +390,7 @@ static int fused_ctas(long long ntiles, const FusedConfig& cfg, const DeviceInfo
 }
 
 size_t fused_scratch_bytes(int dtype, int L, long long G, long long n) {
-    FusedConfig cfg;
+    FusedPlanConfig cfg;
     const DeviceInfo& di = device_info();
     const bool ok = dtype == REPRO_F64 ? pick_config<double>((int)G, L, di, cfg) : pick_config<float>((int)G, L, di, cfg);
     if (!ok) return 0;
@@ -671,7 +401,7 @@ size_t fused_scratch_bytes(int dtype, int L, long long G, long long n) {
 cudaError_t launch_groupby_fused(const int32_t* keys, const void* vals, long long n, int dtype, int L, long long G,
                                  void* state, void* scratch, cudaStream_t s, int max_ctas) {
     const DeviceInfo& di = device_info();
-    FusedConfig cfg;
+    FusedPlanConfig cfg;
     const bool ok = dtype == REPRO_F64 ? pick_config<double>((int)G, L, di, cfg) : pick_config<float>((int)G, L, di, cfg);
     if (!ok) return cudaErrorInvalidValue;
     FusedArgs a;

@@ -34,6 +34,13 @@ cudaError_t launch_groupby_two_pass(const int32_t* keys, const void* vals, long 
                                     long long G, void* state, void* scratch, cudaStream_t s);
 
 // Single-pass fused path (shared-memory group tables, TMA-staged tiles).
+struct FusedPlanConfig {
+    int S, R, ncw, ctas_per_sm, copies;  // stages, rows per tile, consumer warps, CTAs per SM, table copies
+};
+// Tile / stage / warp configuration for a group table of G groups (extra_smem
+// bytes reserved on top of the kernel's layout); false if none fits.
+bool fused_plan_config(int dtype, int L, int G, size_t extra_smem, FusedPlanConfig& cfg);
+size_t fused_plan_smem(int dtype, int L, int G, const FusedPlanConfig& cfg);
 bool fused_supported(int dtype, int L, long long G, const void* keys, const void* vals);
 size_t fused_scratch_bytes(int dtype, int L, long long G, long long n);
 // max_ctas > 0 caps the number of CTAs (and so the partial tables in scratch).
