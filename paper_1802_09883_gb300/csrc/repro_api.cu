@@ -86,6 +86,11 @@ repro_status repro_groupby_sum(const int32_t* keys, const void* values, int64_t 
         if (scratch.err != cudaSuccess) return from_cuda(scratch.err);
         return from_cuda(launch_groupby_fused(keys, values, n, dtype, L, num_groups, state, scratch.p, s));
     }
+    if (n > 0 && partitioned_supported(dtype, L, num_groups, n, keys, values)) {
+        Scratch scratch(partitioned_scratch_bytes(dtype, L, num_groups, n), s);
+        if (scratch.err != cudaSuccess) return from_cuda(scratch.err);
+        return from_cuda(launch_groupby_partitioned(keys, values, n, dtype, L, num_groups, state, scratch.p, s));
+    }
     Scratch scratch(two_pass_scratch_bytes(num_groups), s);
     if (scratch.err != cudaSuccess) return from_cuda(scratch.err);
     return from_cuda(launch_groupby_two_pass(keys, values, n, dtype, L, num_groups, state, scratch.p, s));

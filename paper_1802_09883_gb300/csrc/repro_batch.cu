@@ -21,53 +21,13 @@
 #include <vector>
 
 #include "fused_device.cuh"
+#include "multi_types.h"
 #include "repro.h"
 #include "repro_internal.h"
 
 namespace rp {
 
 namespace {
-
-struct MTask {
-    const int32_t* keys;
-    const void* vals;
-    long long n;
-    int G;
-    int pad;
-    unsigned char* hdr;   // the task's state (header + records)
-};
-
-struct MItem {
-    int task;
-    int excl;             // 1: the item covers the whole task -> merge into its state
-    long long row0, row1; // rows [row0, row1) of the task; row0 is a multiple of R
-    long long part;       // first record of this item's partial table (excl == 0)
-};
-
-struct MergeBlk {
-    int task;
-    int g0;               // first group of this block (32 groups per block)
-    int nparts;           // partial tables of the task
-    int pad;
-    long long part;       // first record of the task's first partial table
-};
-
-struct StageMeta {
-    int item;             // -1: no more work
-    int rows;             // rows of this tile
-    int rows_tma;         // rows delivered by TMA (a multiple of 4), the rest read from global
-    int last;             // last tile of the item
-    long long row0;       // first row of the tile within the task
-};
-
-struct MultiArgs {
-    const MTask* tasks;
-    const MItem* items;
-    int nitems;
-    int* counter;
-    int R, S, C, Gcap;
-    unsigned char* partials;
-};
 
 __host__ __device__ constexpr size_t rec_bytes(int L) { return 8 + 16 * (size_t)L; }
 
@@ -229,9 +189,10 @@ __global__ void __launch_bounds__(32 * (NCW + 1)) k_fused_multi(MultiArgs a, int
         if (tid == NC) {
             long long i = 0;  // tiles issued by this CTA (ring position)
             bool ok = true;
+            const int nitems = a.nitems_ptr ? *a.nitems_ptr : a.nitems;
             for (;;) {
                 const int w = atomicAdd(a.counter, 1);
-                const bool done = w >= a.nitems;
+                const bool done = w >= nitems;
                 const MItem it = done ? MItem{0, 0, 0, 0, 0} : a.items[w];
                 const MTask tk = a.tasks[done ? 0 : it.task];
                 const long long nrows = it.row1 - it.row0;
@@ -319,12 +280,11 @@ __global__ void __launch_bounds__(32 * (NCW + 1)) k_fused_multi(MultiArgs a, int
         ++tcount;
         if (sm.last) {
             unsigned* errors = &reinterpret_cast<repro_state_header*>(tk.hdr)->errors;
-            const bool hdr_ok = task_header_ok(tk.hdr, dtype, L, G);
+            const bool hdr_ok = task_header_ok(tk.hdr, dtype, L, tk.G_hdr);
             if (__any_sync(0xffffffffu, bad_key) && (ctid & 31) == 0) atomicOr(errors, REPRO_ERR_KEY);
             bad_key = false;
             if (ctid == 0 && !hdr_ok) atomicOr(errors, REPRO_ERR_LAYOUT);
-            unsigned char* dst = it.excl ? tk.hdr + sizeof(repro_state_header)
-                                         : a.partials + (size_t)it.part * rec_bytes(L);
+            unsigned char* dst = it.excl ? tk.recs : a.partials + (size_t)it.part * rec_bytes(L);
             if (hdr_ok || !it.excl)
                 flush_table<L>(dst, G, tab, sK, sKp, sF, !it.excl, ctid, NC);
             else
@@ -335,23 +295,28 @@ __global__ void __launch_bounds__(32 * (NCW + 1)) k_fused_multi(MultiArgs a, int
 }
 
 // state += sum of a task's partial tables; one block = 32 groups of one task,
-// 8 warps splitting the partials.
+// 8 warps splitting the partials.  Blocks at or beyond *nblks_ptr (when
+// given) have nothing to do.
 template <int L>
 __global__ void __launch_bounds__(256) k_merge_items(const MTask* __restrict__ tasks, const MergeBlk* __restrict__ blks,
-                                                     const unsigned char* __restrict__ parts, int dtype) {
+                                                     const int* nblks_ptr, const unsigned char* __restrict__ parts,
+                                                     int dtype) {
     constexpr int NW = 8;
     constexpr size_t rec = 8 + 16 * L;
     __shared__ int sKw[NW][32];
     __shared__ unsigned sFw[NW][32];
     __shared__ long long sAcc[NW][32][L][2];
+    if (nblks_ptr && (int)blockIdx.x >= *nblks_ptr) return;
     const MergeBlk b = blks[blockIdx.x];
     const MTask tk = tasks[b.task];
     const int G = tk.G;
-    if (!task_header_ok(tk.hdr, dtype, L, G)) return;  // flagged by k_fused_multi
-    StateView st{tk.hdr, L, G};
+    if (!task_header_ok(tk.hdr, dtype, L, tk.G_hdr)) return;  // flagged by k_fused_multi
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const long long g = (long long)b.g0 + lane;
     const bool valid = g < G;
+    int* pK = reinterpret_cast<int*>(tk.recs + (size_t)g * rec);
+    unsigned* pF = reinterpret_cast<unsigned*>(tk.recs + (size_t)g * rec + 4);
+    long long* pb = reinterpret_cast<long long*>(tk.recs + (size_t)g * rec + 8);
     int K = 0;
     unsigned fl = 0;
     if (valid)
@@ -363,7 +328,7 @@ __global__ void __launch_bounds__(256) k_merge_items(const MTask* __restrict__ t
     sKw[w][lane] = K;
     sFw[w][lane] = fl;
     __syncthreads();
-    int Kg = valid ? *st.K(g) : 0;
+    int Kg = valid ? *pK : 0;
 #pragma unroll
     for (int i = 0; i < NW; ++i) Kg = max(Kg, sKw[i][lane]);
     __int128 acc[L];
@@ -385,24 +350,30 @@ __global__ void __launch_bounds__(256) k_merge_items(const MTask* __restrict__ t
     }
     __syncthreads();
     if (w == 0 && valid) {
-        const int d = Kg - *st.K(g);
+        const int d = Kg - *pK;
         __int128 tot[L];
 #pragma unroll
         for (int j = 0; j < L; ++j) {
-            tot[j] = (j - d >= 0) ? bin_read(st.lo(g, j - d), st.hi(g, j - d)) : 0;
+            tot[j] = (j - d >= 0) ? bin_read(&pb[2 * (j - d)], &pb[2 * (j - d) + 1]) : 0;
 #pragma unroll
             for (int i = 0; i < NW; ++i)
                 tot[j] += (((__int128)sAcc[i][lane][j][1]) << 64) + (__int128)(unsigned long long)sAcc[i][lane][j][0];
         }
-        unsigned f = *st.flags(g);
+        unsigned f = *pF;
 #pragma unroll
         for (int i = 0; i < NW; ++i) f |= sFw[i][lane];
 #pragma unroll
-        for (int j = 0; j < L; ++j) bin_write(st.lo(g, j), st.hi(g, j), tot[j]);
-        *st.K(g) = Kg;
-        *st.flags(g) = f;
+        for (int j = 0; j < L; ++j) bin_write(&pb[2 * j], &pb[2 * j + 1], tot[j]);
+        *pK = Kg;
+        *pF = f;
     }
 }
+
+// Host launchers shared with the partitioned path.
+cudaError_t launch_multi(int dtype, int L, const FusedPlanConfig& cfg, int gcap, const void* tasks, const void* items,
+                         int nitems, const int* nitems_ptr, int* counter, void* partials, int ctas, cudaStream_t s);
+cudaError_t launch_merge_items(int L, int dtype, const void* tasks, const void* blks, int nblks, const int* nblks_ptr,
+                               const void* partials, cudaStream_t s);
 
 // ---------------------------------------------------------------------- plan
 
@@ -436,6 +407,43 @@ cudaError_t launch_multi_L(int L, int ncw, const MultiArgs& a, int dtype, int ct
 }
 
 }  // namespace
+
+cudaError_t launch_multi(int dtype, int L, const FusedPlanConfig& cfg, int gcap, const void* tasks, const void* items,
+                         int nitems, const int* nitems_ptr, int* counter, void* partials, int ctas, cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(int), s);
+    if (e != cudaSuccess) return e;
+    MultiArgs a;
+    a.tasks = (const MTask*)tasks;
+    a.items = (const MItem*)items;
+    a.nitems = nitems;
+    a.nitems_ptr = nitems_ptr;
+    a.counter = counter;
+    a.R = cfg.R;
+    a.S = cfg.S;
+    a.C = cfg.copies;
+    a.Gcap = gcap;
+    a.partials = (unsigned char*)partials;
+    const size_t smem = fused_plan_smem(dtype, L, gcap, cfg) + sizeof(StageMeta) * (size_t)cfg.S;
+    return dtype == REPRO_F64 ? launch_multi_L<double>(L, cfg.ncw, a, dtype, ctas, smem, s)
+                              : launch_multi_L<float>(L, cfg.ncw, a, dtype, ctas, smem, s);
+}
+
+cudaError_t launch_merge_items(int L, int dtype, const void* tasks, const void* blks, int nblks, const int* nblks_ptr,
+                               const void* partials, cudaStream_t s) {
+    const MTask* t = (const MTask*)tasks;
+    const MergeBlk* b = (const MergeBlk*)blks;
+    const unsigned char* p = (const unsigned char*)partials;
+    prof_begin(PROF_MERGE, s);
+    switch (L) {
+        case 1: k_merge_items<1><<<nblks, 256, 0, s>>>(t, b, nblks_ptr, p, dtype); break;
+        case 2: k_merge_items<2><<<nblks, 256, 0, s>>>(t, b, nblks_ptr, p, dtype); break;
+        case 3: k_merge_items<3><<<nblks, 256, 0, s>>>(t, b, nblks_ptr, p, dtype); break;
+        default: k_merge_items<4><<<nblks, 256, 0, s>>>(t, b, nblks_ptr, p, dtype); break;
+    }
+    prof_end(PROF_MERGE, s);
+    count_launches(1);
+    return cudaGetLastError();
+}
 
 struct BatchPlan {
     int dtype = 0, L = 0;
@@ -511,8 +519,9 @@ repro_status repro_batch_prepare(const repro_task* tasks, int ntasks, repro_dtyp
         tpi = std::max(8ll, std::min(tpi, (1ll << 23) / R));
         std::vector<MTask> htasks(ntasks);
         for (int t = 0; t < ntasks; ++t)
-            htasks[t] = MTask{tasks[t].keys, tasks[t].values, tasks[t].n, (int)tasks[t].num_groups, 0,
-                              (unsigned char*)tasks[t].state};
+            htasks[t] = MTask{tasks[t].keys, tasks[t].values, tasks[t].n, (int)tasks[t].num_groups,
+                              (int)tasks[t].num_groups, (unsigned char*)tasks[t].state,
+                              (unsigned char*)tasks[t].state + sizeof(repro_state_header)};
         std::vector<MItem> items;
         std::vector<MergeBlk> blks;
         long long part = 0;
@@ -539,7 +548,7 @@ repro_status repro_batch_prepare(const repro_task* tasks, int ntasks, repro_dtyp
                          [](const MItem& x, const MItem& y) { return x.row1 - x.row0 > y.row1 - y.row0; });
         P.nitems = (int)items.size();
         P.nblks = (int)blks.size();
-        P.smem = fused_plan_smem(dtype, L, (int)gcap, P.cfg) + sizeof(StageMeta) * (size_t)P.cfg.S;
+        P.smem = 0;
         cudaError_t e = cudaMalloc(&P.d_tasks, sizeof(MTask) * std::max(1, ntasks));
         if (e == cudaSuccess) e = cudaMalloc(&P.d_items, sizeof(MItem) * std::max(1, P.nitems));
         if (e == cudaSuccess) e = cudaMalloc(&P.d_blks, sizeof(MergeBlk) * std::max(1, P.nblks));
@@ -570,33 +579,13 @@ repro_status repro_batch_run(repro_batch_plan plan, void* stream) {
     cudaStream_t s = (cudaStream_t)stream;
     cudaError_t e = cudaSuccess;
     if (P.nitems > 0) {
-        e = cudaMemsetAsync(P.d_counter, 0, sizeof(int), s);
-        if (e != cudaSuccess) return REPRO_ECUDA;
-        MultiArgs a;
-        a.tasks = P.d_tasks;
-        a.items = P.d_items;
-        a.nitems = P.nitems;
-        a.counter = P.d_counter;
-        a.R = P.cfg.R;
-        a.S = P.cfg.S;
-        a.C = P.cfg.copies;
-        a.Gcap = P.gcap_;
-        a.partials = P.d_partials;
         const int ctas = std::min(P.ctas, std::max(1, P.nitems));
-        e = P.dtype == REPRO_F64 ? launch_multi_L<double>(P.L, P.cfg.ncw, a, P.dtype, ctas, P.smem, s)
-                                 : launch_multi_L<float>(P.L, P.cfg.ncw, a, P.dtype, ctas, P.smem, s);
+        e = launch_multi(P.dtype, P.L, P.cfg, P.gcap_, P.d_tasks, P.d_items, P.nitems, nullptr, P.d_counter,
+                         P.d_partials, ctas, s);
         if (e != cudaSuccess) return REPRO_ECUDA;
         if (P.nblks > 0) {
-            prof_begin(PROF_MERGE, s);
-            switch (P.L) {
-                case 1: k_merge_items<1><<<P.nblks, 256, 0, s>>>(P.d_tasks, P.d_blks, P.d_partials, P.dtype); break;
-                case 2: k_merge_items<2><<<P.nblks, 256, 0, s>>>(P.d_tasks, P.d_blks, P.d_partials, P.dtype); break;
-                case 3: k_merge_items<3><<<P.nblks, 256, 0, s>>>(P.d_tasks, P.d_blks, P.d_partials, P.dtype); break;
-                default: k_merge_items<4><<<P.nblks, 256, 0, s>>>(P.d_tasks, P.d_blks, P.d_partials, P.dtype); break;
-            }
-            prof_end(PROF_MERGE, s);
-            count_launches(1);
-            if ((e = cudaGetLastError()) != cudaSuccess) return REPRO_ECUDA;
+            e = launch_merge_items(P.L, P.dtype, P.d_tasks, P.d_blks, P.nblks, nullptr, P.d_partials, s);
+            if (e != cudaSuccess) return REPRO_ECUDA;
         }
     }
     for (const repro_task& k : P.slow) {

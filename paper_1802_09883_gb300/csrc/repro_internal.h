@@ -47,6 +47,20 @@ size_t fused_scratch_bytes(int dtype, int L, long long G, long long n);
 cudaError_t launch_groupby_fused(const int32_t* keys, const void* vals, long long n, int dtype, int L, long long G,
                                  void* state, void* scratch, cudaStream_t s, int max_ctas = 0);
 
+// Large group counts: partition by key range, then the multi-task kernel
+// over the partitions (repro_partition.cu).
+bool partitioned_supported(int dtype, int L, long long G, long long n, const void* keys, const void* vals);
+size_t partitioned_scratch_bytes(int dtype, int L, long long G, long long n);
+cudaError_t launch_groupby_partitioned(const int32_t* keys, const void* vals, long long n, int dtype, int L,
+                                       long long G, void* state, void* scratch, cudaStream_t s);
+
+// Multi-task single-pass kernel and its partial merge (repro_batch.cu); the
+// task / item / merge-block arrays are laid out as in multi_types.h.
+cudaError_t launch_multi(int dtype, int L, const FusedPlanConfig& cfg, int gcap, const void* tasks, const void* items,
+                         int nitems, const int* nitems_ptr, int* counter, void* partials, int ctas, cudaStream_t s);
+cudaError_t launch_merge_items(int L, int dtype, const void* tasks, const void* blks, int nblks, const int* nblks_ptr,
+                               const void* partials, cudaStream_t s);
+
 cudaError_t launch_merge(void* dst, const void* src, int dtype, int L, long long G, cudaStream_t s);
 cudaError_t launch_finalize(const void* state, int dtype, int L, long long G, void* out, cudaStream_t s);
 

@@ -304,3 +304,48 @@ def test_fused_variants_in_subprocess(env):
     r = subprocess.run([sys.executable, "-c", _SUB.format(root=root)], env={**os.environ, **env},
                        capture_output=True, text=True, timeout=600)
     assert r.returncode == 0 and "ok" in r.stdout, r.stdout + r.stderr
+
+
+# ------------------------------------------------- partitioned large-G path
+
+@pytest.mark.parametrize("G,dist,L", [(1 << 16, "zipf", 3), (1 << 16, "uniform", 2), (1 << 20, "uniform", 4),
+                                      (5000, "zipf", 3), (300_000, "uniform", 3)])
+def test_partitioned_path_matches_oracle(G, dist, L):
+    n = 1 << 22
+    w = WL.sweep_cell(G, dist, L, n=n, seed=G + L, device=DEV)
+    st, out = run_gpu(w.keys, w.values, w.G, w.L)
+    assert st.check() == 0
+    ost, _ = oracle_state(_np(w.keys), _np(w.values), w.G, w.L, threads=8)
+    assert_state_equal(st, ost)
+    assert_bits_equal(_np(out), O.finalize(ost))
+
+
+def test_partitioned_path_accumulates_and_reports_bad_keys():
+    G, L = 70_000, 3
+    g = torch.Generator(device=DEV)
+    g.manual_seed(44)
+    k1 = WL.uniform_keys(300_000, G, g, DEV)
+    v1 = WL.random_values(300_000, -30, 30, g, DEV)
+    k2 = WL.uniform_keys(200_000, G, g, DEV)
+    v2 = WL.random_values(200_000, -5, 60, g, DEV)  # raises windows of the first call
+    k2[123] = G + 5
+    st = R.State(G, L)
+    st.add(k1, v1)
+    st.add(k2, v2)
+    with pytest.raises(R.ReproError):
+        st.check()
+    mask = (k2 >= 0) & (k2 < G)
+    ost, _ = oracle_state(np.concatenate([_np(k1), _np(k2[mask])]), np.concatenate([_np(v1), _np(v2[mask])]), G, L)
+    assert_state_equal(st, ost)
+
+
+@pytest.mark.parametrize("n", [1, 5, 2447, 9999])
+def test_partitioned_path_small_inputs_with_idle_ctas(n):
+    """Row counts that leave most partition CTAs without rows."""
+    G, L = 20000, 3
+    w = WL.plain(n=n, G=G, L=L, seed=n, device=DEV, e_lo=-45, e_hi=45)
+    st, out = run_gpu(w.keys, w.values, G, L)
+    assert st.check() == 0
+    ost, _ = oracle_state(_np(w.keys), _np(w.values), G, L, threads=1)
+    assert_state_equal(st, ost)
+    assert_bits_equal(_np(out), O.finalize(ost))
