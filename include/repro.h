@@ -20,9 +20,11 @@
  *    anything is enqueued.  Errors found in the data (a key outside
  *    [0, num_groups)) are recorded in the state's header and reported by
  *    repro_state_check().
- *  - Scratch memory is taken stream-ordered from the device's default memory
- *    pool (cudaMallocAsync) and returned on the same stream; REPRO_ENOMEM if
- *    it cannot be had.
+ *  - Scratch memory is taken stream-ordered (cudaMallocFromPoolAsync) from a
+ *    memory pool the library creates per device and returned to it on the
+ *    same stream; the pool keeps freed bytes cached for the next call
+ *    (repro_release_cached_memory hands them back).  REPRO_ENOMEM if scratch
+ *    cannot be had.
  *  - L (levels) is 1..4; num_groups is 1 .. 2^31 - 1; keys are dense int32
  *    group ids in [0, num_groups) (the paper's IdentityHashing, Sec. VI-A).
  */
@@ -231,6 +233,10 @@ const char* repro_strerror(repro_status status);
 
 /* Version of the state layout and the library (major * 100 + minor). */
 int repro_version(void);
+
+/* Synchronise the current device and return the scratch bytes cached in the
+   library's memory pool to the driver. */
+repro_status repro_release_cached_memory(void);
 
 /* Profiling aid (not part of the computation).  While enabled, the library
    records a pair of CUDA events on the caller's stream around every launch

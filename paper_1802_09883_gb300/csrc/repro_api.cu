@@ -44,13 +44,41 @@ static repro_status from_cuda(cudaError_t e) {
     return REPRO_ECUDA;
 }
 
-// Stream-ordered scratch from the default memory pool, freed on scope exit.
+// The library's own memory pool on the current device: scratch returns to
+// it on free and stays cached (release threshold = unlimited), so repeated
+// calls do not map and unmap multi-gigabyte scratch from the driver.
+// repro_release_cached_memory() hands the cached bytes back.
+static cudaMemPool_t library_pool(cudaError_t& err) {
+    static cudaMemPool_t pools[64] = {};
+    static std::mutex mu;
+    int dev = 0;
+    err = cudaGetDevice(&dev);
+    if (err != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+    std::lock_guard<std::mutex> lock(mu);
+    if (!pools[dev]) {
+        cudaMemPoolProps props = {};
+        props.allocType = cudaMemAllocationTypePinned;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = dev;
+        cudaMemPool_t p = nullptr;
+        err = cudaMemPoolCreate(&p, &props);
+        if (err != cudaSuccess) return nullptr;
+        uint64_t thr = UINT64_MAX;
+        cudaMemPoolSetAttribute(p, cudaMemPoolAttrReleaseThreshold, &thr);
+        pools[dev] = p;
+    }
+    return pools[dev];
+}
+
+// Stream-ordered scratch from the library pool, freed on scope exit.
 struct Scratch {
     void* p = nullptr;
     cudaStream_t s;
     cudaError_t err = cudaSuccess;
     Scratch(size_t bytes, cudaStream_t st) : s(st) {
-        if (bytes) err = cudaMallocAsync(&p, bytes, s);
+        if (!bytes) return;
+        cudaMemPool_t pool = library_pool(err);
+        if (pool) err = cudaMallocFromPoolAsync(&p, bytes, pool, s);
     }
     ~Scratch() {
         if (p) cudaFreeAsync(p, s);
@@ -157,5 +185,14 @@ const char* repro_strerror(repro_status status) {
 }
 
 int repro_version(void) { return 100; }
+
+repro_status repro_release_cached_memory(void) {
+    cudaError_t e;
+    cudaMemPool_t pool = library_pool(e);
+    if (!pool) return from_cuda(e);
+    e = cudaDeviceSynchronize();
+    if (e == cudaSuccess) e = cudaMemPoolTrimTo(pool, 0);
+    return from_cuda(e);
+}
 
 }  // extern "C"

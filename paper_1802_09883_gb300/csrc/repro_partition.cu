@@ -28,6 +28,7 @@ namespace rp {
 namespace {
 
 constexpr int kPartThreads = 512;
+constexpr int kScatterRows = 8;  // rows per thread per scatter tile
 constexpr int kMaxParts = 4096;
 
 struct PartGeom {
@@ -108,22 +109,141 @@ __global__ void __launch_bounds__(1024) k_part_scan(const int* __restrict__ coun
 }
 
 template <typename T>
+struct RowQuad;
+template <>
+struct RowQuad<double> {
+    static __device__ __forceinline__ void load(const double* p, double v[4]) {
+        const double2 a = reinterpret_cast<const double2*>(p)[0], b = reinterpret_cast<const double2*>(p)[1];
+        v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+    }
+};
+template <>
+struct RowQuad<float> {
+    static __device__ __forceinline__ void load(const float* p, float v[4]) {
+        const float4 a = reinterpret_cast<const float4*>(p)[0];
+        v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+    }
+};
+
+// Exclusive scan of n (<= 8 * blockDim.x) ints in shared memory, in place;
+// returns the total.  All threads of the block call it.
+__device__ int block_exclusive_scan(int* a, int n, int* warp_tot) {
+    const int per = (n + blockDim.x - 1) / blockDim.x;
+    const int b0 = threadIdx.x * per;
+    int local = 0;
+    for (int i = b0; i < min(n, b0 + per); ++i) local += a[i];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int incl = local;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    if (lane == 31) warp_tot[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        const int nw = blockDim.x >> 5;
+        int w = lane < nw ? warp_tot[lane] : 0;
+        int wi = w;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, wi, o);
+            if (lane >= o) wi += y;
+        }
+        if (lane < nw) warp_tot[lane] = wi - w;  // exclusive
+        if (lane == nw - 1) warp_tot[32] = wi;   // total
+    }
+    __syncthreads();
+    int run = warp_tot[warp] + incl - local;
+    for (int i = b0; i < min(n, b0 + per); ++i) {
+        const int v = a[i];
+        a[i] = run;
+        run += v;
+    }
+    const int total = warp_tot[32];
+    __syncthreads();
+    return total;
+}
+
+// Copy every row to its partition, one tile of kScatterRows * blockDim.x rows at a
+// time: every row takes its rank in its partition with one shared atomic, a
+// block scan gives each partition its place in the tile and one global slot
+// range per tile, rows are sorted in shared memory, and consecutive threads
+// then write consecutive runs (coalesced stores).
+template <typename T>
 __global__ void __launch_bounds__(kPartThreads) k_part_scatter(const int32_t* __restrict__ keys,
                                                                const T* __restrict__ vals, long long n, int G,
                                                                PartGeom pg, const int* __restrict__ offsets,
                                                                int32_t* __restrict__ okeys, T* __restrict__ ovals) {
-    extern __shared__ int s_cur[];
-    for (int p = threadIdx.x; p < pg.F; p += blockDim.x) s_cur[p] = offsets[(size_t)p * pg.C + blockIdx.x];
+    extern __shared__ __align__(16) unsigned char s_raw[];
+    constexpr int RPT = kScatterRows;  // rows per thread per tile
+    const int TILE = RPT * kPartThreads;
+    T* s_vals = reinterpret_cast<T*>(s_raw);                              // [TILE]
+    int* s_keys = reinterpret_cast<int*>(s_vals + TILE);                  // [TILE] global keys, sorted
+    int* s_cur = s_keys + TILE;                                           // [F] global write cursor
+    int* s_cnt = s_cur + pg.F;                                            // [F] rows per partition in the tile
+    int* s_gb = s_cnt + pg.F;                                             // [F] global base of the tile's run
+    int* s_wt = s_gb + pg.F;                                              // [33] scan scratch
+    for (int p = threadIdx.x; p < pg.F; p += blockDim.x) {
+        s_cur[p] = offsets[(size_t)p * pg.C + blockIdx.x];
+        s_cnt[p] = 0;
+    }
     __syncthreads();
     const long long beg = blockIdx.x * pg.chunk;
-    const long long end = min(n, beg + pg.chunk);
+    const long long end = max(beg, min(n, beg + pg.chunk));
     const int mask = pg.Gp - 1;
-    for (long long i = beg + threadIdx.x; i < end; i += blockDim.x) {
-        const int k = keys[i];
-        if ((unsigned)k >= (unsigned)G) continue;
-        const int pos = atomicAdd(&s_cur[k >> pg.shift], 1);
-        okeys[pos] = k & mask;
-        ovals[pos] = vals[i];
+    for (long long tb = beg; tb < end; tb += TILE) {
+        int k[RPT];
+        T v[RPT];
+        int rank[RPT];
+#pragma unroll
+        for (int h = 0; h < RPT / 4; ++h) {  // quads strided by the block: coalesced 16-byte loads
+            const long long r0 = tb + 4ll * (threadIdx.x + h * kPartThreads);
+            int* kq = &k[4 * h];
+            T* vq = &v[4 * h];
+            kq[0] = kq[1] = kq[2] = kq[3] = -1;
+            vq[0] = vq[1] = vq[2] = vq[3] = 0;
+            if (r0 + 3 < end) {
+                const int4 k4 = *reinterpret_cast<const int4*>(keys + r0);
+                kq[0] = k4.x; kq[1] = k4.y; kq[2] = k4.z; kq[3] = k4.w;
+                RowQuad<T>::load(vals + r0, vq);
+            } else {
+#pragma unroll
+                for (int j = 0; j < 4; ++j)
+                    if (r0 + j < end) {
+                        kq[j] = keys[r0 + j];
+                        vq[j] = vals[r0 + j];
+                    }
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < RPT; ++j)
+            rank[j] = (unsigned)k[j] < (unsigned)G ? atomicAdd(&s_cnt[k[j] >> pg.shift], 1) : -1;
+        __syncthreads();
+        // reserve each partition's run in global memory, then place of each partition in the tile
+        for (int p = threadIdx.x; p < pg.F; p += blockDim.x) {
+            s_gb[p] = s_cur[p];
+            s_cur[p] += s_cnt[p];
+        }
+        const int nvalid = block_exclusive_scan(s_cnt, pg.F, s_wt);  // s_cnt now holds tile starts
+#pragma unroll
+        for (int j = 0; j < RPT; ++j)
+            if (rank[j] >= 0) {
+                const int pos = s_cnt[k[j] >> pg.shift] + rank[j];
+                s_keys[pos] = k[j];
+                s_vals[pos] = v[j];
+            }
+        __syncthreads();
+        for (int i = threadIdx.x; i < nvalid; i += blockDim.x) {
+            const int kk = s_keys[i];
+            const int p = kk >> pg.shift;
+            const int pos = s_gb[p] + (i - s_cnt[p]);
+            okeys[pos] = kk & mask;
+            ovals[pos] = s_vals[i];
+        }
+        __syncthreads();
+        for (int p = threadIdx.x; p < pg.F; p += blockDim.x) s_cnt[p] = 0;
+        __syncthreads();
     }
 }
 
@@ -304,12 +424,21 @@ cudaError_t launch_groupby_partitioned(const int32_t* keys, const void* vals, lo
     prof_begin(PROF_PARTITION, s);
     k_part_hist<<<pp.pg.C, kPartThreads, hsmem, s>>>(keys, n, (int)G, pp.pg, counts, errors);
     k_part_scan<<<1, 1024, 0, s>>>(counts, pp.pg, offsets, pstart, pcount);
-    if (dtype == REPRO_F64)
-        k_part_scatter<double><<<pp.pg.C, kPartThreads, hsmem, s>>>(keys, (const double*)vals, n, (int)G, pp.pg,
-                                                                    offsets, okeys, (double*)ovals);
-    else
-        k_part_scatter<float><<<pp.pg.C, kPartThreads, hsmem, s>>>(keys, (const float*)vals, n, (int)G, pp.pg,
-                                                                   offsets, okeys, (float*)ovals);
+    const size_t vsz = dtype == REPRO_F64 ? 8 : 4;
+    const size_t ssmem = (size_t)kScatterRows * kPartThreads * (vsz + 4) + 3 * (size_t)pp.pg.F * 4 + 33 * 4;
+    if (dtype == REPRO_F64) {
+        if ((e = cudaFuncSetAttribute(k_part_scatter<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)ssmem)) != cudaSuccess)
+            return e;
+        k_part_scatter<double><<<pp.pg.C, kPartThreads, ssmem, s>>>(keys, (const double*)vals, n, (int)G, pp.pg,
+                                                                     offsets, okeys, (double*)ovals);
+    } else {
+        if ((e = cudaFuncSetAttribute(k_part_scatter<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)ssmem)) != cudaSuccess)
+            return e;
+        k_part_scatter<float><<<pp.pg.C, kPartThreads, ssmem, s>>>(keys, (const float*)vals, n, (int)G, pp.pg,
+                                                                    offsets, okeys, (float*)ovals);
+    }
     prof_end(PROF_PARTITION, s);
     k_part_plan<<<1, 1024, 0, s>>>(pstart, pcount, pp.pg, (int)G, pp.cfg.R, pp.tpi, okeys, ovals,
                                    dtype == REPRO_F64 ? 8 : 4, (unsigned char*)state, L, (MTask*)(b + ly.tasks),
