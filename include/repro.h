@@ -131,6 +131,20 @@ repro_status repro_groupby_sum(const int32_t* keys, const void* values, int64_t 
                                void* stream);
 
 /*
+ * Several SUM aggregates over one grouping given as two low-cardinality
+ * uint8 key columns (SQL: SELECT SUM(c0), SUM(c1), ... GROUP BY k1, k2, the
+ * shape of the paper's TPC-H Q1 aggregation, Sec. VI-E): the group of row i
+ * is key1[i] * card2 + key2[i] (rows whose composite key is not below
+ * num_groups are skipped and flag REPRO_ERR_KEY in every state), and column
+ * c is added into states[c] exactly as repro_groupby_sum would.
+ * cols and states are HOST arrays of ncols DEVICE pointers.  Scratch: 4
+ * bytes per row for the composite keys.
+ */
+repro_status repro_groupby_sum_cols(const uint8_t* key1, const uint8_t* key2, int card2,
+                                    const void* const* cols, int ncols, int64_t n, repro_dtype dtype,
+                                    int L, int64_t num_groups, void* const* states, void* stream);
+
+/*
  * repro_groupby_sum without any allocation.  The paper has no counterpart:
  * this is a deployment variant of repro_groupby_sum for callers that cannot
  * allocate device memory while they aggregate -- a host whose buffer
@@ -227,6 +241,91 @@ repro_status groupby_sum_fp64(const int32_t* keys, const double* values, int64_t
 /* Float variant of the conventional baseline (float accumulators). */
 repro_status groupby_sum_fp32(const int32_t* keys, const float* values, int64_t n,
                               int64_t num_groups, float* out, void* stream);
+
+/*
+ * Request server: continuous batching of aggregation queries.
+ *
+ * The paper aggregates one relation per query (Sec. II problem statement,
+ * Sec. V Algorithm 4); a server answers many such queries that arrive over
+ * time, without changing any query's result: every bin add is exact, so a
+ * query's state, and so its result, is the same whatever it shares the
+ * device with (Sec. III reproducibility requirement).
+ *
+ * A scheduler thread admits submitted queries in arrival order while their
+ * device memory (state plus scratch, estimated at submit) fits the budget and
+ * a slot is free.  It then runs iterations: each iteration takes the next
+ * chunk_rows rows of every admitted query; chunks whose group table fits the
+ * single-pass kernel go into one multi-task persistent launch, the others
+ * through the partitioned path on a second stream.  Partial states stay on
+ * the device between iterations.  After its last chunk a query is finalized
+ * into its output and its state freed; a host callback stamps the completion
+ * time.  At most max_inflight iterations are queued ahead of the device.
+ */
+typedef struct repro_server_s* repro_server;
+
+typedef struct {
+    int64_t memory_budget; /* bytes for admitted queries' states + scratch; 0: a quarter of free memory */
+    int64_t chunk_rows;    /* rows per query per iteration, rounded up to a multiple of 4096; 0: 2^24 */
+    int32_t max_active;    /* admitted queries at a time; 0: 256 */
+    int32_t max_inflight;  /* iterations queued on the device; 0: 3 */
+} repro_server_config;
+
+typedef struct {
+    int32_t done;       /* 1 once out holds the result */
+    int32_t status;     /* repro_status of the query: data errors as repro_state_check reports them */
+    uint32_t errors;    /* the state's error word (REPRO_ERR_*) */
+    uint32_t reserved;
+    int64_t arrival_ns; /* repro_server_now_ns() clock: arrival, admission, result in out */
+    int64_t admit_ns;
+    int64_t done_ns;
+} repro_request_info;
+
+typedef struct {
+    int64_t submitted, completed;
+    int64_t iterations;     /* scheduler iterations issued */
+    int64_t batch_launches; /* multi-task launches */
+    int64_t large_calls;    /* partitioned-path chunk calls */
+    int64_t memory_in_use, memory_peak, memory_budget;
+    int32_t active, waiting; /* admitted and not finished; arrived and not admitted */
+} repro_server_stats;
+
+/* Monotonic clock of the server's timestamps, in nanoseconds. */
+int64_t repro_server_now_ns(void);
+
+/* Create a server on the current device (cfg may be NULL for defaults). */
+repro_status repro_server_create(const repro_server_config* cfg, repro_server* out);
+
+/*
+ * Submit one query: SUM of values grouped by keys (as repro_groupby_sum) into
+ * a fresh state, finalized into out (num_groups elements of the dtype).
+ * keys and values: DEVICE memory of the server's device, unchanged until the
+ * query is done.  out: device memory or page-locked host memory.
+ * ready_event (cudaEvent_t, may be NULL): the server's streams wait on it
+ * before reading the inputs.  arrival_ns: the query is not admitted before
+ * this time of repro_server_now_ns() (0: now); it is the start of the query's
+ * latency.  *id receives the query's handle.
+ * REPRO_EINVAL for bad arguments or pointers that are not device-accessible,
+ * REPRO_ERANGE if the query alone needs more than the memory budget.
+ */
+repro_status repro_server_submit(repro_server srv, const int32_t* keys, const void* values, int64_t n,
+                                 repro_dtype dtype, int L, int64_t num_groups, void* out, void* ready_event,
+                                 int64_t arrival_ns, uint64_t* id);
+
+/* Non-blocking state of a query (info->done = 0 while it runs).  REPRO_EINVAL
+   for an unknown or released id. */
+repro_status repro_server_poll(repro_server srv, uint64_t id, repro_request_info* info);
+
+/* Wait up to timeout_s seconds for a query: REPRO_ETIMEOUT if it is not done. */
+repro_status repro_server_wait(repro_server srv, uint64_t id, double timeout_s, repro_request_info* info);
+
+/* Forget a finished query (REPRO_EINVAL if unknown or still running). */
+repro_status repro_server_release(repro_server srv, uint64_t id);
+
+repro_status repro_server_stats_get(repro_server srv, repro_server_stats* st);
+
+/* Finish every submitted query (honouring arrival times), then free the
+   server.  Results of unreleased queries are no longer readable. */
+repro_status repro_server_destroy(repro_server srv);
 
 /* Human-readable text for a status code (static storage). */
 const char* repro_strerror(repro_status status);

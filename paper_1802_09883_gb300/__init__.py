@@ -80,13 +80,27 @@ def lib(build_if_stale: bool = True):
         L.repro_batch_run.argtypes = [vp, vp]
         L.repro_batch_destroy.argtypes = [vp]
         L.repro_groupby_sum_batched.argtypes = [vp, i32, i32, i32, vp]
+        L.repro_groupby_sum_cols.argtypes = [vp, vp, i32, vp, i32, i64, i32, i32, i64, vp, vp]
+        L.repro_release_cached_memory.argtypes = []
         L.repro_strerror.argtypes = [i32]
         L.repro_strerror.restype = ctypes.c_char_p
         L.repro_version.restype = i32
+        u64p = ctypes.POINTER(ctypes.c_uint64)
+        L.repro_server_now_ns.argtypes = []
+        L.repro_server_now_ns.restype = i64
+        L.repro_server_create.argtypes = [vp, ctypes.POINTER(vp)]
+        L.repro_server_submit.argtypes = [vp, vp, vp, i64, i32, i32, i64, vp, vp, i64, u64p]
+        L.repro_server_poll.argtypes = [vp, ctypes.c_uint64, vp]
+        L.repro_server_wait.argtypes = [vp, ctypes.c_uint64, ctypes.c_double, vp]
+        L.repro_server_release.argtypes = [vp, ctypes.c_uint64]
+        L.repro_server_stats_get.argtypes = [vp, vp]
+        L.repro_server_destroy.argtypes = [vp]
         for name in ("repro_state_init", "repro_groupby_sum", "repro_groupby_sum_noalloc", "repro_merge",
                      "repro_finalize", "repro_batch_prepare", "repro_batch_run", "repro_batch_destroy",
-                     "repro_groupby_sum_batched",
-                     "repro_state_check", "groupby_sum_fp64", "groupby_sum_fp32"):
+                     "repro_groupby_sum_batched", "repro_groupby_sum_cols", "repro_release_cached_memory",
+                     "repro_state_check", "groupby_sum_fp64", "groupby_sum_fp32", "repro_server_create",
+                     "repro_server_submit", "repro_server_poll", "repro_server_wait", "repro_server_release",
+                     "repro_server_stats_get", "repro_server_destroy"):
             getattr(L, name).restype = i32
         _lib = L
     return _lib
@@ -298,3 +312,31 @@ def groupby_sum_batched(tasks, L: int = 3):
     torch.cuda.current_stream(plan.device).synchronize()
     plan.close()
     return states
+
+
+def groupby_sum_cols(key1: torch.Tensor, key2: torch.Tensor, card2: int, cols, num_groups: int, L: int = 3,
+                     states=None):
+    """SUM of every column in `cols` grouped by (key1 * card2 + key2), two
+    uint8 key columns; returns (and accumulates into) one State per column."""
+    _require_cuda(key1, "key1")
+    _require_cuda(key2, "key2")
+    if key1.dtype != torch.uint8 or key2.dtype != torch.uint8 or key1.numel() != key2.numel():
+        raise ValueError("key1 and key2 must be uint8 columns of the same length")
+    cols = [c.contiguous() for c in cols]
+    dtype = cols[0].dtype
+    if any(c.dtype != dtype or c.numel() != key1.numel() for c in cols):
+        raise ValueError("all columns must share dtype and length with the keys")
+    if states is None:
+        states = [State(num_groups, L, dtype, device=cols[0].device) for _ in cols]
+    key1, key2 = key1.contiguous(), key2.contiguous()
+    cp = (ctypes.c_void_p * len(cols))(*[c.data_ptr() for c in cols])
+    sp = (ctypes.c_void_p * len(states))(*[st.tensor.data_ptr() for st in states])
+    _check(lib().repro_groupby_sum_cols(key1.data_ptr(), key2.data_ptr(), card2, ctypes.cast(cp, ctypes.c_void_p),
+                                        len(cols), key1.numel(), _dtype_code(dtype), L, num_groups,
+                                        ctypes.cast(sp, ctypes.c_void_p), _stream(cols[0].device)),
+           "repro_groupby_sum_cols")
+    return states
+
+
+def release_cached_memory():
+    _check(lib().repro_release_cached_memory(), "repro_release_cached_memory")

@@ -1,0 +1,36 @@
+// batch_plan.h -- host-side planning of a multi-task single-pass launch,
+// shared by repro_batch_prepare (repro_batch.cu) and the request server
+// (repro_serve.cu).  Not installed.
+#pragma once
+
+#include <vector>
+
+#include "multi_types.h"
+#include "repro.h"
+#include "repro_internal.h"
+
+namespace rp {
+
+// Bytes of one partial-table record: int32 K, uint32 flags, L 128-bit bins.
+constexpr size_t batch_rec_bytes(int L) { return 8 + 16 * (size_t)L; }
+
+struct HostBatch {
+    FusedPlanConfig cfg{};
+    int gcap = 1;                  // largest group table among the single-pass tasks
+    int ctas = 0;                  // CTAs of the persistent launch
+    std::vector<MTask> tasks;      // one per input task (index = task number)
+    std::vector<MItem> items;      // largest first
+    std::vector<MergeBlk> blks;    // partial-merge blocks of the tasks cut into several items
+    long long part_recs = 0;       // partial-table records the items write
+    std::vector<repro_task> slow;  // tasks outside the single-pass path (two-pass path)
+    long long slow_gmax = 0;
+};
+
+// Cut tasks into items: about four items per CTA, each at least 8 tiles and
+// at most 2^23 rows (no 64-bit table bin can overflow within an item); items
+// grow further while the partial tables would exceed max_part_bytes.
+// Validates the tasks (REPRO_EINVAL) and the table size (REPRO_ERANGE).
+repro_status plan_batch_host(const repro_task* tasks, int ntasks, int dtype, int L, size_t max_part_bytes,
+                             HostBatch& H);
+
+}  // namespace rp

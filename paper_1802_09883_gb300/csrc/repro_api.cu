@@ -48,7 +48,7 @@ static repro_status from_cuda(cudaError_t e) {
 // it on free and stays cached (release threshold = unlimited), so repeated
 // calls do not map and unmap multi-gigabyte scratch from the driver.
 // repro_release_cached_memory() hands the cached bytes back.
-static cudaMemPool_t library_pool(cudaError_t& err) {
+cudaMemPool_t library_pool(cudaError_t& err) {
     static cudaMemPool_t pools[64] = {};
     static std::mutex mu;
     int dev = 0;
@@ -85,9 +85,46 @@ struct Scratch {
     }
 };
 
+// Composite group id from two uint8 key columns: gid = k1 * card2 + k2, or -1
+// (an invalid key) when it falls outside [0, G).  Four rows per thread.
+__global__ void k_composite_keys(const uint8_t* __restrict__ k1, const uint8_t* __restrict__ k2, int card2,
+                                 long long n, long long G, int32_t* __restrict__ gid) {
+    const long long stride = 4ll * gridDim.x * blockDim.x;
+    for (long long i = 4ll * (blockIdx.x * (long long)blockDim.x + threadIdx.x); i < n; i += stride) {
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+            if (i + j < n) {
+                const long long g = (long long)k1[i + j] * card2 + k2[i + j];
+                gid[i + j] = g < G ? (int32_t)g : -1;
+            }
+    }
+}
+
+
 }  // namespace rp
 
 using namespace rp;
+
+namespace rp {
+
+int groupby_dispatch(const int32_t* keys, const void* values, long long n, int dtype, int L, long long num_groups,
+                     void* state, cudaStream_t s) {
+    if (n > 0 && fused_supported(dtype, L, num_groups, keys, values)) {
+        Scratch scratch(fused_scratch_bytes(dtype, L, num_groups, n), s);
+        if (scratch.err != cudaSuccess) return from_cuda(scratch.err);
+        return from_cuda(launch_groupby_fused(keys, values, n, dtype, L, num_groups, state, scratch.p, s));
+    }
+    if (n > 0 && partitioned_supported(dtype, L, num_groups, n, keys, values)) {
+        Scratch scratch(partitioned_scratch_bytes(dtype, L, num_groups, n), s);
+        if (scratch.err != cudaSuccess) return from_cuda(scratch.err);
+        return from_cuda(launch_groupby_partitioned(keys, values, n, dtype, L, num_groups, state, scratch.p, s));
+    }
+    Scratch scratch(two_pass_scratch_bytes(num_groups), s);
+    if (scratch.err != cudaSuccess) return from_cuda(scratch.err);
+    return from_cuda(launch_groupby_two_pass(keys, values, n, dtype, L, num_groups, state, scratch.p, s));
+}
+
+}  // namespace rp
 
 extern "C" {
 
@@ -108,20 +145,35 @@ repro_status repro_groupby_sum(const int32_t* keys, const void* values, int64_t 
     if (n > 0 && (!keys || !values)) return REPRO_EINVAL;
     if ((uintptr_t)state % 16 || (uintptr_t)keys % 4 || (uintptr_t)values % (dtype == REPRO_F64 ? 8 : 4))
         return REPRO_EINVAL;
+    return (repro_status)groupby_dispatch(keys, values, n, dtype, L, num_groups, state, (cudaStream_t)stream);
+}
+
+repro_status repro_groupby_sum_cols(const uint8_t* key1, const uint8_t* key2, int card2, const void* const* cols,
+                                    int ncols, int64_t n, repro_dtype dtype, int L, int64_t num_groups,
+                                    void* const* states, void* stream) {
+    if (!cols || !states || ncols < 1 || card2 < 1 || n < 0 || !valid_dtype(dtype) || !valid_shape(L, num_groups))
+        return REPRO_EINVAL;
+    if (n > 0 && (!key1 || !key2)) return REPRO_EINVAL;
+    for (int c = 0; c < ncols; ++c) {
+        if (!states[c] || (uintptr_t)states[c] % 16) return REPRO_EINVAL;
+        if (n > 0 && (!cols[c] || (uintptr_t)cols[c] % (dtype == REPRO_F64 ? 8 : 4))) return REPRO_EINVAL;
+    }
+    if (n == 0) return REPRO_OK;
     cudaStream_t s = (cudaStream_t)stream;
-    if (n > 0 && fused_supported(dtype, L, num_groups, keys, values)) {
-        Scratch scratch(fused_scratch_bytes(dtype, L, num_groups, n), s);
-        if (scratch.err != cudaSuccess) return from_cuda(scratch.err);
-        return from_cuda(launch_groupby_fused(keys, values, n, dtype, L, num_groups, state, scratch.p, s));
+    Scratch gid(sizeof(int32_t) * (size_t)n, s);
+    if (gid.err != cudaSuccess) return from_cuda(gid.err);
+    const int th = 256;
+    long long blocks = (n + 4ll * th - 1) / (4ll * th);
+    if (blocks > (long long)device_info().sms * 8) blocks = (long long)device_info().sms * 8;
+    k_composite_keys<<<(int)blocks, th, 0, s>>>(key1, key2, card2, n, num_groups, (int32_t*)gid.p);
+    count_launches(1);
+    if (cudaGetLastError() != cudaSuccess) return REPRO_ECUDA;
+    for (int c = 0; c < ncols; ++c) {
+        const repro_status st =
+            (repro_status)groupby_dispatch((const int32_t*)gid.p, cols[c], n, dtype, L, num_groups, states[c], s);
+        if (st != REPRO_OK) return st;
     }
-    if (n > 0 && partitioned_supported(dtype, L, num_groups, n, keys, values)) {
-        Scratch scratch(partitioned_scratch_bytes(dtype, L, num_groups, n), s);
-        if (scratch.err != cudaSuccess) return from_cuda(scratch.err);
-        return from_cuda(launch_groupby_partitioned(keys, values, n, dtype, L, num_groups, state, scratch.p, s));
-    }
-    Scratch scratch(two_pass_scratch_bytes(num_groups), s);
-    if (scratch.err != cudaSuccess) return from_cuda(scratch.err);
-    return from_cuda(launch_groupby_two_pass(keys, values, n, dtype, L, num_groups, state, scratch.p, s));
+    return REPRO_OK;
 }
 
 repro_status repro_merge(void* dst, const void* src, repro_dtype dtype, int L, int64_t num_groups, void* stream) {

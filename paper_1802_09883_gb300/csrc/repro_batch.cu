@@ -20,12 +20,17 @@
 #include <new>
 #include <vector>
 
+#include "batch_plan.h"
 #include "fused_device.cuh"
 #include "multi_types.h"
 #include "repro.h"
 #include "repro_internal.h"
 
 namespace rp {
+
+// Partial tables of one prepared plan are kept below 1 GiB where the work
+// allows (larger items otherwise).
+constexpr size_t kBatchPartBytes = 1ull << 30;
 
 namespace {
 
@@ -445,12 +450,88 @@ cudaError_t launch_merge_items(int L, int dtype, const void* tasks, const void* 
     return cudaGetLastError();
 }
 
+repro_status plan_batch_host(const repro_task* tasks, int ntasks, int dtype, int L, size_t max_part_bytes,
+                             HostBatch& H) {
+    if (ntasks < 0 || (ntasks > 0 && !tasks) || (dtype != REPRO_F64 && dtype != REPRO_F32) || L < 1 || L > 4)
+        return REPRO_EINVAL;
+    for (int t = 0; t < ntasks; ++t) {
+        const repro_task& k = tasks[t];
+        if (!k.state || k.n < 0 || k.num_groups < 1 || k.num_groups > INT32_MAX || (k.n > 0 && (!k.keys || !k.values)))
+            return REPRO_EINVAL;
+        if ((uintptr_t)k.state % 16 || (uintptr_t)k.keys % 4 || (uintptr_t)k.values % (dtype == REPRO_F64 ? 8 : 4))
+            return REPRO_EINVAL;
+    }
+    H = HostBatch{};
+    // single-pass tasks: aligned rows and a table that fits
+    std::vector<int> fast;
+    long long gcap = 1;
+    for (int t = 0; t < ntasks; ++t) {
+        const repro_task& k = tasks[t];
+        if (k.n == 0) continue;
+        if (fused_supported(dtype, L, k.num_groups, k.keys, k.values)) {
+            fast.push_back(t);
+            gcap = std::max(gcap, (long long)k.num_groups);
+        } else {
+            H.slow.push_back(k);
+            H.slow_gmax = std::max(H.slow_gmax, (long long)k.num_groups);
+        }
+    }
+    H.tasks.resize(ntasks);
+    for (int t = 0; t < ntasks; ++t)
+        H.tasks[t] = MTask{tasks[t].keys, tasks[t].values, tasks[t].n, (int)tasks[t].num_groups,
+                           (int)tasks[t].num_groups, (unsigned char*)tasks[t].state,
+                           (unsigned char*)tasks[t].state + sizeof(repro_state_header)};
+    if (fast.empty()) return REPRO_OK;
+    if (!fused_plan_config(dtype, L, (int)gcap, sizeof(StageMeta) * 4, H.cfg)) return REPRO_ERANGE;
+    H.gcap = (int)gcap;
+    const int R = H.cfg.R;
+    long long total_tiles = 0;
+    for (int t : fast) total_tiles += (tasks[t].n + R - 1) / R;
+    H.ctas = device_info().sms * H.cfg.ctas_per_sm;
+    const long long tpi_max = (1ll << 23) / R;
+    long long tpi = (total_tiles + 4ll * H.ctas - 1) / (4ll * H.ctas);
+    tpi = std::max(8ll, std::min(tpi, tpi_max));
+    auto part_records = [&](long long tp) {
+        long long part = 0;
+        for (int t : fast) {
+            const long long nit = ((tasks[t].n + R - 1) / R + tp - 1) / tp;
+            if (nit > 1) part += nit * tasks[t].num_groups;
+        }
+        return part;
+    };
+    while (tpi < tpi_max && (size_t)part_records(tpi) * batch_rec_bytes(L) > max_part_bytes)
+        tpi = std::min(tpi_max, 2 * tpi);
+    long long part = 0;
+    for (int t : fast) {
+        const long long ntile = (tasks[t].n + R - 1) / R;
+        const long long nit = (ntile + tpi - 1) / tpi;
+        const int G = (int)tasks[t].num_groups;
+        for (long long k = 0; k < nit; ++k) {
+            MItem it;
+            it.task = t;
+            it.excl = nit == 1;
+            it.row0 = k * tpi * R;
+            it.row1 = std::min<long long>(tasks[t].n, (k + 1) * tpi * R);
+            it.part = nit == 1 ? -1 : part + k * G;
+            H.items.push_back(it);
+        }
+        if (nit > 1) {
+            for (int g0 = 0; g0 < G; g0 += 32) H.blks.push_back(MergeBlk{t, g0, (int)nit, 0, part});
+            part += nit * G;
+        }
+    }
+    // largest items first: the dynamic schedule then balances the tail
+    std::stable_sort(H.items.begin(), H.items.end(),
+                     [](const MItem& x, const MItem& y) { return x.row1 - x.row0 > y.row1 - y.row0; });
+    H.part_recs = part;
+    return REPRO_OK;
+}
+
 struct BatchPlan {
     int dtype = 0, L = 0;
     FusedPlanConfig cfg{};
     int gcap_ = 1;
     int ctas = 0;
-    size_t smem = 0;
     int nitems = 0, nblks = 0;
     MTask* d_tasks = nullptr;
     MItem* d_items = nullptr;
@@ -474,96 +555,37 @@ extern "C" {
 
 repro_status repro_batch_prepare(const repro_task* tasks, int ntasks, repro_dtype dtype, int L,
                                  repro_batch_plan* out) {
-    if (!out || ntasks < 0 || (ntasks > 0 && !tasks) || (dtype != REPRO_F64 && dtype != REPRO_F32) || L < 1 ||
-        L > 4)
-        return REPRO_EINVAL;
+    if (!out) return REPRO_EINVAL;
     *out = nullptr;
-    for (int t = 0; t < ntasks; ++t) {
-        const repro_task& k = tasks[t];
-        if (!k.state || k.n < 0 || k.num_groups < 1 || k.num_groups > INT32_MAX || (k.n > 0 && (!k.keys || !k.values)))
-            return REPRO_EINVAL;
-        if ((uintptr_t)k.state % 16 || (uintptr_t)k.keys % 4 || (uintptr_t)k.values % (dtype == REPRO_F64 ? 8 : 4))
-            return REPRO_EINVAL;
-    }
+    HostBatch H;
+    repro_status st = plan_batch_host(tasks, ntasks, dtype, L, kBatchPartBytes, H);
+    if (st != REPRO_OK) return st;
     repro_batch_plan_s* plan = new (std::nothrow) repro_batch_plan_s;
     if (!plan) return REPRO_ENOMEM;
     BatchPlan& P = plan->p;
     P.dtype = dtype;
     P.L = L;
-    // single-pass tasks: aligned rows and a table that fits
-    std::vector<int> fast;
-    long long gcap = 1, total_tiles = 0, slow_gmax = 0;
-    for (int t = 0; t < ntasks; ++t) {
-        const repro_task& k = tasks[t];
-        if (k.n == 0) continue;
-        if (fused_supported(dtype, L, k.num_groups, k.keys, k.values)) {
-            fast.push_back(t);
-            gcap = std::max(gcap, (long long)k.num_groups);
-        } else {
-            P.slow.push_back(k);
-            slow_gmax = std::max(slow_gmax, (long long)k.num_groups);
-        }
-    }
-    repro_status st = REPRO_OK;
-    if (!fast.empty()) {
-        if (!fused_plan_config(dtype, L, (int)gcap, sizeof(StageMeta) * 4, P.cfg)) {
-            delete plan;
-            return REPRO_ERANGE;
-        }
-        const int R = P.cfg.R;
-        for (int t : fast) total_tiles += (tasks[t].n + R - 1) / R;
-        P.ctas = device_info().sms * P.cfg.ctas_per_sm;
-        // autotuned item size: about four items per CTA, at least 8 tiles,
-        // at most 2^23 rows (no int64 table bin can overflow within an item)
-        long long tpi = (total_tiles + 4ll * P.ctas - 1) / (4ll * P.ctas);
-        tpi = std::max(8ll, std::min(tpi, (1ll << 23) / R));
-        std::vector<MTask> htasks(ntasks);
-        for (int t = 0; t < ntasks; ++t)
-            htasks[t] = MTask{tasks[t].keys, tasks[t].values, tasks[t].n, (int)tasks[t].num_groups,
-                              (int)tasks[t].num_groups, (unsigned char*)tasks[t].state,
-                              (unsigned char*)tasks[t].state + sizeof(repro_state_header)};
-        std::vector<MItem> items;
-        std::vector<MergeBlk> blks;
-        long long part = 0;
-        for (int t : fast) {
-            const long long ntile = (tasks[t].n + R - 1) / R;
-            const long long nit = (ntile + tpi - 1) / tpi;
-            const int G = (int)tasks[t].num_groups;
-            for (long long k = 0; k < nit; ++k) {
-                MItem it;
-                it.task = t;
-                it.excl = nit == 1;
-                it.row0 = k * tpi * R;
-                it.row1 = std::min<long long>(tasks[t].n, (k + 1) * tpi * R);
-                it.part = nit == 1 ? -1 : part + k * G;
-                items.push_back(it);
-            }
-            if (nit > 1) {
-                for (int g0 = 0; g0 < G; g0 += 32) blks.push_back(MergeBlk{t, g0, (int)nit, 0, part});
-                part += nit * G;
-            }
-        }
-        // largest items first: the dynamic schedule then balances the tail
-        std::stable_sort(items.begin(), items.end(),
-                         [](const MItem& x, const MItem& y) { return x.row1 - x.row0 > y.row1 - y.row0; });
-        P.nitems = (int)items.size();
-        P.nblks = (int)blks.size();
-        P.smem = 0;
+    P.cfg = H.cfg;
+    P.gcap_ = H.gcap;
+    P.ctas = H.ctas;
+    P.slow = H.slow;
+    P.nitems = (int)H.items.size();
+    P.nblks = (int)H.blks.size();
+    if (P.nitems > 0) {
         cudaError_t e = cudaMalloc(&P.d_tasks, sizeof(MTask) * std::max(1, ntasks));
-        if (e == cudaSuccess) e = cudaMalloc(&P.d_items, sizeof(MItem) * std::max(1, P.nitems));
+        if (e == cudaSuccess) e = cudaMalloc(&P.d_items, sizeof(MItem) * P.nitems);
         if (e == cudaSuccess) e = cudaMalloc(&P.d_blks, sizeof(MergeBlk) * std::max(1, P.nblks));
-        if (e == cudaSuccess) e = cudaMalloc(&P.d_partials, std::max<size_t>(16, (size_t)part * (8 + 16 * (size_t)L)));
+        if (e == cudaSuccess) e = cudaMalloc(&P.d_partials, std::max<size_t>(16, (size_t)H.part_recs * batch_rec_bytes(L)));
         if (e == cudaSuccess) e = cudaMalloc(&P.d_counter, sizeof(int));
-        if (e == cudaSuccess) e = cudaMemcpy(P.d_tasks, htasks.data(), sizeof(MTask) * ntasks, cudaMemcpyHostToDevice);
-        if (e == cudaSuccess && P.nitems)
-            e = cudaMemcpy(P.d_items, items.data(), sizeof(MItem) * P.nitems, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(P.d_tasks, H.tasks.data(), sizeof(MTask) * ntasks, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess)
+            e = cudaMemcpy(P.d_items, H.items.data(), sizeof(MItem) * P.nitems, cudaMemcpyHostToDevice);
         if (e == cudaSuccess && P.nblks)
-            e = cudaMemcpy(P.d_blks, blks.data(), sizeof(MergeBlk) * P.nblks, cudaMemcpyHostToDevice);
+            e = cudaMemcpy(P.d_blks, H.blks.data(), sizeof(MergeBlk) * P.nblks, cudaMemcpyHostToDevice);
         if (e != cudaSuccess) st = e == cudaErrorMemoryAllocation ? REPRO_ENOMEM : REPRO_ECUDA;
-        P.gcap_ = (int)gcap;
     }
     if (st == REPRO_OK && !P.slow.empty()) {
-        if (cudaMalloc(&P.d_slow_scratch, two_pass_scratch_bytes(slow_gmax)) != cudaSuccess) st = REPRO_ENOMEM;
+        if (cudaMalloc(&P.d_slow_scratch, two_pass_scratch_bytes(H.slow_gmax)) != cudaSuccess) st = REPRO_ENOMEM;
     }
     if (st != REPRO_OK) {
         repro_batch_destroy(plan);

@@ -19,6 +19,15 @@ struct DeviceInfo {
 // Properties of the current device (queried once per device).
 const DeviceInfo& device_info();
 
+// The library's stream-ordered memory pool on the current device (cached:
+// freed blocks stay with the pool until repro_release_cached_memory).
+cudaMemPool_t library_pool(cudaError_t& err);
+
+// One accumulation into a state: the single-pass path when its table fits,
+// else the partitioned path, else the two-pass path (returns a repro_status).
+int groupby_dispatch(const int32_t* keys, const void* values, long long n, int dtype, int L, long long num_groups,
+                     void* state, cudaStream_t s);
+
 // Profiling hooks (repro_profile_enable / repro_profile_read) and the launch
 // counter (repro_launch_count).
 enum ProfKernel { PROF_WINDOW, PROF_ACCUM, PROF_FUSED, PROF_PARTITION, PROF_MERGE, PROF_FINALIZE, PROF_FP64,

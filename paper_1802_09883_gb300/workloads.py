@@ -127,3 +127,71 @@ def few_groups_multicol(n: int = 60_000_000, seed: int = 2, device="cpu") -> Tup
     d = torch.randint(0, 11, (n,), generator=g, device=device, dtype=torch.int64).to(torch.float64) / 100
     cols = torch.stack([p, d, p * (1 - d), p * d])
     return k1, k2, cols
+
+
+def log_uniform_ints(m: int, lo: float, hi: float, gen, device="cpu") -> torch.Tensor:
+    """m integers round(10^U) with U uniform in [log10 lo, log10 hi]."""
+    import math
+    u = torch.rand(m, generator=gen, device=device, dtype=torch.float64)
+    x = torch.pow(10.0, math.log10(lo) + u * (math.log10(hi) - math.log10(lo)))
+    return x.round().clamp_(lo, hi).to(torch.int64)
+
+
+def batched_tasks(num_tasks: int = 4096, seed: int = 3, rows=(1e3, 1e7), groups=(1, 1e5), device="cpu",
+                  dtype=torch.float64, e_lo: int = -10, e_hi: int = 10):
+    """Independent aggregations: rows and group counts log-uniform in the
+    given ranges, keys uniform over each task's groups, values as in plain().
+    Returns a list of (keys, values, G)."""
+    g = _gen(seed, device)
+    n = log_uniform_ints(num_tasks, rows[0], rows[1], g, device).tolist()
+    G = log_uniform_ints(num_tasks, groups[0], groups[1], g, device).tolist()
+    out = []
+    for i in range(num_tasks):
+        keys = uniform_keys(n[i], G[i], g, device)
+        vals = random_values(n[i], e_lo, e_hi, g, device, dtype)
+        out.append((keys, vals, int(G[i])))
+    return out
+
+
+@dataclass
+class ServingTable:
+    """A resident table the queries of a serving trace scan: one int32 key
+    column per group-count level (keys uniform over that many groups) and one
+    value column, all max_rows long."""
+    keys: torch.Tensor      # int32[levels, max_rows]
+    values: torch.Tensor    # float64[max_rows] (or float32)
+    groups: Tuple[int, ...]
+
+    def query(self, start: int, rows: int, level: int):
+        return self.keys[level, start:start + rows], self.values[start:start + rows], self.groups[level]
+
+
+def serving_table(max_rows: int, groups=(1, 1e6), levels: int = 25, seed: int = 4, device="cpu",
+                  dtype=torch.float64) -> ServingTable:
+    """Key columns for `levels` group counts log-spaced over `groups`
+    (round(10^x)), values as in plain()."""
+    import math
+    lo, hi = math.log10(groups[0]), math.log10(groups[1])
+    Gs = tuple(sorted({int(round(10 ** (lo + (hi - lo) * i / max(1, levels - 1)))) for i in range(levels)}))
+    g = _gen(seed, device)
+    keys = torch.empty((len(Gs), max_rows), dtype=torch.int32, device=device)
+    for i, G in enumerate(Gs):
+        keys[i] = uniform_keys(max_rows, G, g, device)
+    vals = random_values(max_rows, -10, 10, g, device, dtype)
+    return ServingTable(keys, vals, Gs)
+
+
+def serving_trace(num_requests: int, table: ServingTable, rows=(1e4, 1e8), seed: int = 4):
+    """Queries over `table`: rows log-uniform in `rows`, group count drawn
+    log-uniformly among the table's levels, a random start (a multiple of 4
+    rows, so every slice keeps 16-byte alignment), and unit-mean exponential
+    inter-arrival gaps (scale them by 1/lambda).  Returns (queries, gaps) with
+    queries a list of (start, rows, level)."""
+    g = _gen(seed, "cpu")
+    max_rows = table.values.numel()
+    n = log_uniform_ints(num_requests, rows[0], min(rows[1], max_rows), g).tolist()
+    lvl = torch.randint(0, len(table.groups), (num_requests,), generator=g).tolist()
+    u = torch.rand(num_requests, generator=g, dtype=torch.float64)
+    start = [int(float(u[i]) * (max_rows - n[i])) // 4 * 4 for i in range(num_requests)]
+    gaps = (-torch.log1p(-torch.rand(num_requests, generator=g, dtype=torch.float64))).tolist()
+    return [(start[i], int(n[i]), int(lvl[i])) for i in range(num_requests)], gaps

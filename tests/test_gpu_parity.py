@@ -349,3 +349,29 @@ def test_partitioned_path_small_inputs_with_idle_ctas(n):
     ost, _ = oracle_state(_np(w.keys), _np(w.values), G, L, threads=1)
     assert_state_equal(st, ost)
     assert_bits_equal(_np(out), O.finalize(ost))
+
+
+# ------------------------------------------- few groups, several columns
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+def test_multicolumn_composite_keys_match_oracle(dtype):
+    k1, k2, cols = WL.few_groups_multicol(n=2_000_003, seed=2, device=DEV)
+    cols = cols.to(dtype)
+    states = R.groupby_sum_cols(k1, k2, 2, list(cols), num_groups=4, L=3)
+    gid = (2 * _np(k1).astype(np.int32) + _np(k2).astype(np.int32))
+    for c, st in enumerate(states):
+        assert st.check() == 0
+        ost, _ = oracle_state(gid, _np(cols[c]), 4, 3)
+        assert_state_equal(st, ost)
+        assert_bits_equal(_np(st.finalize()), O.finalize(ost))
+
+
+def test_multicolumn_bad_composite_keys_flag_every_state():
+    k1 = torch.tensor([0, 1, 3, 0], dtype=torch.uint8, device=DEV)
+    k2 = torch.tensor([1, 1, 1, 0], dtype=torch.uint8, device=DEV)
+    cols = [torch.tensor([1.0, 2.0, 3.0, 4.0], dtype=torch.float64, device=DEV) for _ in range(2)]
+    states = R.groupby_sum_cols(k1, k2, 2, cols, num_groups=4, L=2)
+    for st in states:
+        with pytest.raises(R.ReproError):
+            st.check()
+        assert _np(st.finalize()).tolist() == [4.0, 1.0, 0.0, 2.0]
