@@ -196,6 +196,14 @@ class State:
                                     _stream(self.device)), "repro_finalize")
         return out
 
+    def error_word(self) -> int:
+        """Synchronise and return the state's error word (REPRO_ERR_* bits)."""
+        err = ctypes.c_uint32(0)
+        st = lib().repro_state_check(self.tensor.data_ptr(), ctypes.byref(err), _stream(self.device))
+        if st not in (0, 2, 6, 7):
+            _check(st, "repro_state_check")
+        return err.value
+
     def check(self) -> int:
         """Synchronise and raise ReproError if a data error was recorded."""
         err = ctypes.c_uint32(0)
