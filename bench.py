@@ -47,6 +47,13 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--verify", action="store_true", help="check sampled groups against the oracle")
+    ap.add_argument("--workload", default="sweep", choices=["sweep", "multicol", "batched", "serve"],
+                    help="sweep: one grouped SUM (default); multicol: 4 SUM columns over two uint8 keys; "
+                         "batched: many aggregations in one launch; serve: the request server")
+    ap.add_argument("--dtype", default="f64", choices=["f64", "f32"], help="multicol value type")
+    ap.add_argument("--rows", type=int, default=0, help="multicol rows / serve table rows (0: default)")
+    ap.add_argument("--tasks", type=int, default=4096, help="batched: number of aggregations")
+    ap.add_argument("--requests", type=int, default=2000, help="serve: queries per trace")
     return ap.parse_args()
 
 
@@ -334,6 +341,293 @@ def load_peaks():
         return {"hbm_gbs": 6800.0, "source": "fallback 6.8 TB/s"}
 
 
+# ------------------------------------------------------- secondary workloads
+
+PROF_NAMES = ("accum", "window", "fused", "partition", "merge", "finalize")
+
+
+def _prof_start(lib):
+    lib.repro_profile_enable(1)
+    for name in PROF_NAMES:
+        lib.repro_profile_read(name.encode(), None, None)
+
+
+def _prof_stop(lib):
+    prof = {}
+    for name in PROF_NAMES:
+        t = ctypes.c_double(0)
+        c = ctypes.c_int64(0)
+        lib.repro_profile_read(name.encode(), ctypes.byref(t), ctypes.byref(c))
+        if c.value:
+            prof[name] = {"ms_per_launch": t.value / c.value, "launches": c.value, "ms_total": t.value}
+    lib.repro_profile_enable(0)
+    return prof
+
+
+def _time(fn, steps, stream):
+    import torch
+
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / steps
+
+
+def _base_line(args, metric, value, unit, ms, dtype, workload, extra_cfg):
+    return {"metric": metric, "value": value, "unit": unit, "n_gpus": 1, "steps": args.steps,
+            "warmup": max(args.warmup, 3), "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": dtype, "data": "synthetic",
+            "config": dict({"workload": workload}, **extra_cfg)}
+
+
+def run_multicol(args, local_rank):
+    """Few-group multi-column aggregate: SUM of 4 columns GROUP BY two uint8
+    keys (4 groups), repro<T,3>; one step = reset, aggregate, finalize."""
+    import torch
+
+    import paper_1802_09883_gb300 as R
+    from paper_1802_09883_gb300 import workloads as WL
+
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    lib = R.lib()
+    n = args.rows or 60_000_000
+    dt = torch.float64 if args.dtype == "f64" else torch.float32
+    esz = 8 if dt == torch.float64 else 4
+    k1, k2, cols = WL.few_groups_multicol(n=n, seed=2, device=dev)
+    cols = cols.to(dt).contiguous()
+    colsl = list(cols)
+    G, L = 4, 3
+    states = [R.State(G, L, dt, device=dev) for _ in colsl]
+    outs = [torch.empty(G, dtype=dt, device=dev) for _ in colsl]
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        for st in states:
+            st.reset()
+        R.groupby_sum_cols(k1, k2, 2, colsl, G, L, states=states)
+        for st, o in zip(states, outs):
+            st.finalize(o)
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    for st in states:
+        st.check()
+    clocks = ClockSampler(local_rank)
+    _prof_start(lib)
+    l0 = lib.repro_launch_count()
+    clocks.start()
+    ms = _time(step, args.steps, stream)
+    clocks.stop()
+    launches = lib.repro_launch_count() - l0
+    prof = _prof_stop(lib)
+    # conventional GroupBy on the same rows (group ids precomputed, untimed)
+    gid = (k1.to(torch.int32) * 2 + k2.to(torch.int32)).contiguous()
+    fp_outs = [torch.empty(G, dtype=dt, device=dev) for _ in colsl]
+    fp = R.groupby_sum_fp64 if dt == torch.float64 else R.groupby_sum_fp32
+
+    def fp_step():
+        for c, o in zip(colsl, fp_outs):
+            fp(gid, c, G, out=o)
+
+    fp_step()
+    fp_ms = _time(fp_step, args.steps, stream)
+    # end to end from pinned host buffers
+    k1h, k2h = k1.cpu().pin_memory(), k2.cpu().pin_memory()
+    colsh = cols.cpu().pin_memory()
+    outs_h = torch.empty((len(colsl), G), dtype=dt, pin_memory=True)
+    k1d, k2d, colsd = torch.empty_like(k1), torch.empty_like(k2), torch.empty_like(cols)
+    colsdl = list(colsd)
+
+    def e2e_step():
+        k1d.copy_(k1h, non_blocking=True)
+        k2d.copy_(k2h, non_blocking=True)
+        colsd.copy_(colsh, non_blocking=True)
+        for st in states:
+            st.reset()
+        R.groupby_sum_cols(k1d, k2d, 2, colsdl, G, L, states=states)
+        for i, (st, o) in enumerate(zip(states, outs)):
+            st.finalize(o)
+            outs_h[i].copy_(o, non_blocking=True)
+
+    e2e_step()
+    e2e_ms = _time(e2e_step, args.steps, stream)
+    for o, oh in zip(outs, outs_h):
+        assert torch.equal(o.cpu(), oh)
+    peaks = load_peaks()
+    fused = prof.get("fused")
+    roof = None
+    if fused:
+        per_launch = n * (4 + esz)  # the fused pass reads one group id and one value per row
+        ach = per_launch / (fused["ms_per_launch"] / 1e3) / 1e9
+        roof = {"bound": "hbm", "kernel": "fused", "achieved": round(ach, 1), "peak": peaks["hbm_gbs"],
+                "unit": "GB/s", "frac": round(ach / peaks["hbm_gbs"], 4), "traffic": None,
+                "peak_source": peaks["source"], "ms_per_launch": fused["ms_per_launch"],
+                "launches_per_step": fused["launches"] / args.steps}
+    algo = n * (2 + 4 * esz) + 4 * G * esz
+    res = _base_line(args, "repro multi-column GroupBy-SUM rows/s (4 SUM columns, 4 groups)", n / (ms / 1e3),
+                     "rows/s", ms, args.dtype,
+                     f"few-group multi-column aggregate, {n} rows, 2 uint8 keys -> 4 groups, 4 SUM columns, "
+                     f"repro<{'double' if esz == 8 else 'float'},3>",
+                     {"n": n, "G": G, "L": L, "columns": 4, "l2": "inputs far larger than L2; no flush"})
+    res.update({"hbm_gbs_algorithmic": algo / (ms / 1e3) / 1e9, "roofline": roof, "kernels": prof,
+                "fp64_baseline": {"kind": "fp64" if esz == 8 else "fp32", "ms_per_step": fp_ms,
+                                  "repro_over_fp_time": ms / fp_ms},
+                "e2e": {"value": n / (e2e_ms / 1e3), "unit": "rows/s", "h2d_bytes_per_step": n * (2 + 4 * esz),
+                        "d2h_bytes_per_step": 4 * G * esz, "ms_per_step": e2e_ms},
+                "gpu_launches": int(launches), "clocks": clocks.summary()})
+    return res
+
+
+def run_batched(args, local_rank):
+    """Many independent aggregations in one persistent launch, replayed from
+    a CUDA graph: one step = reset all states, aggregate, finalize all."""
+    import torch
+
+    import paper_1802_09883_gb300 as R
+    from paper_1802_09883_gb300 import workloads as WL
+
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    lib = R.lib()
+    L = 3
+    t_gen = time.time()
+    tasks = WL.batched_tasks(args.tasks, seed=3, device=dev)
+    torch.cuda.synchronize()
+    t_gen = time.time() - t_gen
+    rows = sum(int(k.numel()) for k, _, _ in tasks)
+    groups = sum(G for _, _, G in tasks)
+    states = [R.State(G, L, torch.float64, device=dev) for _, _, G in tasks]
+    outs = [torch.empty(G, dtype=torch.float64, device=dev) for _, _, G in tasks]
+    t_plan = time.time()
+    plan = R.BatchPlan([(k, v, st) for (k, v, _), st in zip(tasks, states)])
+    plan.set_outputs(outs)
+    t_plan = time.time() - t_plan
+    side = torch.cuda.Stream(dev)
+    side.wait_stream(torch.cuda.current_stream(dev))
+    with torch.cuda.stream(side):
+        l0 = lib.repro_launch_count()
+        plan.reset().run().finalize()  # eager warm-up; counts the launches of one step
+        torch.cuda.synchronize()
+        per_step_launches = lib.repro_launch_count() - l0
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph, stream=side):
+            plan.reset().run().finalize()
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream(dev)
+    for _ in range(max(args.warmup, 3)):
+        graph.replay()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local_rank)
+    clocks.start()
+    ms = _time(graph.replay, args.steps, stream)
+    clocks.stop()
+    # bit-equality of a sample of tasks against the one-task path
+    sample = list(range(0, len(tasks), max(1, len(tasks) // 16)))
+    same = all(torch.equal(outs[i].view(torch.int64),
+                           R.groupby_sum(tasks[i][0], tasks[i][1], tasks[i][2], L).view(torch.int64))
+               for i in sample)
+    # per-kernel times from one eager step with the profiler on
+    with torch.cuda.stream(side):
+        _prof_start(lib)
+        plan.reset().run().finalize()
+        torch.cuda.synchronize()
+        prof = _prof_stop(lib)
+    # conventional FP64 GroupBy over the same tasks, one call each
+    fp_outs = [torch.empty(G, dtype=torch.float64, device=dev) for _, _, G in tasks]
+
+    def fp_step():
+        for (k, v, G), o in zip(tasks, fp_outs):
+            R.groupby_sum_fp64(k, v, G, out=o)
+
+    fp_step()
+    fp_ms = _time(fp_step, max(1, args.steps // 4), stream)
+    peaks = load_peaks()
+    algo = rows * 12 + groups * 8
+    ach = algo / (ms / 1e3) / 1e9
+    slow = sum(1 for _, _, G in tasks if G > 9000)
+    res = _base_line(args, "repro batched GroupBy-SUM rows/s (independent aggregations, one graph replay)",
+                     rows / (ms / 1e3), "rows/s", ms, "f64",
+                     f"batched: {len(tasks)} aggregations, rows log-uniform 1e3-1e7, groups log-uniform 1-1e5, "
+                     f"repro<double,3>, values as the plain config", 
+                     {"tasks": len(tasks), "rows": rows, "groups": groups, "L": L,
+                      "l2": f"inputs {rows * 12 / 1e9:.1f} GB, far larger than L2; no flush"})
+    res.update({"hbm_gbs_algorithmic": ach,
+                "roofline": {"bound": "hbm", "kernel": "whole step (graph replay)", "achieved": round(ach, 1),
+                             "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": round(ach / peaks["hbm_gbs"], 4),
+                             "traffic": None, "peak_source": peaks["source"]},
+                "kernels": prof, "fp64_baseline": {"ms_per_step": fp_ms, "repro_over_fp64_time": ms / fp_ms,
+                                                   "kind": "one groupby_sum_fp64 call per task"},
+                "e2e": None, "e2e_note": "inputs of this workload are generated on the device (tens of GB)",
+                "gpu_launches": int(per_step_launches * args.steps), "clocks": clocks.summary(),
+                "verify": {"tasks_checked": len(sample), "bit_equal_to_single_task": bool(same)},
+                "plan": {"prepare_s": t_plan, "tasks_beyond_smem_table": slow, "generate_s": t_gen}})
+    plan.close()
+    return res
+
+
+def run_serve(args, local_rank):
+    """Request server under Poisson arrivals: capacity from a closed-loop
+    trace, then latency at 0.5 / 0.7 / 0.9 of that rate."""
+    import numpy as np
+    import torch
+
+    import paper_1802_09883_gb300 as R
+    from paper_1802_09883_gb300 import serve as S
+    from paper_1802_09883_gb300 import workloads as WL
+
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    lib = R.lib()
+    max_rows = args.rows or 100_000_000
+    table = WL.serving_table(max_rows, groups=(1, 1e6), levels=25, seed=4, device=dev)
+    trace, gaps = WL.serving_trace(args.requests, table, rows=(1e4, 1e8), seed=4)
+    queries = [table.query(*q) for q in trace]
+    rows = sum(int(q[0].numel()) for q in queries)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local_rank)
+    with S.Server(chunk_rows=1 << 24, max_active=256) as srv:
+        S.run_trace(srv, queries[:64], [0.0] * 64)  # warm-up
+        l0 = lib.repro_launch_count()
+        clocks.start()
+        closed = S.run_trace(srv, queries, [0.0] * len(queries))
+        rate = len(queries) / closed["span_s"]
+        open_runs = {}
+        for frac in (0.5, 0.7, 0.9):
+            arr = np.cumsum(gaps) / (frac * rate)
+            r = S.run_trace(srv, queries, arr)
+            open_runs[str(frac)] = {k: r[k] for k in ("p50_ms", "p99_ms", "mean_ms", "max_ms", "rows_per_s",
+                                                       "span_s")}
+        clocks.stop()
+        launches = lib.repro_launch_count() - l0
+        stats = srv.stats()
+        # a sample of results in the mix vs each query alone
+        sample = list(range(0, len(queries), max(1, len(queries) // 12)))
+        mix = S.run_trace(srv, [queries[i] for i in sample], [0.0] * len(sample), keep_results=True)
+    same = all(torch.equal(o.view(torch.int64), R.groupby_sum(*queries[i]).cpu().view(torch.int64))
+               for i, o in zip(sample, mix["results"]))
+    res = _base_line(args, "repro serving rows/s (closed loop) with p50/p99 latency under Poisson arrivals",
+                     closed["rows_per_s"], "rows/s", closed["span_s"] * 1e3, "f64",
+                     f"serving: {len(queries)} queries, rows log-uniform 1e4-1e8, groups log-uniform 1-1e6 "
+                     f"(25 levels), repro<double,3>, results to pinned host memory",
+                     {"requests": len(queries), "rows": rows, "table_rows": max_rows, "L": 3,
+                      "chunk_rows": 1 << 24, "l2": "queries scan a 10 GB resident table; no flush"})
+    res.update({"serving": {"capacity_requests_per_s": rate, "closed_loop": {k: closed[k] for k in (
+                    "p50_ms", "p99_ms", "mean_ms", "rows_per_s", "span_s")}, "poisson": open_runs,
+                    "server": {k: stats[k] for k in ("iterations", "batch_launches", "large_calls",
+                                                     "memory_peak", "memory_budget")}},
+                "verify": {"queries_checked": len(sample), "bit_equal_alone_and_in_mix": bool(same)},
+                "e2e": {"value": closed["rows_per_s"], "unit": "rows/s", "h2d_bytes_per_step": 0,
+                        "d2h_bytes_per_step": sum(q[2] for q in queries) * 8,
+                        "note": "queries scan a device-resident table; each result is copied to host"},
+                "gpu_launches": int(launches), "clocks": clocks.summary(), "roofline": None})
+    return res
+
+
 # -------------------------------------------------------- CPU oracle timing
 
 def cpu_oracle_rate(G, dist, L, rows, threads):
@@ -409,6 +703,11 @@ def main():
         res = run_reference(args, rank)
         if res is not None:
             print(json.dumps(res), flush=True)
+        return
+    if args.workload != "sweep":
+        if rank == 0:
+            fn = {"multicol": run_multicol, "batched": run_batched, "serve": run_serve}[args.workload]
+            print(json.dumps(fn(args, local_rank)), flush=True)
         return
     res = run_ours(args, rank, world, local_rank)
     if rank == 0:

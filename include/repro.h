@@ -186,8 +186,9 @@ repro_status repro_groupby_sum_noalloc(const int32_t* keys, const void* values, 
  * single-pass path share the persistent launch: the plan cuts them into
  * work items of whole tiles (the item size is tuned to the batch: about four
  * items per CTA, at most 2^23 rows), largest first; an item that covers a
- * whole task merges straight into its state.  Other tasks run through the
- * two-pass path, one after the other, inside repro_batch_run.
+ * whole task merges straight into its state.  Other tasks run one after
+ * the other inside repro_batch_run: through the partitioned path (large
+ * group counts), or the two-pass path (rows not 16-byte aligned).
  * All tasks use the same dtype and L; states must not overlap.
  */
 typedef struct {
@@ -204,6 +205,18 @@ repro_status repro_batch_prepare(const repro_task* tasks, int ntasks, repro_dtyp
                                  repro_batch_plan* plan);
 repro_status repro_batch_run(repro_batch_plan plan, void* stream);
 repro_status repro_batch_destroy(repro_batch_plan plan);
+/* Re-initialise every task's state (one launch; capturable). */
+repro_status repro_batch_reset(repro_batch_plan plan, void* stream);
+
+/* Give the plan one output per task (HOST array of ntasks DEVICE pointers to
+   num_groups elements of the dtype, or NULL to skip a task); copied to the
+   device synchronously, like repro_batch_prepare. */
+repro_status repro_batch_set_outputs(repro_batch_plan plan, void* const* outs);
+
+/* Finalize every task with an output into it (one launch; capturable).
+   REPRO_EINVAL before repro_batch_set_outputs. */
+repro_status repro_batch_finalize(repro_batch_plan plan, void* stream);
+
 repro_status repro_groupby_sum_batched(const repro_task* tasks, int ntasks, repro_dtype dtype, int L,
                                        void* stream);
 

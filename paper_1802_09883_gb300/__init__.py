@@ -79,6 +79,9 @@ def lib(build_if_stale: bool = True):
         L.repro_batch_prepare.argtypes = [vp, i32, i32, i32, ctypes.POINTER(vp)]
         L.repro_batch_run.argtypes = [vp, vp]
         L.repro_batch_destroy.argtypes = [vp]
+        L.repro_batch_reset.argtypes = [vp, vp]
+        L.repro_batch_set_outputs.argtypes = [vp, vp]
+        L.repro_batch_finalize.argtypes = [vp, vp]
         L.repro_groupby_sum_batched.argtypes = [vp, i32, i32, i32, vp]
         L.repro_groupby_sum_cols.argtypes = [vp, vp, i32, vp, i32, i64, i32, i32, i64, vp, vp]
         L.repro_release_cached_memory.argtypes = []
@@ -97,6 +100,7 @@ def lib(build_if_stale: bool = True):
         L.repro_server_destroy.argtypes = [vp]
         for name in ("repro_state_init", "repro_groupby_sum", "repro_groupby_sum_noalloc", "repro_merge",
                      "repro_finalize", "repro_batch_prepare", "repro_batch_run", "repro_batch_destroy",
+                     "repro_batch_reset", "repro_batch_set_outputs", "repro_batch_finalize",
                      "repro_groupby_sum_batched", "repro_groupby_sum_cols", "repro_release_cached_memory",
                      "repro_state_check", "groupby_sum_fp64", "groupby_sum_fp32", "repro_server_create",
                      "repro_server_submit", "repro_server_poll", "repro_server_wait", "repro_server_release",
@@ -298,6 +302,33 @@ class BatchPlan:
 
     def run(self):
         _check(lib().repro_batch_run(self._plan, _stream(self.device)), "repro_batch_run")
+        return self
+
+    def reset(self):
+        """Re-initialise every task's state in one launch."""
+        _check(lib().repro_batch_reset(self._plan, _stream(self.device)), "repro_batch_reset")
+        return self
+
+    def set_outputs(self, outs):
+        """One device tensor (num_groups of the dtype) or None per task."""
+        if len(outs) != len(self._keep):
+            raise ValueError("one output per task")
+        ptrs = (ctypes.c_void_p * len(outs))()
+        for i, (o, (_, _, st)) in enumerate(zip(outs, self._keep)):
+            if o is None:
+                continue
+            _require_cuda(o, "out")
+            if o.dtype != self.dtype or o.numel() < st.G or not o.is_contiguous():
+                raise ValueError("output %d: contiguous, the batch dtype, num_groups elements" % i)
+            ptrs[i] = o.data_ptr()
+        _check(lib().repro_batch_set_outputs(self._plan, ctypes.cast(ptrs, ctypes.c_void_p)),
+               "repro_batch_set_outputs")
+        self._outs = list(outs)
+        return self
+
+    def finalize(self):
+        """Finalize every task with an output, in one launch."""
+        _check(lib().repro_batch_finalize(self._plan, _stream(self.device)), "repro_batch_finalize")
         return self
 
     def close(self):

@@ -9,7 +9,8 @@
 // owns the whole task) or write it as a partial that k_merge_items folds in
 // afterwards (operator+=(repro), Algorithm 4's merge).  Tasks the single-pass
 // table cannot hold (large G) or whose rows are not 16-byte aligned run
-// through the two-pass path.  repro_batch_run only launches kernels and
+// through the partitioned path (or, unaligned, the two-pass path).
+// repro_batch_run only launches kernels and
 // copies nothing from the host, so it can be captured in a CUDA graph.
 #include <cuda_runtime.h>
 
@@ -527,12 +528,39 @@ repro_status plan_batch_host(const repro_task* tasks, int ntasks, int dtype, int
     return REPRO_OK;
 }
 
+// One launch re-initialises every task's state (grid.y = task).
+__global__ void k_batch_init(const MTask* __restrict__ tasks, int task0, int dtype, int L) {
+    const MTask t = tasks[task0 + blockIdx.y];
+    const StateView st{t.hdr, L, t.G_hdr};
+    if (blockIdx.x == 0 && threadIdx.x == 0) state_init_header(st, dtype);
+    for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < t.G_hdr;
+         g += (long long)gridDim.x * blockDim.x)
+        state_init_group(st, g);
+}
+
+// One launch finalizes every task with an output (eq. (1) per group).
+template <typename T>
+__global__ void k_batch_finalize(const MTask* __restrict__ tasks, void* const* __restrict__ outs, int task0,
+                                 int dtype, int L) {
+    const MTask t = tasks[task0 + blockIdx.y];
+    T* out = static_cast<T*>(outs[task0 + blockIdx.y]);
+    if (!out) return;
+    const StateView st{t.hdr, L, t.G_hdr};
+    if (!cta_header_ok(st, dtype)) return;
+    for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < t.G_hdr;
+         g += (long long)gridDim.x * blockDim.x)
+        out[g] = state_finalize_group<T>(st, g);
+}
+
 struct BatchPlan {
     int dtype = 0, L = 0;
     FusedPlanConfig cfg{};
     int gcap_ = 1;
     int ctas = 0;
     int nitems = 0, nblks = 0;
+    int ntasks = 0;
+    long long gmax = 1;                 // largest group count of any task
+    void** d_outs = nullptr;            // repro_batch_set_outputs
     MTask* d_tasks = nullptr;
     MItem* d_items = nullptr;
     MergeBlk* d_blks = nullptr;
@@ -571,13 +599,18 @@ repro_status repro_batch_prepare(const repro_task* tasks, int ntasks, repro_dtyp
     P.slow = H.slow;
     P.nitems = (int)H.items.size();
     P.nblks = (int)H.blks.size();
-    if (P.nitems > 0) {
-        cudaError_t e = cudaMalloc(&P.d_tasks, sizeof(MTask) * std::max(1, ntasks));
-        if (e == cudaSuccess) e = cudaMalloc(&P.d_items, sizeof(MItem) * P.nitems);
+    P.ntasks = ntasks;
+    for (int t = 0; t < ntasks; ++t) P.gmax = std::max<long long>(P.gmax, tasks[t].num_groups);
+    if (ntasks > 0) {
+        cudaError_t e = cudaMalloc(&P.d_tasks, sizeof(MTask) * ntasks);
+        if (e == cudaSuccess) e = cudaMemcpy(P.d_tasks, H.tasks.data(), sizeof(MTask) * ntasks, cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) st = e == cudaErrorMemoryAllocation ? REPRO_ENOMEM : REPRO_ECUDA;
+    }
+    if (st == REPRO_OK && P.nitems > 0) {
+        cudaError_t e = cudaMalloc(&P.d_items, sizeof(MItem) * P.nitems);
         if (e == cudaSuccess) e = cudaMalloc(&P.d_blks, sizeof(MergeBlk) * std::max(1, P.nblks));
         if (e == cudaSuccess) e = cudaMalloc(&P.d_partials, std::max<size_t>(16, (size_t)H.part_recs * batch_rec_bytes(L)));
         if (e == cudaSuccess) e = cudaMalloc(&P.d_counter, sizeof(int));
-        if (e == cudaSuccess) e = cudaMemcpy(P.d_tasks, H.tasks.data(), sizeof(MTask) * ntasks, cudaMemcpyHostToDevice);
         if (e == cudaSuccess)
             e = cudaMemcpy(P.d_items, H.items.data(), sizeof(MItem) * P.nitems, cudaMemcpyHostToDevice);
         if (e == cudaSuccess && P.nblks)
@@ -585,7 +618,16 @@ repro_status repro_batch_prepare(const repro_task* tasks, int ntasks, repro_dtyp
         if (e != cudaSuccess) st = e == cudaErrorMemoryAllocation ? REPRO_ENOMEM : REPRO_ECUDA;
     }
     if (st == REPRO_OK && !P.slow.empty()) {
-        if (cudaMalloc(&P.d_slow_scratch, two_pass_scratch_bytes(H.slow_gmax)) != cudaSuccess) st = REPRO_ENOMEM;
+        // tasks beyond the single-pass table: the partitioned path where it
+        // applies, else the two-pass path; they run one after another and
+        // share one scratch buffer of the largest need
+        size_t need = 16;
+        for (const repro_task& k : P.slow) {
+            const bool part = partitioned_supported(dtype, L, k.num_groups, k.n, k.keys, k.values);
+            need = std::max(need, part ? partitioned_scratch_bytes(dtype, L, k.num_groups, k.n)
+                                       : two_pass_scratch_bytes(k.num_groups));
+        }
+        if (cudaMalloc(&P.d_slow_scratch, need) != cudaSuccess) st = REPRO_ENOMEM;
     }
     if (st != REPRO_OK) {
         repro_batch_destroy(plan);
@@ -611,9 +653,66 @@ repro_status repro_batch_run(repro_batch_plan plan, void* stream) {
         }
     }
     for (const repro_task& k : P.slow) {
-        e = launch_groupby_two_pass(k.keys, k.values, k.n, P.dtype, P.L, k.num_groups, k.state, P.d_slow_scratch, s);
+        if (partitioned_supported(P.dtype, P.L, k.num_groups, k.n, k.keys, k.values))
+            e = launch_groupby_partitioned(k.keys, k.values, k.n, P.dtype, P.L, k.num_groups, k.state,
+                                           P.d_slow_scratch, s);
+        else
+            e = launch_groupby_two_pass(k.keys, k.values, k.n, P.dtype, P.L, k.num_groups, k.state,
+                                        P.d_slow_scratch, s);
         if (e != cudaSuccess) return REPRO_ECUDA;
     }
+    return REPRO_OK;
+}
+
+// grid.x: enough CTAs per task to cover the largest group table in a few
+// passes; grid.y: tasks, at most 65535 per launch.
+static dim3 batch_grid(const BatchPlan& P, int tasks_in_launch) {
+    const long long bx = std::min<long long>(32, std::max<long long>(1, (P.gmax + 1023) / 1024));
+    return dim3((unsigned)bx, (unsigned)tasks_in_launch, 1);
+}
+
+repro_status repro_batch_reset(repro_batch_plan plan, void* stream) {
+    if (!plan) return REPRO_EINVAL;
+    BatchPlan& P = plan->p;
+    cudaStream_t s = (cudaStream_t)stream;
+    for (int t0 = 0; t0 < P.ntasks; t0 += 65535) {
+        const int nt = std::min(65535, P.ntasks - t0);
+        k_batch_init<<<batch_grid(P, nt), 256, 0, s>>>(P.d_tasks, t0, P.dtype, P.L);
+        count_launches(1);
+        if (cudaGetLastError() != cudaSuccess) return REPRO_ECUDA;
+    }
+    return REPRO_OK;
+}
+
+repro_status repro_batch_set_outputs(repro_batch_plan plan, void* const* outs) {
+    if (!plan || !outs) return REPRO_EINVAL;
+    BatchPlan& P = plan->p;
+    const size_t esz = P.dtype == REPRO_F64 ? 8 : 4;
+    for (int t = 0; t < P.ntasks; ++t)
+        if ((uintptr_t)outs[t] % esz) return REPRO_EINVAL;
+    if (P.ntasks == 0) return REPRO_OK;
+    if (!P.d_outs && cudaMalloc((void**)&P.d_outs, sizeof(void*) * P.ntasks) != cudaSuccess) return REPRO_ENOMEM;
+    return cudaMemcpy(P.d_outs, outs, sizeof(void*) * P.ntasks, cudaMemcpyHostToDevice) == cudaSuccess
+               ? REPRO_OK
+               : REPRO_ECUDA;
+}
+
+repro_status repro_batch_finalize(repro_batch_plan plan, void* stream) {
+    if (!plan) return REPRO_EINVAL;
+    BatchPlan& P = plan->p;
+    if (P.ntasks > 0 && !P.d_outs) return REPRO_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    prof_begin(PROF_FINALIZE, s);
+    for (int t0 = 0; t0 < P.ntasks; t0 += 65535) {
+        const int nt = std::min(65535, P.ntasks - t0);
+        if (P.dtype == REPRO_F64)
+            k_batch_finalize<double><<<batch_grid(P, nt), 256, 0, s>>>(P.d_tasks, P.d_outs, t0, P.dtype, P.L);
+        else
+            k_batch_finalize<float><<<batch_grid(P, nt), 256, 0, s>>>(P.d_tasks, P.d_outs, t0, P.dtype, P.L);
+        count_launches(1);
+        if (cudaGetLastError() != cudaSuccess) return REPRO_ECUDA;
+    }
+    prof_end(PROF_FINALIZE, s);
     return REPRO_OK;
 }
 
@@ -621,6 +720,7 @@ repro_status repro_batch_destroy(repro_batch_plan plan) {
     if (!plan) return REPRO_OK;
     BatchPlan& P = plan->p;
     cudaFree(P.d_tasks);
+    cudaFree(P.d_outs);
     cudaFree(P.d_items);
     cudaFree(P.d_blks);
     cudaFree(P.d_partials);

@@ -427,4 +427,70 @@ __device__ __forceinline__ float inf_of<float>(bool neg) {
     return __int_as_float(neg ? (int)0xff800000u : 0x7f800000);
 }
 
+// ------------------------------------------------- per-group state helpers
+
+__device__ __forceinline__ bool header_ok(const StateView& st, int dtype) {
+    const repro_state_header* h = st.header();
+    return h->magic == REPRO_STATE_MAGIC && h->dtype == (uint32_t)dtype && h->L == (uint32_t)st.L &&
+           h->num_groups == st.G;
+}
+
+// One thread per CTA checks the header(s); a mismatch marks the state and
+// makes every thread of the CTA return.
+__device__ __forceinline__ bool cta_header_ok(const StateView& a, int dtype, const StateView* b = nullptr) {
+    __shared__ int s_ok;
+    if (threadIdx.x == 0) {
+        int ok = header_ok(a, dtype);
+        if (b && !header_ok(*b, dtype)) ok = 0;
+        if (!ok) atomicOr(&a.header()->errors, REPRO_ERR_LAYOUT);
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+__device__ __forceinline__ void state_init_header(const StateView& st, int dtype) {
+    repro_state_header* h = st.header();
+    h->magic = REPRO_STATE_MAGIC;
+    h->dtype = (uint32_t)dtype;
+    h->L = (uint32_t)st.L;
+    h->errors = 0;
+    h->num_groups = st.G;
+    for (int i = 0; i < 40; ++i) h->reserved[i] = 0;
+}
+
+__device__ __forceinline__ void state_init_group(const StateView& st, long long g) {
+    *st.K(g) = 0;
+    *st.flags(g) = 0;
+    for (int j = 0; j < st.L; ++j) {
+        *st.lo(g, j) = 0;
+        *st.hi(g, j) = 0;
+    }
+}
+
+// The result of one group (eq. (1)): the special values first, else
+// V_j = RN(T_j u_j) folded from the lowest level up, left-associative.
+template <typename T>
+__device__ __forceinline__ T state_finalize_group(const StateView& st, long long g) {
+    constexpr int W = Traits<T>::W, GMIN = Traits<T>::GMIN;
+    const unsigned f = *st.flags(g);
+    if ((f & (REPRO_FLAG_NAN | REPRO_FLAG_RANGE)) || ((f & REPRO_FLAG_POS_INF) && (f & REPRO_FLAG_NEG_INF)))
+        return quiet_nan<T>();
+    if (f & REPRO_FLAG_POS_INF) return inf_of<T>(false);
+    if (f & REPRO_FLAG_NEG_INF) return inf_of<T>(true);
+    const int K = *st.K(g);
+    bool first = true;
+    T q = (T)0;
+    for (int j = st.L - 1; j >= 0; --j) {
+        if (K - j < 0) continue;
+        const __int128 t = bin_read(st.lo(g, j), st.hi(g, j));
+        const bool neg = t < 0;
+        const unsigned __int128 mag = neg ? (unsigned __int128)(-t) : (unsigned __int128)t;
+        const T v = round_scaled<T>(neg, mag, GMIN + (K - j) * W);
+        q = first ? v : t_add(q, v);
+        first = false;
+    }
+    return q;
+}
+
 }  // namespace rp

@@ -20,50 +20,13 @@
 
 namespace rp {
 
-// ------------------------------------------------------------------ helpers
-
-__device__ __forceinline__ bool header_ok(const StateView& st, int dtype) {
-    const repro_state_header* h = st.header();
-    return h->magic == REPRO_STATE_MAGIC && h->dtype == (uint32_t)dtype && h->L == (uint32_t)st.L &&
-           h->num_groups == st.G;
-}
-
-// One thread per CTA checks the header(s); a mismatch marks the state and
-// makes every thread of the CTA return.
-__device__ __forceinline__ bool cta_header_ok(const StateView& a, int dtype, const StateView* b = nullptr) {
-    __shared__ int s_ok;
-    if (threadIdx.x == 0) {
-        int ok = header_ok(a, dtype);
-        if (b && !header_ok(*b, dtype)) ok = 0;
-        if (!ok) atomicOr(&a.header()->errors, REPRO_ERR_LAYOUT);
-        s_ok = ok;
-    }
-    __syncthreads();
-    return s_ok != 0;
-}
-
 // ------------------------------------------------------------------- kernels
 
 __global__ void k_init_state(unsigned char* base, int dtype, int L, long long G) {
     StateView st{base, L, G};
     const long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (tid == 0) {
-        repro_state_header* h = st.header();
-        h->magic = REPRO_STATE_MAGIC;
-        h->dtype = (uint32_t)dtype;
-        h->L = (uint32_t)L;
-        h->errors = 0;
-        h->num_groups = G;
-        for (int i = 0; i < 40; ++i) h->reserved[i] = 0;
-    }
-    for (long long g = tid; g < G; g += (long long)gridDim.x * blockDim.x) {
-        *st.K(g) = 0;
-        *st.flags(g) = 0;
-        for (int j = 0; j < L; ++j) {
-            *st.lo(g, j) = 0;
-            *st.hi(g, j) = 0;
-        }
-    }
+    if (tid == 0) state_init_header(st, dtype);
+    for (long long g = tid; g < G; g += (long long)gridDim.x * blockDim.x) state_init_group(st, g);
 }
 
 // Max-abs pre-pass.  Kmax[g] (zeroed by the caller) receives max K(b) over
@@ -213,34 +176,9 @@ template <typename T>
 __global__ void k_finalize(const unsigned char* base, int dtype, int L, long long G, T* __restrict__ out) {
     StateView st{const_cast<unsigned char*>(base), L, G};
     if (!cta_header_ok(st, dtype)) return;
-    constexpr int W = Traits<T>::W, GMIN = Traits<T>::GMIN;
     for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < G;
-         g += (long long)gridDim.x * blockDim.x) {
-        const unsigned f = *st.flags(g);
-        T q;
-        if ((f & (REPRO_FLAG_NAN | REPRO_FLAG_RANGE)) ||
-            ((f & REPRO_FLAG_POS_INF) && (f & REPRO_FLAG_NEG_INF))) {
-            q = quiet_nan<T>();
-        } else if (f & REPRO_FLAG_POS_INF) {
-            q = inf_of<T>(false);
-        } else if (f & REPRO_FLAG_NEG_INF) {
-            q = inf_of<T>(true);
-        } else {
-            const int K = *st.K(g);
-            bool first = true;
-            q = (T)0;
-            for (int j = L - 1; j >= 0; --j) {
-                if (K - j < 0) continue;
-                const __int128 t = bin_read(st.lo(g, j), st.hi(g, j));
-                const bool neg = t < 0;
-                const unsigned __int128 mag = neg ? (unsigned __int128)(-t) : (unsigned __int128)t;
-                const T v = round_scaled<T>(neg, mag, GMIN + (K - j) * W);
-                q = first ? v : t_add(q, v);
-                first = false;
-            }
-        }
-        out[g] = q;
-    }
+         g += (long long)gridDim.x * blockDim.x)
+        out[g] = state_finalize_group<T>(st, g);
 }
 
 // Conventional floating-point GroupBy (non-reproducible baseline).

@@ -70,11 +70,12 @@ class Server:
         self._reqs = {}
 
     def submit(self, keys: torch.Tensor, values: torch.Tensor, num_groups: int, L: int = 3,
-               out: Optional[torch.Tensor] = None, arrival_ns: int = 0, host_out: bool = True) -> Request:
+               out: Optional[torch.Tensor] = None, arrival_ns: int = 0, host_out: bool = True,
+               ready: Optional[torch.cuda.Event] = None) -> Request:
         """Queue SUM(values) GROUP BY keys; the result lands in `out` (pinned
         host memory by default).  The inputs must stay unchanged until the
-        request is done; work queued on the current stream before this call is
-        waited for."""
+        request is done.  The server waits for `ready` (default: an event
+        recorded now on the current stream) before reading them."""
         _require_cuda(keys, "keys")
         _require_cuda(values, "values")
         if keys.dtype != torch.int32 or keys.numel() != values.numel():
@@ -83,8 +84,9 @@ class Server:
         if out is None:
             out = (torch.empty(num_groups, dtype=values.dtype, pin_memory=True) if host_out
                    else torch.empty(num_groups, dtype=values.dtype, device=values.device))
-        ready = torch.cuda.Event()
-        ready.record(torch.cuda.current_stream(values.device))
+        if ready is None:
+            ready = torch.cuda.Event()
+            ready.record(torch.cuda.current_stream(values.device))
         rid = ctypes.c_uint64()
         _check(lib().repro_server_submit(self._h, keys.data_ptr(), values.data_ptr(), keys.numel(),
                                          _dtype_code(values.dtype), L, num_groups, out.data_ptr(),
@@ -136,12 +138,17 @@ def run_trace(server: Server, queries: Sequence[tuple], arrivals_s: Sequence[flo
               keep_results: bool = False, timeout_s: float = 600.0) -> dict:
     """Submit `queries` ((keys, values, num_groups) on the device) with arrival
     times `arrivals_s` (seconds after the start), wait for all, and return
-    per-request latency (arrival -> result in host memory) and the rows/s."""
-    torch.cuda.current_stream(server.device).synchronize()
-    t0 = now_ns() + 2_000_000
+    per-request latency (arrival -> result in host memory) and the rows/s.
+    Outputs are allocated and every query submitted before the first arrival
+    (the start is put far enough ahead), so the client adds no delay."""
+    outs = [torch.empty(q[2], dtype=q[1].dtype, pin_memory=True) for q in queries]
+    ready = torch.cuda.Event()
+    ready.record(torch.cuda.current_stream(server.device))
+    t0 = now_ns() + 5_000_000 + 40_000 * len(queries)
     reqs: List[Request] = []
-    for (k, v, G), a in zip(queries, arrivals_s):
-        reqs.append(server.submit(k, v, G, L, arrival_ns=t0 + int(a * 1e9)))
+    for (k, v, G), a, o in zip(queries, arrivals_s, outs):
+        reqs.append(server.submit(k, v, G, L, out=o, arrival_ns=t0 + int(a * 1e9), ready=ready))
+    late = max(0, now_ns() - t0)
     lat, first, last = [], None, 0
     results = []
     for r in reqs:
@@ -158,4 +165,4 @@ def run_trace(server: Server, queries: Sequence[tuple], arrivals_s: Sequence[flo
     return {"requests": len(reqs), "rows": rows, "span_s": span, "rows_per_s": rows / span if span > 0 else 0.0,
             "p50_ms": float(np.percentile(lat, 50) * 1e3), "p99_ms": float(np.percentile(lat, 99) * 1e3),
             "mean_ms": float(lat.mean() * 1e3), "max_ms": float(lat.max() * 1e3),
-            "results": results if keep_results else None}
+            "submit_overrun_ms": late * 1e-6, "results": results if keep_results else None}

@@ -104,3 +104,19 @@ def test_bad_keys_flag_only_their_task():
     assert states[0].check() == 0
     with pytest.raises(R.ReproError):
         states[1].check()
+
+
+def test_batch_reset_and_finalize_in_one_launch_each():
+    tasks = _tasks(21, 30, torch.float64)
+    states = [R.State(G, 3, torch.float64) for _, _, G in tasks]
+    outs = [torch.empty(G, dtype=torch.float64, device=DEV) for _, _, G in tasks]
+    plan = R.BatchPlan([(k, v, st) for (k, v, _), st in zip(tasks, states)])
+    plan.set_outputs(outs)
+    for rep in range(2):  # the reset makes the second pass equal the first
+        plan.reset().run().finalize()
+        torch.cuda.synchronize()
+        for (k, v, G), st, o in zip(tasks, states, outs):
+            ref = _single(k, v, G, 3)
+            assert torch.equal(st.tensor, ref.tensor), rep
+            assert torch.equal(o.view(torch.int64), ref.finalize().view(torch.int64)), rep
+    plan.close()
