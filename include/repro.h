@@ -269,7 +269,7 @@ repro_status groupby_sum_fp32(const int32_t* keys, const float* values, int64_t 
  * a slot is free.  It then runs iterations: each iteration takes the next
  * chunk_rows rows of every admitted query; chunks whose group table fits the
  * single-pass kernel go into one multi-task persistent launch, the others
- * through the partitioned path on a second stream.  Partial states stay on
+ * through the partitioned path on one of four more streams.  Partial states stay on
  * the device between iterations.  After its last chunk a query is finalized
  * into its output and its state freed; a host callback stamps the completion
  * time.  At most max_inflight iterations are queued ahead of the device.

@@ -566,10 +566,21 @@ struct BatchPlan {
     MergeBlk* d_blks = nullptr;
     unsigned char* d_partials = nullptr;
     int* d_counter = nullptr;
-    // tasks outside the single-pass path: run one by one through the two-pass path
+    // Tasks outside the single-pass path run through the partitioned (or
+    // two-pass) path on `lanes` side streams forked from the caller's stream
+    // and joined back into it, each lane with its own scratch; tasks are
+    // assigned largest first to the least-loaded lane.
     std::vector<repro_task> slow;
-    void* d_slow_scratch = nullptr;
+    std::vector<int> slow_lane;
+    std::vector<cudaStream_t> lanes;
+    std::vector<cudaEvent_t> joins;
+    cudaEvent_t fork = nullptr;
+    size_t slow_each = 0;
+    unsigned char* d_slow_scratch = nullptr;
 };
+
+// Side streams for the tasks beyond the single-pass table.
+constexpr int kSlowLanes = 8;
 
 }  // namespace rp
 
@@ -619,15 +630,35 @@ repro_status repro_batch_prepare(const repro_task* tasks, int ntasks, repro_dtyp
     }
     if (st == REPRO_OK && !P.slow.empty()) {
         // tasks beyond the single-pass table: the partitioned path where it
-        // applies, else the two-pass path; they run one after another and
-        // share one scratch buffer of the largest need
+        // applies, else the two-pass path
         size_t need = 16;
         for (const repro_task& k : P.slow) {
             const bool part = partitioned_supported(dtype, L, k.num_groups, k.n, k.keys, k.values);
             need = std::max(need, part ? partitioned_scratch_bytes(dtype, L, k.num_groups, k.n)
                                        : two_pass_scratch_bytes(k.num_groups));
         }
-        if (cudaMalloc(&P.d_slow_scratch, need) != cudaSuccess) st = REPRO_ENOMEM;
+        const int nl = std::min<int>(kSlowLanes, (int)P.slow.size());
+        std::stable_sort(P.slow.begin(), P.slow.end(),
+                         [](const repro_task& x, const repro_task& y) { return x.n > y.n; });
+        std::vector<long long> load(nl, 0);
+        for (const repro_task& k : P.slow) {
+            const int l = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+            P.slow_lane.push_back(l);
+            load[l] += k.n + 4096;
+        }
+        P.slow_each = (need + 255) & ~(size_t)255;
+        if (cudaMalloc((void**)&P.d_slow_scratch, P.slow_each * nl) != cudaSuccess) st = REPRO_ENOMEM;
+        cudaError_t e = cudaSuccess;
+        if (st == REPRO_OK) e = cudaEventCreateWithFlags(&P.fork, cudaEventDisableTiming);
+        for (int l = 0; l < nl && st == REPRO_OK && e == cudaSuccess; ++l) {
+            cudaStream_t ls = nullptr;
+            cudaEvent_t je = nullptr;
+            e = cudaStreamCreateWithFlags(&ls, cudaStreamNonBlocking);
+            if (e == cudaSuccess) P.lanes.push_back(ls);
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&je, cudaEventDisableTiming);
+            if (e == cudaSuccess) P.joins.push_back(je);
+        }
+        if (st == REPRO_OK && e != cudaSuccess) st = REPRO_ECUDA;
     }
     if (st != REPRO_OK) {
         repro_batch_destroy(plan);
@@ -642,6 +673,25 @@ repro_status repro_batch_run(repro_batch_plan plan, void* stream) {
     BatchPlan& P = plan->p;
     cudaStream_t s = (cudaStream_t)stream;
     cudaError_t e = cudaSuccess;
+    // fork: the side lanes start with the caller's stream as it stands here,
+    // and run next to the persistent launch below
+    if (!P.slow.empty()) {
+        if (cudaEventRecord(P.fork, s) != cudaSuccess) return REPRO_ECUDA;
+        for (cudaStream_t ls : P.lanes)
+            if (cudaStreamWaitEvent(ls, P.fork, 0) != cudaSuccess) return REPRO_ECUDA;
+        for (size_t i = 0; i < P.slow.size(); ++i) {
+            const repro_task& k = P.slow[i];
+            const int l = P.slow_lane[i];
+            unsigned char* scratch = P.d_slow_scratch + (size_t)l * P.slow_each;
+            if (partitioned_supported(P.dtype, P.L, k.num_groups, k.n, k.keys, k.values))
+                e = launch_groupby_partitioned(k.keys, k.values, k.n, P.dtype, P.L, k.num_groups, k.state, scratch,
+                                               P.lanes[l]);
+            else
+                e = launch_groupby_two_pass(k.keys, k.values, k.n, P.dtype, P.L, k.num_groups, k.state, scratch,
+                                            P.lanes[l]);
+            if (e != cudaSuccess) return REPRO_ECUDA;
+        }
+    }
     if (P.nitems > 0) {
         const int ctas = std::min(P.ctas, std::max(1, P.nitems));
         e = launch_multi(P.dtype, P.L, P.cfg, P.gcap_, P.d_tasks, P.d_items, P.nitems, nullptr, P.d_counter,
@@ -652,14 +702,10 @@ repro_status repro_batch_run(repro_batch_plan plan, void* stream) {
             if (e != cudaSuccess) return REPRO_ECUDA;
         }
     }
-    for (const repro_task& k : P.slow) {
-        if (partitioned_supported(P.dtype, P.L, k.num_groups, k.n, k.keys, k.values))
-            e = launch_groupby_partitioned(k.keys, k.values, k.n, P.dtype, P.L, k.num_groups, k.state,
-                                           P.d_slow_scratch, s);
-        else
-            e = launch_groupby_two_pass(k.keys, k.values, k.n, P.dtype, P.L, k.num_groups, k.state,
-                                        P.d_slow_scratch, s);
-        if (e != cudaSuccess) return REPRO_ECUDA;
+    // join: the caller's stream continues once every lane is done
+    for (size_t l = 0; l < P.lanes.size(); ++l) {
+        if (cudaEventRecord(P.joins[l], P.lanes[l]) != cudaSuccess) return REPRO_ECUDA;
+        if (cudaStreamWaitEvent(s, P.joins[l], 0) != cudaSuccess) return REPRO_ECUDA;
     }
     return REPRO_OK;
 }
@@ -726,6 +772,9 @@ repro_status repro_batch_destroy(repro_batch_plan plan) {
     cudaFree(P.d_partials);
     cudaFree(P.d_counter);
     cudaFree(P.d_slow_scratch);
+    for (cudaStream_t ls : P.lanes) cudaStreamDestroy(ls);
+    for (cudaEvent_t je : P.joins) cudaEventDestroy(je);
+    if (P.fork) cudaEventDestroy(P.fork);
     delete plan;
     return REPRO_OK;
 }

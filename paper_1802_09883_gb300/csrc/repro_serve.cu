@@ -9,8 +9,8 @@
 //   2. takes the next chunk of every admitted query: chunks of single-pass
 //      queries (table fits shared memory) become the tasks of one multi-task
 //      persistent launch per (dtype, L) on the batch stream; the other
-//      queries run their chunk through the partitioned path on the second
-//      stream;
+//      queries run their chunk through the partitioned path on one of four
+//      more streams (fixed per query, the least loaded at admission);
 //   3. finalizes queries that received their last chunk, copies each state's
 //      error word to a pinned slot, frees the state in stream order and
 //      enqueues a host callback that stamps the completion time and returns
@@ -63,6 +63,10 @@ size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 // allows (the planner makes items longer otherwise).
 constexpr size_t kServePartBytes = 256ull << 20;
 
+// Stream 0 runs the batched launches; streams 1 .. kLanes-1 run the queries
+// whose tables need the partitioned path, each query on one of them.
+constexpr int kLanes = 5;
+
 struct Req {
     uint64_t id = 0;
     const int32_t* keys = nullptr;
@@ -77,7 +81,8 @@ struct Req {
     repro_status status = REPRO_OK;
     uint32_t errors = 0;
     long long pos = 0;   // rows issued so far
-    int lane = 0;        // 0: batch stream, 1: partitioned stream
+    int lane = 0;        // 0: batch stream, else a partitioned-path stream
+    bool large = false;  // needs the partitioned path
     void* state = nullptr;
     size_t need = 0;     // bytes charged to the budget while admitted
     int slot = -1;       // pinned error-word slot
@@ -93,7 +98,7 @@ struct Arena {
 
 struct Iter {
     std::vector<Arena*> arenas;
-    cudaEvent_t ev[2] = {nullptr, nullptr};
+    cudaEvent_t ev[kLanes] = {};
 };
 
 struct Server;
@@ -109,7 +114,7 @@ struct Server {
     repro_server_config cfg{};
     int device = 0;
     cudaMemPool_t pool = nullptr;
-    cudaStream_t stream[2] = {nullptr, nullptr};
+    cudaStream_t stream[kLanes] = {};
     uint32_t* err_words = nullptr;  // pinned, one per slot
 
     std::mutex mu;
@@ -239,6 +244,13 @@ struct Server {
     bool issue(std::vector<Req*>& admitted_now) {
         cudaError_t e = cudaSuccess;
         for (Req* r : admitted_now) {
+            if (r->large) {  // the partitioned lane with the fewest rows left to issue
+                long long left[kLanes] = {};
+                for (Req* q : active) left[q->lane] += q->n - q->pos;
+                r->lane = 1;
+                for (int l = 2; l < kLanes; ++l)
+                    if (left[l] < left[r->lane]) r->lane = l;
+            }
             cudaStream_t s = stream[r->lane];
             if (r->ready) e = cudaStreamWaitEvent(s, r->ready, 0);
             const size_t sb = repro_state_bytes((repro_dtype)r->dtype, r->L, r->G);
@@ -253,7 +265,7 @@ struct Server {
         inflight.emplace_back();
         Iter& it = inflight.back();
         std::map<std::pair<int, int>, std::vector<repro_task>> batches;
-        std::vector<Req*> fin[2], keep;
+        std::vector<Req*> fin[kLanes], keep;
         long long large_calls = 0;
         for (Req* r : active) {
             const long long rows = std::min<long long>(cfg.chunk_rows, r->n - r->pos);
@@ -263,7 +275,8 @@ struct Server {
                 if (r->lane == 0) {
                     batches[{r->dtype, r->L}].push_back(repro_task{k, v, rows, r->G, r->state});
                 } else {
-                    if (groupby_dispatch(k, v, rows, r->dtype, r->L, r->G, r->state, stream[1]) != REPRO_OK) {
+                    const int st_ = groupby_dispatch(k, v, rows, r->dtype, r->L, r->G, r->state, stream[r->lane]);
+                    if (st_ != REPRO_OK) {
                         for (Req* q : keep) active.push_back(q);
                         return false;
                     }
@@ -277,7 +290,7 @@ struct Server {
         // on an error, queries not yet handed to a completion callback go back
         // to the active list, which fail_all() then reports
         auto give_back = [&](int from) {
-            for (int l = from; l < 2; ++l)
+            for (int l = from; l < kLanes; ++l)
                 for (Req* r : fin[l]) active.push_back(r);
             return false;
         };
@@ -286,7 +299,7 @@ struct Server {
             if (launch_batch(b.first.first, b.first.second, b.second, it) != cudaSuccess) return give_back(0);
             ++launches;
         }
-        for (int l = 0; l < 2; ++l) {
+        for (int l = 0; l < kLanes; ++l) {
             if (fin[l].empty()) continue;
             for (Req* r : fin[l]) {
                 e = launch_finalize(r->state, r->dtype, r->L, r->G, r->out, stream[l]);
@@ -304,7 +317,7 @@ struct Server {
             }
             fin[l].clear();
         }
-        for (int l = 0; l < 2; ++l) {
+        for (int l = 0; l < kLanes; ++l) {
             it.ev[l] = take_event();
             if (!it.ev[l] || cudaEventRecord(it.ev[l], stream[l]) != cudaSuccess) return false;
         }
@@ -357,8 +370,7 @@ struct Server {
                 break;
             }
         }
-        cudaStreamSynchronize(stream[0]);
-        cudaStreamSynchronize(stream[1]);
+        for (cudaStream_t st_ : stream) cudaStreamSynchronize(st_);
         while (!inflight.empty()) retire_oldest();
     }
 };
@@ -444,12 +456,12 @@ repro_status repro_server_create(const repro_server_config* cfg, repro_server* o
     S.device = dev;
     cudaError_t e = cudaSuccess;
     S.pool = library_pool(e);
-    if (S.pool) e = cudaStreamCreateWithFlags(&S.stream[0], cudaStreamNonBlocking);
-    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&S.stream[1], cudaStreamNonBlocking);
+    for (int l = 0; l < kLanes && S.pool && e == cudaSuccess; ++l)
+        e = cudaStreamCreateWithFlags(&S.stream[l], cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaHostAlloc((void**)&S.err_words, sizeof(uint32_t) * c.max_active, cudaHostAllocDefault);
     if (!S.pool || e != cudaSuccess) {
-        if (S.stream[0]) cudaStreamDestroy(S.stream[0]);
-        if (S.stream[1]) cudaStreamDestroy(S.stream[1]);
+        for (cudaStream_t st_ : S.stream)
+            if (st_) cudaStreamDestroy(st_);
         if (S.err_words) cudaFreeHost(S.err_words);
         delete h;
         return e == cudaErrorMemoryAllocation ? REPRO_ENOMEM : REPRO_ECUDA;
@@ -459,8 +471,7 @@ repro_status repro_server_create(const repro_server_config* cfg, repro_server* o
     try {
         S.thr = std::thread([&S] { S.run(); });
     } catch (...) {
-        cudaStreamDestroy(S.stream[0]);
-        cudaStreamDestroy(S.stream[1]);
+        for (cudaStream_t st_ : S.stream) cudaStreamDestroy(st_);
         cudaFreeHost(S.err_words);
         delete h;
         return REPRO_ENOMEM;
@@ -497,9 +508,9 @@ repro_status repro_server_submit(repro_server srv, const int32_t* keys, const vo
     r->out = out;
     r->ready = (cudaEvent_t)ready_event;
     r->arrival_ns = arrival_ns > 0 ? arrival_ns : now_ns();
-    r->lane = (n == 0 || fused_supported(dtype, L, num_groups, keys, values)) ? 0 : 1;
+    r->large = !(n == 0 || fused_supported(dtype, L, num_groups, keys, values));
     r->need = repro_state_bytes(dtype, L, num_groups);
-    if (r->lane == 1) {
+    if (r->large) {
         const long long rows = std::min<long long>(n, S.cfg.chunk_rows);
         r->need += partitioned_supported(dtype, L, num_groups, rows, keys, values)
                        ? partitioned_scratch_bytes(dtype, L, num_groups, rows)
@@ -588,8 +599,7 @@ repro_status repro_server_destroy(repro_server srv) {
         delete a;
     }
     cudaStreamSynchronize(S.stream[0]);
-    cudaStreamDestroy(S.stream[0]);
-    cudaStreamDestroy(S.stream[1]);
+    for (cudaStream_t st_ : S.stream) cudaStreamDestroy(st_);
     cudaFreeHost(S.err_words);
     cudaSetDevice(cur);
     const repro_status st = S.fatal;

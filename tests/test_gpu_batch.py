@@ -66,8 +66,9 @@ def test_one_large_task_split_into_many_items_and_merged():
     assert torch.equal(st.tensor, ref.tensor)
 
 
-def test_batch_plan_replays_in_a_cuda_graph():
-    tasks = _tasks(9, 12, torch.float64, big_g=False)
+@pytest.mark.parametrize("big_g", [False, True])  # True: side lanes (partitioned tasks) forked inside the graph
+def test_batch_plan_replays_in_a_cuda_graph(big_g):
+    tasks = _tasks(9, 30 if big_g else 12, torch.float64, big_g=big_g)
     states = [R.State(G, 3, torch.float64) for _, _, G in tasks]
     plan = R.BatchPlan([(k, v, st) for (k, v, _), st in zip(tasks, states)])
     s = torch.cuda.Stream()
