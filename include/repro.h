@@ -340,6 +340,48 @@ repro_status repro_server_stats_get(repro_server srv, repro_server_stats* st);
    server.  Results of unreleased queries are no longer readable. */
 repro_status repro_server_destroy(repro_server srv);
 
+/*
+ * Autotuning.  The paper picks its partitioning fan-out and buffer sizes per
+ * machine offline and notes that the best values depend on the group count
+ * (Sec. V-C, Sec. VI).  repro_tune_groupby times every configuration that
+ * fits on the caller's inputs -- for the single-pass path its stages, rows
+ * per tile, consumer warps, CTAs per SM and table copies; for the
+ * partitioned path its partition width (fan-out) -- and records the fastest
+ * for (dtype, L, num_groups rounded up to a power of two); later calls in that
+ * bucket use it.  It allocates its own state and scratch, runs each
+ * candidate a few times on `stream` and synchronises; the inputs are only
+ * read.  No choice changes any result (every candidate computes the same
+ * exact bins).  A batch plan or a call that has already chosen keeps its
+ * choice.  REPRO_EINVAL for bad arguments or n == 0.
+ */
+typedef struct {
+    int32_t path;            /* 0 single pass, 1 partitioned, 2 two pass (nothing to tune) */
+    int32_t candidates;      /* configurations timed */
+    int32_t stages, tile_rows, consumer_warps, ctas_per_sm, table_copies; /* single-pass choice */
+    int32_t partition_shift; /* partitioned choice: log2 of the groups per partition */
+    double best_ms;          /* median time of one call with the choice */
+    double default_ms;       /* the same with the built-in rule's choice */
+} repro_tune_result;
+
+repro_status repro_tune_groupby(const int32_t* keys, const void* values, int64_t n, repro_dtype dtype, int L,
+                                int64_t num_groups, void* stream, repro_tune_result* out);
+
+/* Write / read the recorded choices as text (one choice per line; load
+   merges into what is recorded).  REPRO_EINVAL if the file cannot be
+   opened or a line is malformed (nothing is loaded then). */
+repro_status repro_tune_save(const char* path);
+repro_status repro_tune_load(const char* path);
+
+/* Forget every recorded choice (the built-in rule applies again). */
+void repro_tune_clear(void);
+
+/* Time the plan with work items of several sizes (about 1, 2, 4, 8 and 16
+   items per CTA) and keep the fastest; *best_ms (may be NULL) receives its
+   median time per run.  Runs the plan several times on `stream` and
+   synchronises; afterwards every task's state is re-initialised (as
+   repro_batch_reset). */
+repro_status repro_batch_tune(repro_batch_plan plan, void* stream, double* best_ms);
+
 /* Human-readable text for a status code (static storage). */
 const char* repro_strerror(repro_status status);
 

@@ -98,13 +98,20 @@ def lib(build_if_stale: bool = True):
         L.repro_server_release.argtypes = [vp, ctypes.c_uint64]
         L.repro_server_stats_get.argtypes = [vp, vp]
         L.repro_server_destroy.argtypes = [vp]
+        L.repro_tune_groupby.argtypes = [vp, vp, i64, i32, i32, i64, vp, vp]
+        L.repro_tune_save.argtypes = [ctypes.c_char_p]
+        L.repro_tune_load.argtypes = [ctypes.c_char_p]
+        L.repro_tune_clear.argtypes = []
+        L.repro_tune_clear.restype = None
+        L.repro_batch_tune.argtypes = [vp, vp, ctypes.POINTER(ctypes.c_double)]
         for name in ("repro_state_init", "repro_groupby_sum", "repro_groupby_sum_noalloc", "repro_merge",
                      "repro_finalize", "repro_batch_prepare", "repro_batch_run", "repro_batch_destroy",
                      "repro_batch_reset", "repro_batch_set_outputs", "repro_batch_finalize",
                      "repro_groupby_sum_batched", "repro_groupby_sum_cols", "repro_release_cached_memory",
                      "repro_state_check", "groupby_sum_fp64", "groupby_sum_fp32", "repro_server_create",
                      "repro_server_submit", "repro_server_poll", "repro_server_wait", "repro_server_release",
-                     "repro_server_stats_get", "repro_server_destroy"):
+                     "repro_server_stats_get", "repro_server_destroy", "repro_tune_groupby", "repro_tune_save",
+                     "repro_tune_load", "repro_batch_tune"):
             getattr(L, name).restype = i32
         _lib = L
     return _lib
@@ -304,6 +311,13 @@ class BatchPlan:
         _check(lib().repro_batch_run(self._plan, _stream(self.device)), "repro_batch_run")
         return self
 
+    def tune(self) -> float:
+        """Time item sizes for this plan and keep the fastest (the states are
+        re-initialised afterwards); returns the median ms of one run."""
+        ms = ctypes.c_double(0)
+        _check(lib().repro_batch_tune(self._plan, _stream(self.device), ctypes.byref(ms)), "repro_batch_tune")
+        return ms.value
+
     def reset(self):
         """Re-initialise every task's state in one launch."""
         _check(lib().repro_batch_reset(self._plan, _stream(self.device)), "repro_batch_reset")
@@ -379,3 +393,36 @@ def groupby_sum_cols(key1: torch.Tensor, key2: torch.Tensor, card2: int, cols, n
 
 def release_cached_memory():
     _check(lib().repro_release_cached_memory(), "repro_release_cached_memory")
+
+
+class _TuneResult(ctypes.Structure):
+    _fields_ = [("path", ctypes.c_int32), ("candidates", ctypes.c_int32), ("stages", ctypes.c_int32),
+                ("tile_rows", ctypes.c_int32), ("consumer_warps", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32),
+                ("table_copies", ctypes.c_int32), ("partition_shift", ctypes.c_int32), ("best_ms", ctypes.c_double),
+                ("default_ms", ctypes.c_double)]
+
+
+def tune(keys: torch.Tensor, values: torch.Tensor, num_groups: int, L: int = 3) -> dict:
+    """Time every configuration that fits on these inputs and record the
+    fastest for (dtype, L, num_groups bucket); returns what was chosen."""
+    _require_cuda(keys, "keys")
+    _require_cuda(values, "values")
+    keys, values = keys.contiguous(), values.contiguous()
+    r = _TuneResult()
+    _check(lib().repro_tune_groupby(keys.data_ptr(), values.data_ptr(), keys.numel(), _dtype_code(values.dtype), L,
+                                    num_groups, _stream(values.device), ctypes.byref(r)), "repro_tune_groupby")
+    out = {name: getattr(r, name) for name, _ in _TuneResult._fields_}
+    out["path"] = ("single_pass", "partitioned", "two_pass")[r.path]
+    return out
+
+
+def tune_save(path: str):
+    _check(lib().repro_tune_save(os.fsencode(path)), "repro_tune_save")
+
+
+def tune_load(path: str):
+    _check(lib().repro_tune_load(os.fsencode(path)), "repro_tune_load")
+
+
+def tune_clear():
+    lib().repro_tune_clear()

@@ -26,11 +26,14 @@ struct HostBatch {
     long long slow_gmax = 0;
 };
 
-// Cut tasks into items: about four items per CTA, each at least 8 tiles and
-// at most 2^23 rows (no 64-bit table bin can overflow within an item); items
-// grow further while the partial tables would exceed max_part_bytes.
-// Validates the tasks (REPRO_EINVAL) and the table size (REPRO_ERANGE).
+// Cut tasks into items: about items_per_cta items per CTA, each at least 8
+// tiles and at most 2^23 rows (no 64-bit table bin can overflow within an
+// item); items grow further while the partial tables would exceed
+// max_part_bytes.  Validates the tasks (REPRO_EINVAL) and the table size
+// (REPRO_ERANGE).
+// With fixed_cfg the single-pass configuration is that one (it must fit)
+// instead of a fresh choice, so a re-plan keeps an existing plan's kernel.
 repro_status plan_batch_host(const repro_task* tasks, int ntasks, int dtype, int L, size_t max_part_bytes,
-                             HostBatch& H);
+                             HostBatch& H, int items_per_cta = 4, const FusedPlanConfig* fixed_cfg = nullptr);
 
 }  // namespace rp

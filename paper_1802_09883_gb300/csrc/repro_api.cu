@@ -109,15 +109,21 @@ namespace rp {
 
 int groupby_dispatch(const int32_t* keys, const void* values, long long n, int dtype, int L, long long num_groups,
                      void* state, cudaStream_t s) {
-    if (n > 0 && fused_supported(dtype, L, num_groups, keys, values)) {
-        Scratch scratch(fused_scratch_bytes(dtype, L, num_groups, n), s);
+    // each path's configuration is chosen once and passed on, so the scratch
+    // size and the launch agree even if the tuned cache changes meanwhile
+    FusedPlanConfig cfg;
+    if (n > 0 && fused_supported(dtype, L, num_groups, keys, values) &&
+        fused_plan_config(dtype, L, (int)num_groups, 0, cfg)) {
+        Scratch scratch(fused_scratch_bytes(cfg, L, num_groups, n), s);
         if (scratch.err != cudaSuccess) return from_cuda(scratch.err);
-        return from_cuda(launch_groupby_fused(keys, values, n, dtype, L, num_groups, state, scratch.p, s));
+        return from_cuda(launch_groupby_fused(keys, values, n, dtype, L, num_groups, cfg, state, scratch.p, s));
     }
-    if (n > 0 && partitioned_supported(dtype, L, num_groups, n, keys, values)) {
-        Scratch scratch(partitioned_scratch_bytes(dtype, L, num_groups, n), s);
+    PartChoice pc;
+    if (n > 0 && partitioned_supported(dtype, L, num_groups, n, keys, values) &&
+        partition_choose(dtype, L, num_groups, pc)) {
+        Scratch scratch(partitioned_scratch_bytes(pc, dtype, L, num_groups, n), s);
         if (scratch.err != cudaSuccess) return from_cuda(scratch.err);
-        return from_cuda(launch_groupby_partitioned(keys, values, n, dtype, L, num_groups, state, scratch.p, s));
+        return from_cuda(launch_groupby_partitioned(keys, values, n, dtype, L, num_groups, pc, state, scratch.p, s));
     }
     Scratch scratch(two_pass_scratch_bytes(num_groups), s);
     if (scratch.err != cudaSuccess) return from_cuda(scratch.err);

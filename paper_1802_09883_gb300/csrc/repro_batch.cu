@@ -452,7 +452,7 @@ cudaError_t launch_merge_items(int L, int dtype, const void* tasks, const void* 
 }
 
 repro_status plan_batch_host(const repro_task* tasks, int ntasks, int dtype, int L, size_t max_part_bytes,
-                             HostBatch& H) {
+                             HostBatch& H, int items_per_cta, const FusedPlanConfig* fixed_cfg) {
     if (ntasks < 0 || (ntasks > 0 && !tasks) || (dtype != REPRO_F64 && dtype != REPRO_F32) || L < 1 || L > 4)
         return REPRO_EINVAL;
     for (int t = 0; t < ntasks; ++t) {
@@ -483,14 +483,20 @@ repro_status plan_batch_host(const repro_task* tasks, int ntasks, int dtype, int
                            (int)tasks[t].num_groups, (unsigned char*)tasks[t].state,
                            (unsigned char*)tasks[t].state + sizeof(repro_state_header)};
     if (fast.empty()) return REPRO_OK;
-    if (!fused_plan_config(dtype, L, (int)gcap, sizeof(StageMeta) * 4, H.cfg)) return REPRO_ERANGE;
+    if (fixed_cfg) {
+        if (!fused_config_fits(dtype, L, (int)gcap, sizeof(StageMeta) * 8, *fixed_cfg)) return REPRO_ERANGE;
+        H.cfg = *fixed_cfg;
+    } else if (!fused_plan_config(dtype, L, (int)gcap, sizeof(StageMeta) * 8, H.cfg)) {
+        return REPRO_ERANGE;
+    }
     H.gcap = (int)gcap;
     const int R = H.cfg.R;
     long long total_tiles = 0;
     for (int t : fast) total_tiles += (tasks[t].n + R - 1) / R;
     H.ctas = device_info().sms * H.cfg.ctas_per_sm;
     const long long tpi_max = (1ll << 23) / R;
-    long long tpi = (total_tiles + 4ll * H.ctas - 1) / (4ll * H.ctas);
+    const long long per = (long long)std::max(1, items_per_cta) * H.ctas;
+    long long tpi = (total_tiles + per - 1) / per;
     tpi = std::max(8ll, std::min(tpi, tpi_max));
     auto part_records = [&](long long tp) {
         long long part = 0;
@@ -560,6 +566,9 @@ struct BatchPlan {
     int nitems = 0, nblks = 0;
     int ntasks = 0;
     long long gmax = 1;                 // largest group count of any task
+    int items_per_cta = 4;              // repro_batch_tune may change it
+    std::vector<repro_task> tasks;      // host copy, for re-planning
+    size_t items_cap = 0, blks_cap = 0, parts_cap = 0;  // device capacities (bytes)
     void** d_outs = nullptr;            // repro_batch_set_outputs
     MTask* d_tasks = nullptr;
     MItem* d_items = nullptr;
@@ -572,6 +581,8 @@ struct BatchPlan {
     // assigned largest first to the least-loaded lane.
     std::vector<repro_task> slow;
     std::vector<int> slow_lane;
+    std::vector<int> slow_part;       // 1: partitioned path with slow_choice, 0: two-pass path
+    std::vector<PartChoice> slow_choice;
     std::vector<cudaStream_t> lanes;
     std::vector<cudaEvent_t> joins;
     cudaEvent_t fork = nullptr;
@@ -581,6 +592,35 @@ struct BatchPlan {
 
 // Side streams for the tasks beyond the single-pass table.
 constexpr int kSlowLanes = 8;
+
+// (Re)allocate the plan's item, merge-block and partial arrays for H and
+// copy H's items and blocks to the device (synchronous).
+repro_status upload_items(BatchPlan& P, const HostBatch& H) {
+    P.nitems = (int)H.items.size();
+    P.nblks = (int)H.blks.size();
+    if (P.nitems == 0) return REPRO_OK;
+    const size_t ib = sizeof(MItem) * P.nitems;
+    const size_t bb = sizeof(MergeBlk) * std::max(1, P.nblks);
+    const size_t pb = std::max<size_t>(16, (size_t)H.part_recs * batch_rec_bytes(P.L));
+    cudaError_t e = cudaSuccess;
+    auto grow = [&](void** ptr, size_t& cap, size_t need) {
+        if (e != cudaSuccess || cap >= need) return;
+        cudaFree(*ptr);
+        *ptr = nullptr;
+        cap = 0;
+        e = cudaMalloc(ptr, need);
+        if (e == cudaSuccess) cap = need;
+    };
+    grow((void**)&P.d_items, P.items_cap, ib);
+    grow((void**)&P.d_blks, P.blks_cap, bb);
+    grow((void**)&P.d_partials, P.parts_cap, pb);
+    if (e == cudaSuccess && !P.d_counter) e = cudaMalloc(&P.d_counter, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemcpy(P.d_items, H.items.data(), ib, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && P.nblks)
+        e = cudaMemcpy(P.d_blks, H.blks.data(), sizeof(MergeBlk) * P.nblks, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? REPRO_ENOMEM : REPRO_ECUDA;
+    return REPRO_OK;
+}
 
 }  // namespace rp
 
@@ -617,29 +657,24 @@ repro_status repro_batch_prepare(const repro_task* tasks, int ntasks, repro_dtyp
         if (e == cudaSuccess) e = cudaMemcpy(P.d_tasks, H.tasks.data(), sizeof(MTask) * ntasks, cudaMemcpyHostToDevice);
         if (e != cudaSuccess) st = e == cudaErrorMemoryAllocation ? REPRO_ENOMEM : REPRO_ECUDA;
     }
-    if (st == REPRO_OK && P.nitems > 0) {
-        cudaError_t e = cudaMalloc(&P.d_items, sizeof(MItem) * P.nitems);
-        if (e == cudaSuccess) e = cudaMalloc(&P.d_blks, sizeof(MergeBlk) * std::max(1, P.nblks));
-        if (e == cudaSuccess) e = cudaMalloc(&P.d_partials, std::max<size_t>(16, (size_t)H.part_recs * batch_rec_bytes(L)));
-        if (e == cudaSuccess) e = cudaMalloc(&P.d_counter, sizeof(int));
-        if (e == cudaSuccess)
-            e = cudaMemcpy(P.d_items, H.items.data(), sizeof(MItem) * P.nitems, cudaMemcpyHostToDevice);
-        if (e == cudaSuccess && P.nblks)
-            e = cudaMemcpy(P.d_blks, H.blks.data(), sizeof(MergeBlk) * P.nblks, cudaMemcpyHostToDevice);
-        if (e != cudaSuccess) st = e == cudaErrorMemoryAllocation ? REPRO_ENOMEM : REPRO_ECUDA;
-    }
+    P.tasks.assign(tasks, tasks + ntasks);
+    if (st == REPRO_OK) st = upload_items(P, H);
     if (st == REPRO_OK && !P.slow.empty()) {
         // tasks beyond the single-pass table: the partitioned path where it
         // applies, else the two-pass path
-        size_t need = 16;
-        for (const repro_task& k : P.slow) {
-            const bool part = partitioned_supported(dtype, L, k.num_groups, k.n, k.keys, k.values);
-            need = std::max(need, part ? partitioned_scratch_bytes(dtype, L, k.num_groups, k.n)
-                                       : two_pass_scratch_bytes(k.num_groups));
-        }
         const int nl = std::min<int>(kSlowLanes, (int)P.slow.size());
         std::stable_sort(P.slow.begin(), P.slow.end(),
                          [](const repro_task& x, const repro_task& y) { return x.n > y.n; });
+        size_t need = 16;
+        for (const repro_task& k : P.slow) {
+            PartChoice pc{};
+            const bool part = partitioned_supported(dtype, L, k.num_groups, k.n, k.keys, k.values) &&
+                              partition_choose(dtype, L, k.num_groups, pc);
+            P.slow_part.push_back(part ? 1 : 0);
+            P.slow_choice.push_back(pc);
+            need = std::max(need, part ? partitioned_scratch_bytes(pc, dtype, L, k.num_groups, k.n)
+                                       : two_pass_scratch_bytes(k.num_groups));
+        }
         std::vector<long long> load(nl, 0);
         for (const repro_task& k : P.slow) {
             const int l = (int)(std::min_element(load.begin(), load.end()) - load.begin());
@@ -683,9 +718,9 @@ repro_status repro_batch_run(repro_batch_plan plan, void* stream) {
             const repro_task& k = P.slow[i];
             const int l = P.slow_lane[i];
             unsigned char* scratch = P.d_slow_scratch + (size_t)l * P.slow_each;
-            if (partitioned_supported(P.dtype, P.L, k.num_groups, k.n, k.keys, k.values))
-                e = launch_groupby_partitioned(k.keys, k.values, k.n, P.dtype, P.L, k.num_groups, k.state, scratch,
-                                               P.lanes[l]);
+            if (P.slow_part[i])
+                e = launch_groupby_partitioned(k.keys, k.values, k.n, P.dtype, P.L, k.num_groups, P.slow_choice[i],
+                                               k.state, scratch, P.lanes[l]);
             else
                 e = launch_groupby_two_pass(k.keys, k.values, k.n, P.dtype, P.L, k.num_groups, k.state, scratch,
                                             P.lanes[l]);
@@ -760,6 +795,56 @@ repro_status repro_batch_finalize(repro_batch_plan plan, void* stream) {
     }
     prof_end(PROF_FINALIZE, s);
     return REPRO_OK;
+}
+
+repro_status repro_batch_tune(repro_batch_plan plan, void* stream, double* best_ms) {
+    if (!plan) return REPRO_EINVAL;
+    BatchPlan& P = plan->p;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (best_ms) *best_ms = 0;
+    cudaEvent_t a = nullptr, b = nullptr;
+    if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess) {
+        if (a) cudaEventDestroy(a);
+        return REPRO_ECUDA;
+    }
+    repro_status st = REPRO_OK;
+    double best = 0;
+    int pick = P.items_per_cta;
+    for (int ipc : {1, 2, 4, 8, 16}) {
+        HostBatch H;
+        st = plan_batch_host(P.tasks.data(), P.ntasks, P.dtype, P.L, kBatchPartBytes, H, ipc, &P.cfg);
+        if (st == REPRO_OK) st = upload_items(P, H);
+        if (st != REPRO_OK) break;
+        std::vector<float> t;
+        for (int rep = 0; rep < 4 && st == REPRO_OK; ++rep) {  // first run untimed
+            if ((st = repro_batch_reset(plan, stream)) != REPRO_OK) break;
+            if (cudaEventRecord(a, s) != cudaSuccess) st = REPRO_ECUDA;
+            if (st == REPRO_OK) st = repro_batch_run(plan, stream);
+            if (st == REPRO_OK && cudaEventRecord(b, s) != cudaSuccess) st = REPRO_ECUDA;
+            if (st == REPRO_OK && cudaEventSynchronize(b) != cudaSuccess) st = REPRO_ECUDA;
+            float ms = 0;
+            if (st == REPRO_OK && cudaEventElapsedTime(&ms, a, b) != cudaSuccess) st = REPRO_ECUDA;
+            if (rep > 0) t.push_back(ms);
+        }
+        if (st != REPRO_OK) break;
+        std::sort(t.begin(), t.end());
+        const double med = t[t.size() / 2];
+        if (best == 0 || med < best) {
+            best = med;
+            pick = ipc;
+        }
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    if (st != REPRO_OK) return st;
+    HostBatch H;
+    st = plan_batch_host(P.tasks.data(), P.ntasks, P.dtype, P.L, kBatchPartBytes, H, pick, &P.cfg);
+    if (st == REPRO_OK) st = upload_items(P, H);
+    if (st == REPRO_OK) P.items_per_cta = pick;
+    if (st == REPRO_OK) st = repro_batch_reset(plan, stream);
+    if (st == REPRO_OK && cudaStreamSynchronize(s) != cudaSuccess) st = REPRO_ECUDA;
+    if (best_ms) *best_ms = best;
+    return st;
 }
 
 repro_status repro_batch_destroy(repro_batch_plan plan) {

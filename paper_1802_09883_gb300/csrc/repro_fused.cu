@@ -278,49 +278,70 @@ __global__ void __launch_bounds__(256) k_merge_partials(const unsigned char* __r
 
 namespace {
 
+// Whether a configuration is well formed and its layout (plus extra bytes)
+// fits ctas_per_sm times into one SM's shared memory.
 template <typename T>
-bool pick_config(int G, int L, const DeviceInfo& di, FusedPlanConfig& cfg, size_t extra = 0) {
-    static FusedPlanConfig forced{0, 0, 0, 0, 0};
-    static bool env_read = false;
-    if (!env_read) {  // tuning aid: REPRO_FUSED_CFG="S,R,ncw,ctas_per_sm[,copies]"
-        const char* e = getenv("REPRO_FUSED_CFG");
-        if (e) {
-            forced.copies = 0;
-            sscanf(e, "%d,%d,%d,%d,%d", &forced.S, &forced.R, &forced.ncw, &forced.ctas_per_sm, &forced.copies);
-        }
-        env_read = true;
-    }
-    // Prefer two CTAs per SM (barrier bubbles of one hide behind the other),
-    // then one CTA with deeper staging; lane-private table copies when the
-    // 32 copies fit next to the stages.
+bool config_fits(const FusedPlanConfig& c, int G, int L, const DeviceInfo& di, size_t extra) {
+    if (c.S < 2 || c.S > 8 || c.R < 1024 || c.R > 8192 || c.R % (128 * c.ncw) || (c.ncw != 8 && c.ncw != 16))
+        return false;
+    if (c.ctas_per_sm < 1 || c.ctas_per_sm > 2 || (c.copies != 1 && c.copies != 32)) return false;
+    const size_t bytes = fused_layout<T>(c.S, c.R, G, L, c.copies).total + extra;
+    return bytes * c.ctas_per_sm + 1024 * c.ctas_per_sm <= di.smem_per_sm && bytes <= di.smem_optin;
+}
+
+// The built-in rule: prefer two CTAs per SM (barrier bubbles of one hide
+// behind the other), then one CTA with deeper staging; lane-private table
+// copies when the 32 copies fit next to the stages.
+template <typename T>
+bool rule_config(int G, int L, const DeviceInfo& di, FusedPlanConfig& cfg, size_t extra) {
     const FusedPlanConfig cands[] = {{3, 2048, 8, 2, 0}, {2, 2048, 8, 2, 0}, {3, 4096, 16, 1, 0}, {4, 1024, 8, 2, 0},
-                                 {4, 2048, 16, 1, 0}, {3, 2048, 16, 1, 0}, {2, 2048, 16, 1, 0}, {2, 1024, 16, 1, 0}};
-    auto fits = [&](FusedPlanConfig c) {
-        if (c.S < 2 || c.R < 256 || c.R % (128 * c.ncw) || (c.ncw != 8 && c.ncw != 16) || c.ctas_per_sm < 1)
-            return false;
-        if (c.copies != 1 && c.copies != 32) return false;
-        const size_t bytes = fused_layout<T>(c.S, c.R, G, L, c.copies).total + extra;
-        return bytes * c.ctas_per_sm + 1024 * c.ctas_per_sm <= di.smem_per_sm && bytes <= di.smem_optin;
-    };
-    if (forced.S) {
-        FusedPlanConfig c = forced;
-        if (c.copies == 0) c.copies = 1;
-        if (fits(c)) {
-            cfg = c;
-            return true;
-        }
-    }
+                                     {4, 2048, 16, 1, 0}, {3, 2048, 16, 1, 0}, {2, 2048, 16, 1, 0}, {2, 1024, 16, 1, 0}};
     for (int copies : {32, 1}) {
         if (copies == 32 && G > 256) continue;
         for (FusedPlanConfig c : cands) {
             c.copies = copies;
-            if (fits(c)) {
+            if (config_fits<T>(c, G, L, di, extra)) {
                 cfg = c;
                 return true;
             }
         }
     }
     return false;
+}
+
+const FusedPlanConfig* env_config() {
+    static FusedPlanConfig forced{0, 0, 0, 0, 0};
+    static std::once_flag once;
+    std::call_once(once, [] {  // tuning aid: REPRO_FUSED_CFG="S,R,ncw,ctas_per_sm[,copies]"
+        const char* e = getenv("REPRO_FUSED_CFG");
+        if (e) {
+            FusedPlanConfig c{0, 0, 0, 0, 1};
+            if (sscanf(e, "%d,%d,%d,%d,%d", &c.S, &c.R, &c.ncw, &c.ctas_per_sm, &c.copies) >= 4) forced = c;
+        }
+    });
+    return forced.S ? &forced : nullptr;
+}
+
+// forced by the tuner (this thread) > REPRO_FUSED_CFG > tuned cache > rule;
+// each only if it fits.
+template <typename T>
+bool pick_config(int dtype, int G, int L, const DeviceInfo& di, FusedPlanConfig& cfg, size_t extra) {
+    if (const FusedPlanConfig* f = tune_forced_fused())
+        if (config_fits<T>(*f, G, L, di, extra)) {
+            cfg = *f;
+            return true;
+        }
+    if (const FusedPlanConfig* f = env_config())
+        if (config_fits<T>(*f, G, L, di, extra)) {
+            cfg = *f;
+            return true;
+        }
+    FusedPlanConfig t;
+    if (tune_lookup_fused(dtype, L, G, t) && config_fits<T>(t, G, L, di, extra)) {
+        cfg = t;
+        return true;
+    }
+    return rule_config<T>(G, L, di, cfg, extra);
 }
 
 long long env_flush_rows() {
@@ -363,8 +384,13 @@ cudaError_t dispatch_L(int L, int ncw, const FusedArgs& a, int ctas, size_t smem
 }  // namespace
 
 bool fused_plan_config(int dtype, int L, int G, size_t extra_smem, FusedPlanConfig& cfg) {
-    return dtype == REPRO_F64 ? pick_config<double>(G, L, device_info(), cfg, extra_smem)
-                              : pick_config<float>(G, L, device_info(), cfg, extra_smem);
+    return dtype == REPRO_F64 ? pick_config<double>(dtype, G, L, device_info(), cfg, extra_smem)
+                              : pick_config<float>(dtype, G, L, device_info(), cfg, extra_smem);
+}
+
+bool fused_config_fits(int dtype, int L, int G, size_t extra_smem, const FusedPlanConfig& cfg) {
+    return dtype == REPRO_F64 ? config_fits<double>(cfg, G, L, device_info(), extra_smem)
+                              : config_fits<float>(cfg, G, L, device_info(), extra_smem);
 }
 
 size_t fused_plan_smem(int dtype, int L, int G, const FusedPlanConfig& c) {
@@ -376,8 +402,7 @@ bool fused_supported(int dtype, int L, long long G, const void* keys, const void
     if (G > 65535) return false;
     if ((uintptr_t)keys % 16 || (uintptr_t)vals % 16) return false;
     FusedPlanConfig cfg;
-    return dtype == REPRO_F64 ? pick_config<double>((int)G, L, device_info(), cfg)
-                              : pick_config<float>((int)G, L, device_info(), cfg);
+    return fused_plan_config(dtype, L, (int)G, 0, cfg);
 }
 
 static int fused_ctas(long long ntiles, const FusedPlanConfig& cfg, const DeviceInfo& di) {
@@ -389,21 +414,16 @@ static int fused_ctas(long long ntiles, const FusedPlanConfig& cfg, const Device
     return (int)c;
 }
 
-size_t fused_scratch_bytes(int dtype, int L, long long G, long long n) {
-    FusedPlanConfig cfg;
-    const DeviceInfo& di = device_info();
-    const bool ok = dtype == REPRO_F64 ? pick_config<double>((int)G, L, di, cfg) : pick_config<float>((int)G, L, di, cfg);
-    if (!ok) return 0;
+size_t fused_scratch_bytes(const FusedPlanConfig& cfg, int L, long long G, long long n) {
     const long long ntiles = n / cfg.R;
-    return (size_t)fused_ctas(ntiles, cfg, di) * (size_t)G * (8 + 16 * (size_t)L);
+    return (size_t)fused_ctas(ntiles, cfg, device_info()) * (size_t)G * (8 + 16 * (size_t)L);
 }
 
 cudaError_t launch_groupby_fused(const int32_t* keys, const void* vals, long long n, int dtype, int L, long long G,
-                                 void* state, void* scratch, cudaStream_t s, int max_ctas) {
+                                 const FusedPlanConfig& cfg, void* state, void* scratch, cudaStream_t s,
+                                 int max_ctas) {
     const DeviceInfo& di = device_info();
-    FusedPlanConfig cfg;
-    const bool ok = dtype == REPRO_F64 ? pick_config<double>((int)G, L, di, cfg) : pick_config<float>((int)G, L, di, cfg);
-    if (!ok) return cudaErrorInvalidValue;
+    if (!fused_config_fits(dtype, L, (int)G, 0, cfg)) return cudaErrorInvalidValue;
     FusedArgs a;
     a.keys = keys;
     a.vals = vals;
@@ -495,14 +515,16 @@ extern "C" repro_status repro_groupby_sum_noalloc(const int32_t* keys, const voi
     if ((uintptr_t)state % 16) return REPRO_EINVAL;
     if (n == 0) return REPRO_OK;
     // only the fused path runs here: aligned inputs and a table that fits
-    if (!fused_supported(dtype, L, num_groups, keys, values)) return REPRO_ERANGE;
+    FusedPlanConfig cfg;
+    if (!fused_supported(dtype, L, num_groups, keys, values) || !fused_plan_config(dtype, L, (int)num_groups, 0, cfg))
+        return REPRO_ERANGE;
     const size_t per_cta = (size_t)num_groups * (8 + 16 * (size_t)L);
     const long long max_ctas = (long long)(kStaticPartialBytes / per_cta);
     if (max_ctas < 1) return REPRO_ERANGE;
     cudaError_t e;
     void* scratch = static_partials_address(e);
     if (!scratch) return REPRO_ECUDA;
-    e = launch_groupby_fused(keys, values, n, dtype, L, num_groups, state, scratch, (cudaStream_t)stream,
+    e = launch_groupby_fused(keys, values, n, dtype, L, num_groups, cfg, state, scratch, (cudaStream_t)stream,
                              (int)(max_ctas < 65535 ? max_ctas : 65535));
     return e == cudaSuccess ? REPRO_OK : REPRO_ECUDA;
 }

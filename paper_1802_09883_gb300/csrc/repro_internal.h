@@ -46,22 +46,42 @@ cudaError_t launch_groupby_two_pass(const int32_t* keys, const void* vals, long 
 struct FusedPlanConfig {
     int S, R, ncw, ctas_per_sm, copies;  // stages, rows per tile, consumer warps, CTAs per SM, table copies
 };
-// Tile / stage / warp configuration for a group table of G groups (extra_smem
-// bytes reserved on top of the kernel's layout); false if none fits.
+// The configuration for a group table of G groups (extra_smem bytes reserved
+// on top of the kernel's layout): the tuner's forced choice on this thread,
+// else REPRO_FUSED_CFG, else the tuned cache, else the built-in rule -- the
+// first that fits; false if none fits.  Callers choose once per call and pass
+// the configuration on, so scratch sizing and launch always agree.
 bool fused_plan_config(int dtype, int L, int G, size_t extra_smem, FusedPlanConfig& cfg);
+bool fused_config_fits(int dtype, int L, int G, size_t extra_smem, const FusedPlanConfig& cfg);
 size_t fused_plan_smem(int dtype, int L, int G, const FusedPlanConfig& cfg);
 bool fused_supported(int dtype, int L, long long G, const void* keys, const void* vals);
-size_t fused_scratch_bytes(int dtype, int L, long long G, long long n);
+size_t fused_scratch_bytes(const FusedPlanConfig& cfg, int L, long long G, long long n);
 // max_ctas > 0 caps the number of CTAs (and so the partial tables in scratch).
 cudaError_t launch_groupby_fused(const int32_t* keys, const void* vals, long long n, int dtype, int L, long long G,
-                                 void* state, void* scratch, cudaStream_t s, int max_ctas = 0);
+                                 const FusedPlanConfig& cfg, void* state, void* scratch, cudaStream_t s,
+                                 int max_ctas = 0);
 
 // Large group counts: partition by key range, then the multi-task kernel
-// over the partitions (repro_partition.cu).
+// over the partitions (repro_partition.cu).  A choice fixes the partition
+// width 2^shift and the multi-task kernel's configuration for it.
+struct PartChoice {
+    int shift;
+    FusedPlanConfig cfg;
+};
+bool partition_choose(int dtype, int L, long long G, PartChoice& pc);
 bool partitioned_supported(int dtype, int L, long long G, long long n, const void* keys, const void* vals);
-size_t partitioned_scratch_bytes(int dtype, int L, long long G, long long n);
+size_t partitioned_scratch_bytes(const PartChoice& pc, int dtype, int L, long long G, long long n);
 cudaError_t launch_groupby_partitioned(const int32_t* keys, const void* vals, long long n, int dtype, int L,
-                                       long long G, void* state, void* scratch, cudaStream_t s);
+                                       long long G, const PartChoice& pc, void* state, void* scratch, cudaStream_t s);
+
+// Measured choices (repro_tune.cu).  The cache holds, per (dtype, L, group
+// count rounded up to a power of two), a single-pass configuration and a
+// partition width; the tuner forces candidates on its own thread while it
+// times them.
+bool tune_lookup_fused(int dtype, int L, long long G, FusedPlanConfig& cfg);
+bool tune_lookup_shift(int dtype, int L, long long G, int& shift);
+const FusedPlanConfig* tune_forced_fused();
+int tune_forced_shift();  // 0: none
 
 // Multi-task single-pass kernel and its partial merge (repro_batch.cu); the
 // task / item / merge-block arrays are laid out as in multi_types.h.

@@ -329,39 +329,40 @@ struct PartPlan {
     long long max_items, max_blks, max_part_recs;
 };
 
-bool make_part_plan(int dtype, int L, long long G, long long n, PartPlan& pp) {
+// Candidate partition widths 2^shift: at most kMaxParts partitions and a
+// single-pass table that fits (with the 256 bytes of stage metadata).
+bool shift_usable(int dtype, int L, long long G, int shift, FusedPlanConfig& cfg) {
+    if (shift < 6 || shift > 12) return false;
+    const long long F = (G + (1ll << shift) - 1) >> shift;
+    if (F > kMaxParts) return false;
+    return fused_plan_config(dtype, L, 1 << shift, 256, cfg);
+}
+
+// The plan of one partitioned call, fully determined by the choice.
+bool make_part_plan(const PartChoice& pc, int L, long long G, long long n, PartPlan& pp) {
     const DeviceInfo& di = device_info();
-    // the largest power-of-two slice of groups whose table keeps two CTAs per
-    // SM (then one), with at most kMaxParts partitions
-    for (int cps_goal = 2; cps_goal >= 1; --cps_goal) {
-        for (int shift = 12; shift >= 6; --shift) {
-            const int Gp = 1 << shift;
-            const long long F = (G + Gp - 1) / Gp;
-            if (F > kMaxParts) break;
-            FusedPlanConfig cfg;
-            if (!fused_plan_config(dtype, L, Gp, 256, cfg)) continue;
-            if (cfg.ctas_per_sm < cps_goal) continue;
-            pp.pg.F = (int)F;
-            pp.pg.shift = shift;
-            pp.pg.Gp = Gp;
-            pp.cfg = cfg;
-            pp.ctas = di.sms * cfg.ctas_per_sm;
-            const long long R = cfg.R;
-            const long long total_tiles = (n + R - 1) / R + F;
-            pp.tpi = std::max(8ll, (total_tiles + 2ll * pp.ctas - 1) / (2ll * pp.ctas));
-            pp.tpi = std::min(pp.tpi, (1ll << 23) / R);
-            pp.max_items = total_tiles / pp.tpi + F + 1;
-            const long long max_split = std::min(F, total_tiles / pp.tpi + 1);
-            pp.max_blks = max_split * ((Gp + 31) / 32);
-            // only partitions with more than tpi tiles are split into several items
-            pp.max_part_recs = (total_tiles / pp.tpi + 1 + max_split) * (long long)Gp;
-            pp.pg.C = di.sms * 2;
-            pp.pg.chunk = ((n + pp.pg.C - 1) / pp.pg.C + 3) & ~3ll;
-            if (pp.pg.chunk < 4) pp.pg.chunk = 4;
-            return true;
-        }
-    }
-    return false;
+    const int Gp = 1 << pc.shift;
+    const long long F = (G + Gp - 1) / Gp;
+    if (F > kMaxParts || pc.shift < 6 || pc.shift > 12) return false;
+    pp.pg.F = (int)F;
+    pp.pg.shift = pc.shift;
+    pp.pg.Gp = Gp;
+    pp.cfg = pc.cfg;
+    pp.ctas = di.sms * pc.cfg.ctas_per_sm;
+    const long long R = pc.cfg.R;
+    const long long total_tiles = (n + R - 1) / R + F;
+    pp.tpi = std::max(8ll, (total_tiles + 2ll * pp.ctas - 1) / (2ll * pp.ctas));
+    pp.tpi = std::min(pp.tpi, (1ll << 23) / R);
+    pp.max_items = total_tiles / pp.tpi + F + 1;
+    const long long max_split = std::min(F, total_tiles / pp.tpi + 1);
+    pp.max_blks = max_split * ((Gp + 31) / 32);
+    // only partitions with more than tpi tiles are split into several items
+    pp.max_part_recs = (total_tiles / pp.tpi + 1 + max_split) * (long long)Gp;
+    pp.pg.C = di.sms * 2;
+    pp.pg.chunk = ((n + pp.pg.C - 1) / pp.pg.C + 3) & ~3ll;
+    if (pp.pg.chunk < 4) pp.pg.chunk = 4;
+    (void)L;
+    return true;
 }
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
@@ -392,23 +393,51 @@ PartScratch part_scratch_layout(const PartPlan& pp, long long n, int dtype, int 
 
 }  // namespace
 
+bool partition_choose(int dtype, int L, long long G, PartChoice& pc) {
+    // forced by the tuner (this thread) > tuned cache > rule; each only if usable
+    int forced = tune_forced_shift();
+    if (forced && shift_usable(dtype, L, G, forced, pc.cfg)) {
+        pc.shift = forced;
+        return true;
+    }
+    int tuned = 0;
+    if (tune_lookup_shift(dtype, L, G, tuned) && shift_usable(dtype, L, G, tuned, pc.cfg)) {
+        pc.shift = tuned;
+        return true;
+    }
+    // rule: the widest power-of-two slice whose table keeps two CTAs per SM
+    // (then one), with at most kMaxParts partitions
+    for (int cps_goal = 2; cps_goal >= 1; --cps_goal)
+        for (int shift = 12; shift >= 6; --shift) {
+            FusedPlanConfig cfg;
+            if (!shift_usable(dtype, L, G, shift, cfg)) continue;
+            if (cfg.ctas_per_sm < cps_goal) continue;
+            pc.shift = shift;
+            pc.cfg = cfg;
+            return true;
+        }
+    return false;
+}
+
 bool partitioned_supported(int dtype, int L, long long G, long long n, const void* keys, const void* vals) {
     if ((uintptr_t)keys % 16 || (uintptr_t)vals % 16) return false;
     if (n <= 0 || n > (1ll << 31) - 4ll * kMaxParts) return false;
-    PartPlan pp;
-    return make_part_plan(dtype, L, G, n, pp);
+    PartChoice pc;
+    return partition_choose(dtype, L, G, pc);
 }
 
-size_t partitioned_scratch_bytes(int dtype, int L, long long G, long long n) {
+size_t partitioned_scratch_bytes(const PartChoice& pc, int dtype, int L, long long G, long long n) {
     PartPlan pp;
-    if (!make_part_plan(dtype, L, G, n, pp)) return 0;
+    if (!make_part_plan(pc, L, G, n, pp)) return 0;
     return part_scratch_layout(pp, n, dtype, L).total;
 }
 
 cudaError_t launch_groupby_partitioned(const int32_t* keys, const void* vals, long long n, int dtype, int L,
-                                       long long G, void* state, void* scratch, cudaStream_t s) {
+                                       long long G, const PartChoice& pc, void* state, void* scratch,
+                                       cudaStream_t s) {
     PartPlan pp;
-    if (!make_part_plan(dtype, L, G, n, pp)) return cudaErrorInvalidValue;
+    if (!make_part_plan(pc, L, G, n, pp) || !fused_config_fits(dtype, L, pp.pg.Gp, 256, pc.cfg))
+        return cudaErrorInvalidValue;
     const PartScratch ly = part_scratch_layout(pp, n, dtype, L);
     unsigned char* b = (unsigned char*)scratch;
     int32_t* okeys = (int32_t*)(b + ly.okeys);

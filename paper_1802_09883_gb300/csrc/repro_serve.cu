@@ -512,8 +512,10 @@ repro_status repro_server_submit(repro_server srv, const int32_t* keys, const vo
     r->need = repro_state_bytes(dtype, L, num_groups);
     if (r->large) {
         const long long rows = std::min<long long>(n, S.cfg.chunk_rows);
-        r->need += partitioned_supported(dtype, L, num_groups, rows, keys, values)
-                       ? partitioned_scratch_bytes(dtype, L, num_groups, rows)
+        PartChoice pc;
+        r->need += partitioned_supported(dtype, L, num_groups, rows, keys, values) &&
+                           partition_choose(dtype, L, num_groups, pc)
+                       ? partitioned_scratch_bytes(pc, dtype, L, num_groups, rows)
                        : two_pass_scratch_bytes(num_groups);
     }
     if (cur != S.device) cudaSetDevice(cur);
