@@ -46,6 +46,7 @@ def parse():
     ap.add_argument("--L", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-tune", action="store_true", help="skip the untimed autotuning before the warm-up")
     ap.add_argument("--verify", action="store_true", help="check sampled groups against the oracle")
     ap.add_argument("--workload", default="sweep", choices=["sweep", "multicol", "batched", "serve"],
                     help="sweep: one grouped SUM (default); multicol: 4 SUM columns over two uint8 keys; "
@@ -154,6 +155,10 @@ def run_ours(args, rank, world, local_rank):
     st = R.State(G, L, torch.float64, device=dev)
     out = torch.empty(G, dtype=torch.float64, device=dev)
     stream = torch.cuda.current_stream(dev)
+
+    tuned = None
+    if not args.no_tune:  # untimed: measured configuration choice for this workload
+        tuned = R.tune(w.keys, w.values, G, L)
 
     def step():
         st.reset()
@@ -299,6 +304,7 @@ def run_ours(args, rank, world, local_rank):
             "e2e": e2e,
             "gpu_launches": int(launches),
             "clocks": clocks.summary(),
+            "tuned": tuned,
         }
         if verify is not None:
             result["verify"] = verify
@@ -507,6 +513,7 @@ def run_batched(args, local_rank):
     plan = R.BatchPlan([(k, v, st) for (k, v, _), st in zip(tasks, states)])
     plan.set_outputs(outs)
     t_plan = time.time() - t_plan
+    tune_ms = None if args.no_tune else plan.tune()  # untimed: item size for this batch
     side = torch.cuda.Stream(dev)
     side.wait_stream(torch.cuda.current_stream(dev))
     with torch.cuda.stream(side):
@@ -565,7 +572,8 @@ def run_batched(args, local_rank):
                 "e2e": None, "e2e_note": "inputs of this workload are generated on the device (tens of GB)",
                 "gpu_launches": int(per_step_launches * args.steps), "clocks": clocks.summary(),
                 "verify": {"tasks_checked": len(sample), "bit_equal_to_single_task": bool(same)},
-                "plan": {"prepare_s": t_plan, "tasks_beyond_smem_table": slow, "generate_s": t_gen}})
+                "plan": {"prepare_s": t_plan, "tasks_beyond_smem_table": slow, "generate_s": t_gen,
+                         "tuned_run_ms": tune_ms}})
     plan.close()
     return res
 

@@ -6,7 +6,9 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <map>
 #include <mutex>
+#include <tuple>
 
 #include "repro.h"
 #include "repro_internal.h"
@@ -33,6 +35,28 @@ const DeviceInfo& device_info() {
         have[dev] = true;
     }
     return cache[dev];
+}
+
+int resident_ctas(const void* kern, int threads, size_t smem) {
+    static std::mutex mu;
+    static std::map<std::tuple<int, const void*, int, size_t>, int> cache;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    const auto key = std::make_tuple(dev, kern, threads, smem);
+    {
+        std::lock_guard<std::mutex> lock(mu);
+        auto it = cache.find(key);
+        if (it != cache.end()) return it->second;
+    }
+    int nb = 0;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, threads, smem) != cudaSuccess) {
+        cudaGetLastError();
+        nb = 0;
+    }
+    std::lock_guard<std::mutex> lock(mu);
+    cache[key] = nb;
+    return nb;
 }
 
 static bool valid_dtype(int t) { return t == REPRO_F64 || t == REPRO_F32; }

@@ -390,6 +390,11 @@ cudaError_t launch_multi_t(const MultiArgs& a, int dtype, int ctas, size_t smem,
     auto kern = k_fused_multi<T, L, NCW>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
+    // a persistent grid must be resident at once (items come from a counter,
+    // so fewer CTAs only take longer)
+    const int occ = resident_ctas((const void*)kern, 32 * (NCW + 1), smem);
+    if (occ < 1) return cudaErrorInvalidConfiguration;
+    ctas = std::min(ctas, device_info().sms * occ);
     prof_begin(PROF_FUSED, s);
     kern<<<ctas, 32 * (NCW + 1), smem, s>>>(a, dtype);
     prof_end(PROF_FUSED, s);

@@ -17,6 +17,7 @@
 // partials into the caller's state (operator+=(repro), Algorithm 4's merge).
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstdint>
 #include <cstdio>
 #include <cstdlib>
@@ -284,7 +285,7 @@ template <typename T>
 bool config_fits(const FusedPlanConfig& c, int G, int L, const DeviceInfo& di, size_t extra) {
     if (c.S < 2 || c.S > 8 || c.R < 1024 || c.R > 8192 || c.R % (128 * c.ncw) || (c.ncw != 8 && c.ncw != 16))
         return false;
-    if (c.ctas_per_sm < 1 || c.ctas_per_sm > 2 || (c.copies != 1 && c.copies != 32)) return false;
+    if (c.ctas_per_sm < 1 || c.ctas_per_sm > 4 || (c.copies != 1 && c.copies != 32)) return false;
     const size_t bytes = fused_layout<T>(c.S, c.R, G, L, c.copies).total + extra;
     return bytes * c.ctas_per_sm + 1024 * c.ctas_per_sm <= di.smem_per_sm && bytes <= di.smem_optin;
 }
@@ -371,6 +372,21 @@ cudaError_t dispatch_ncw(int ncw, const FusedArgs& a, int ctas, size_t smem, cud
     return launch_fused_t<T, L, 16>(a, ctas, smem, s);
 }
 
+template <typename T, int L>
+const void* kernel_ncw(int ncw) {
+    return ncw == 8 ? (const void*)k_fused<T, L, 8> : (const void*)k_fused<T, L, 16>;
+}
+
+template <typename T>
+const void* kernel_of(int L, int ncw) {
+    switch (L) {
+        case 1: return kernel_ncw<T, 1>(ncw);
+        case 2: return kernel_ncw<T, 2>(ncw);
+        case 3: return kernel_ncw<T, 3>(ncw);
+        default: return kernel_ncw<T, 4>(ncw);
+    }
+}
+
 template <typename T>
 cudaError_t dispatch_L(int L, int ncw, const FusedArgs& a, int ctas, size_t smem, cudaStream_t s) {
     switch (L) {
@@ -433,15 +449,21 @@ cudaError_t launch_groupby_fused(const int32_t* keys, const void* vals, long lon
     a.S = cfg.S;
     a.C = cfg.copies;
     a.ntiles = n / cfg.R;
+    const size_t smem = dtype == REPRO_F64 ? fused_layout<double>(cfg.S, cfg.R, (int)G, L, cfg.copies).total
+                                           : fused_layout<float>(cfg.S, cfg.R, (int)G, L, cfg.copies).total;
+    // a persistent grid must be resident at once: never more CTAs per SM than
+    // registers and shared memory allow
+    const void* kern = dtype == REPRO_F64 ? kernel_of<double>(L, cfg.ncw) : kernel_of<float>(L, cfg.ncw);
+    const int occ = resident_ctas(kern, 32 * (cfg.ncw + 1), smem);
+    if (occ < 1) return cudaErrorInvalidConfiguration;
     int ctas = fused_ctas(a.ntiles, cfg, di);
+    ctas = std::min(ctas, di.sms * std::min(occ, cfg.ctas_per_sm));
     if (max_ctas > 0 && ctas > max_ctas) ctas = max_ctas;
     a.tiles_per_cta = (int)((a.ntiles + ctas - 1) / ctas);
     const long long fr = env_flush_rows();
     a.flush_rows = fr > 0 ? fr : (1ll << 23);
     a.partials = (unsigned char*)scratch;
     a.errors = &reinterpret_cast<repro_state_header*>(state)->errors;
-    const size_t smem = dtype == REPRO_F64 ? fused_layout<double>(cfg.S, cfg.R, (int)G, L, cfg.copies).total
-                                           : fused_layout<float>(cfg.S, cfg.R, (int)G, L, cfg.copies).total;
     cudaError_t e = dtype == REPRO_F64 ? dispatch_L<double>(L, cfg.ncw, a, ctas, smem, s)
                                        : dispatch_L<float>(L, cfg.ncw, a, ctas, smem, s);
     if (e != cudaSuccess) return e;

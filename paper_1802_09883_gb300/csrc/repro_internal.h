@@ -28,6 +28,10 @@ cudaMemPool_t library_pool(cudaError_t& err);
 int groupby_dispatch(const int32_t* keys, const void* values, long long n, int dtype, int L, long long num_groups,
                      void* state, cudaStream_t s);
 
+// CTAs of `kern` (threads per CTA, dynamic shared memory) that fit on one SM
+// at once (opts the kernel into that much shared memory first); 0 if none.
+int resident_ctas(const void* kern, int threads, size_t smem);
+
 // Profiling hooks (repro_profile_enable / repro_profile_read) and the launch
 // counter (repro_launch_count).
 enum ProfKernel { PROF_WINDOW, PROF_ACCUM, PROF_FUSED, PROF_PARTITION, PROF_MERGE, PROF_FINALIZE, PROF_FP64,

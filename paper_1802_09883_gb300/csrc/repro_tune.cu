@@ -138,7 +138,7 @@ repro_status repro_tune_groupby(const int32_t* keys, const void* values, int64_t
         for (int S : {2, 3, 4})
             for (int R : {1024, 2048, 4096})
                 for (int ncw : {8, 16})
-                    for (int cps : {1, 2})
+                    for (int cps : {1, 2, 3, 4})
                         for (int copies : {1, 32}) {
                             const FusedPlanConfig c{S, R, ncw, cps, copies};
                             if (fused_config_fits(dtype, L, (int)G, 0, c)) cands.push_back(c);
