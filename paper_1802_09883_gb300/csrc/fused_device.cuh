@@ -98,8 +98,17 @@ __device__ __forceinline__ void add_row(const Split& s, int K, const Table& t, i
     if (j + 2 < L && s.kb >= 2 && low != 0) add_digit(t, t.at(g, j + 2, copy), low);
 }
 
+// CTA-table window of a group no row has reached yet (its bins are zero).
+constexpr int kNoWindow = -1;
+// Bit of a group's flag word: the group is on this tile's raise list.
+constexpr unsigned kQueued = 0x80000000u;
+
 // Phase A for one row: add it, flag it, or defer it until its group's window
-// is raised.
+// is raised.  The first row of a group claims the window with one
+// compare-and-swap (no raise is needed while the bins are zero); a row above
+// an established window is deferred, and the first such row of the tile puts
+// the group on the raise list.  Within phase A a window changes only from
+// kNoWindow, so every add lands at the window the tile ends with.
 template <typename T, int L>
 __device__ __forceinline__ void consume_row(int g, T b, int idx, int G, const Table& t, int copy, int* sK,
                                             int* sKp, unsigned* sF, unsigned short* dlist, int* rlist, int* cnt,
@@ -114,13 +123,18 @@ __device__ __forceinline__ void consume_row(int g, T b, int idx, int G, const Ta
         return;
     }
     if (s.mant == 0) return;
-    const int K = sK[g];
+    int K = sK[g];
+    if (K < 0) {
+        const int old = atomicCAS(&sK[g], kNoWindow, s.kb);
+        K = old < 0 ? s.kb : old;
+    }
     if (s.kb <= K) {
         add_row<T, L>(s, K, t, g, copy);
         return;
     }
     dlist[atomicAdd(&cnt[0], 1)] = (unsigned short)idx;
-    if (atomicMax(&sKp[g], s.kb) == K) rlist[atomicAdd(&cnt[1], 1)] = g;  // first raiser of g in this tile
+    atomicMax(&sKp[g], s.kb);
+    if (!(atomicOr(&sF[g], kQueued) & kQueued)) rlist[atomicAdd(&cnt[1], 1)] = g;
 }
 
 // Shared-window addresses of the hot loop's arrays.
@@ -223,7 +237,7 @@ __device__ __forceinline__ void consume_quad(const SAddr& sa, const int32_t* tk,
 // and add the deferred rows.  Consumer-uniform; uses named barrier 1.
 template <typename T, int L>
 __device__ __forceinline__ void raise_and_add(int nr, int nd, const int32_t* tk, const T* tv, const Table& t,
-                                              int* sK, const int* sKp, const unsigned short* dlist,
+                                              int* sK, const int* sKp, unsigned* sF, const unsigned short* dlist,
                                               const int* rlist, int ctid, int NC) {
     for (int i = ctid; i < nr * t.C; i += NC) {
         const int g = rlist[i / t.C];
@@ -243,7 +257,10 @@ __device__ __forceinline__ void raise_and_add(int nr, int nd, const int32_t* tk,
         }
     }
     named_bar_sync(1, NC);
-    for (int i = ctid; i < nr; i += NC) sK[rlist[i]] = sKp[rlist[i]];
+    for (int i = ctid; i < nr; i += NC) {
+        sK[rlist[i]] = sKp[rlist[i]];
+        sF[rlist[i]] &= ~kQueued;
+    }
     named_bar_sync(1, NC);
     for (int i = ctid; i < nd; i += NC) {
         const int r = dlist[i];
@@ -278,14 +295,14 @@ __device__ void flush_partial(unsigned char* part, int G, const Table& t, const 
         }
         if (first) {
             *pK = K;
-            *pF = sF[g];
+            *pF = sF[g] & ~kQueued;
         } else {
             const int d = K - *pK;  // the CTA window only rises
 #pragma unroll
             for (int j = L - 1; j >= 0; --j)
                 if (j - d >= 0) acc[j] += bin_read(&pb[2 * (j - d)], &pb[2 * (j - d) + 1]);
             *pK = K;
-            *pF |= sF[g];
+            *pF |= sF[g] & ~kQueued;
         }
 #pragma unroll
         for (int j = 0; j < L; ++j) bin_write(&pb[2 * j], &pb[2 * j + 1], acc[j]);

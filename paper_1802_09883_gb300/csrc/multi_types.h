@@ -15,6 +15,7 @@ struct MTask {
     int G_hdr;            // num_groups its state header must show
     unsigned char* hdr;   // the state's header (checks, error word)
     unsigned char* recs;  // the task's first group record
+    const int* win;       // per group its window (K of its largest |value|, -1: none), or null
 };
 
 struct MItem {

@@ -47,8 +47,9 @@ __device__ __forceinline__ bool task_header_ok(const unsigned char* hdr, int dty
 template <typename T, int L>
 __device__ __forceinline__ void raise_and_add_multi(int nr, int nd, const int32_t* tk, const T* tv,
                                                     const int32_t* gk, const T* gv, int rows_tma, const Table& t,
-                                                    int* sK, const int* sKp, const unsigned short* dlist,
-                                                    const int* rlist, int ctid, int NC) {
+                                                    int* sK, const int* sKp, unsigned* sF,
+                                                    const unsigned short* dlist, const int* rlist, int ctid,
+                                                    int NC) {
     for (int i = ctid; i < nr * t.C; i += NC) {
         const int g = rlist[i / t.C];
         const int copy = i % t.C;
@@ -67,7 +68,10 @@ __device__ __forceinline__ void raise_and_add_multi(int nr, int nd, const int32_
         }
     }
     named_bar_sync(1, NC);
-    for (int i = ctid; i < nr; i += NC) sK[rlist[i]] = sKp[rlist[i]];
+    for (int i = ctid; i < nr; i += NC) {
+        sK[rlist[i]] = sKp[rlist[i]];
+        sF[rlist[i]] &= ~kQueued;
+    }
     named_bar_sync(1, NC);
     for (int i = ctid; i < nd; i += NC) {
         const int r = dlist[i];
@@ -117,13 +121,13 @@ __device__ void flush_table(unsigned char* recs, int G, const Table& t, int* sK,
                 if (js >= 0) acc[j] += bin_read(&pb[2 * js], &pb[2 * js + 1]);
             }
         }
-        const unsigned f = sF[g] | (overwrite ? 0u : *pF);
+        const unsigned f = (sF[g] & ~kQueued) | (overwrite ? 0u : *pF);
 #pragma unroll
         for (int j = 0; j < L; ++j) bin_write(&pb[2 * j], &pb[2 * j + 1], acc[j]);
         *pK = K;
         *pF = f;
-        sK[g] = 0;
-        sKp[g] = 0;
+        sK[g] = kNoWindow;
+        sKp[g] = kNoWindow;
         sF[g] = 0;
     }
 }
@@ -138,8 +142,8 @@ __device__ void clear_table(int G, const Table& t, int* sK, int* sKp, unsigned* 
                 t.lo[x] = 0;
                 t.hi[x] = 0;
             }
-        sK[g] = 0;
-        sKp[g] = 0;
+        sK[g] = kNoWindow;
+        sKp[g] = kNoWindow;
         sF[g] = 0;
     }
 }
@@ -176,8 +180,8 @@ __global__ void __launch_bounds__(32 * (NCW + 1)) k_fused_multi(MultiArgs a, int
         tab.hi[i] = 0;
     }
     for (int g = tid; g < a.Gcap; g += blockDim.x) {
-        sK[g] = 0;
-        sKp[g] = 0;
+        sK[g] = kNoWindow;
+        sKp[g] = kNoWindow;
         sF[g] = 0;
     }
     if (tid < 16) ctl[tid] = 0;
@@ -258,6 +262,10 @@ __global__ void __launch_bounds__(32 * (NCW + 1)) k_fused_multi(MultiArgs a, int
         const MItem it = a.items[sm.item];
         const MTask tk = a.tasks[it.task];
         const int G = tk.G;
+        if (tk.win && sm.row0 == it.row0) {  // known windows: no row of the item raises one
+            for (int g = ctid; g < G; g += NC) sK[g] = sKp[g] = (int)tk.win[g];
+            named_bar_sync(1, NC);
+        }
         int* cnt = &ctl[2 * (tcount % 3)];
         const int32_t* tk_s = skeys + (size_t)s * R;
         const T* tv_s = svals + (size_t)s * R;
@@ -277,8 +285,8 @@ __global__ void __launch_bounds__(32 * (NCW + 1)) k_fused_multi(MultiArgs a, int
         }
         const int nd = cnt[0], nr = cnt[1];
         if (nr > 0) {
-            raise_and_add_multi<T, L>(nr, nd, tk_s, tv_s, gk, gv, sm.rows_tma, tab, sK, sKp, dlist, rlist, ctid,
-                                      NC);
+            raise_and_add_multi<T, L>(nr, nd, tk_s, tv_s, gk, gv, sm.rows_tma, tab, sK, sKp, sF, dlist, rlist,
+                                      ctid, NC);
             named_bar_sync(1, NC);
         }
         __syncwarp();
@@ -486,7 +494,7 @@ repro_status plan_batch_host(const repro_task* tasks, int ntasks, int dtype, int
     for (int t = 0; t < ntasks; ++t)
         H.tasks[t] = MTask{tasks[t].keys, tasks[t].values, tasks[t].n, (int)tasks[t].num_groups,
                            (int)tasks[t].num_groups, (unsigned char*)tasks[t].state,
-                           (unsigned char*)tasks[t].state + sizeof(repro_state_header)};
+                           (unsigned char*)tasks[t].state + sizeof(repro_state_header), nullptr};
     if (fast.empty()) return REPRO_OK;
     if (fixed_cfg) {
         if (!fused_config_fits(dtype, L, (int)gcap, sizeof(StageMeta) * 8, *fixed_cfg)) return REPRO_ERANGE;

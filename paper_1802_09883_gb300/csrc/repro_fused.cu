@@ -76,8 +76,8 @@ __global__ void __launch_bounds__(32 * (NCW + 1)) k_fused(FusedArgs a) {
         tab.hi[i] = 0;
     }
     for (int g = tid; g < G; g += blockDim.x) {
-        sK[g] = 0;
-        sKp[g] = 0;
+        sK[g] = kNoWindow;
+        sKp[g] = kNoWindow;
         sF[g] = 0;
     }
     if (tid < 16) ctl[tid] = 0;
@@ -163,7 +163,7 @@ __global__ void __launch_bounds__(32 * (NCW + 1)) k_fused(FusedArgs a) {
         if (*abort_flag) break;
         const int nd = cnt[0], nr = cnt[1];
         if (nr > 0) {
-            raise_and_add<T, L>(nr, nd, tk, tv, tab, sK, sKp, dlist, rlist, ctid, NC);
+            raise_and_add<T, L>(nr, nd, tk, tv, tab, sK, sKp, sF, dlist, rlist, ctid, NC);
             named_bar_sync(1, NC);
         }
         __syncwarp();
@@ -191,7 +191,7 @@ __global__ void __launch_bounds__(32 * (NCW + 1)) k_fused(FusedArgs a) {
         named_bar_sync(1, NC);
         const int nd = cnt[0], nr = cnt[1];
         if (nr > 0) {
-            raise_and_add<T, L>(nr, nd, tk, tv, tab, sK, sKp, dlist, rlist, ctid, NC);
+            raise_and_add<T, L>(nr, nd, tk, tv, tab, sK, sKp, sF, dlist, rlist, ctid, NC);
         }
     }
     if (__any_sync(0xffffffffu, bad_key) && (ctid & 31) == 0) atomicOr(a.errors, REPRO_ERR_KEY);

@@ -67,9 +67,11 @@ cudaError_t launch_groupby_fused(const int32_t* keys, const void* vals, long lon
 
 // Large group counts: partition by key range, then the multi-task kernel
 // over the partitions (repro_partition.cu).  A choice fixes the partition
-// width 2^shift and the multi-task kernel's configuration for it.
+// width 2^shift, the coarse width 2^shift1 of a first pass (0: one pass) and
+// the multi-task kernel's configuration.
 struct PartChoice {
     int shift;
+    int shift1;
     FusedPlanConfig cfg;
 };
 bool partition_choose(int dtype, int L, long long G, PartChoice& pc);

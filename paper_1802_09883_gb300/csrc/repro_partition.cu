@@ -5,21 +5,33 @@
 // owning a disjoint slice of the caller's state (Algorithm 4's private
 // tables; the slices make the merge into the shared table a plain write).
 //
-//   k_part_hist     per CTA chunk, rows per partition (and bad keys)
-//   k_part_scan     partition starts (4-row aligned for the TMA copies) and
-//                   each CTA's write cursor in every partition
-//   k_part_scatter  copy every row to its partition with its key made local
-//                   (row order inside a partition does not matter: the sum
-//                   is exact)
-//   k_part_plan     turn partition sizes into tasks and work items on the
-//                   device (no host round trip)
-// then launch_multi / launch_merge_items (repro_batch.cu).
+// Up to 64 partitions the rows are partitioned in one pass.  Beyond that a
+// single pass would write runs of only a few rows per partition per tile
+// (scattered stores), so the rows are partitioned twice, as the paper's
+// multi-pass radix partitioning does for large fan-outs: a coarse pass by the
+// high key bits, then, inside every coarse partition, a fine pass by the
+// next bits.  Each pass:
+//
+//   k_part_hist     per unit (a CTA's chunk of rows, or a chunk of one
+//                   coarse partition), rows per bucket (and bad keys)
+//   k_scan_totals / k_scan_starts / k_scan_offsets
+//                   partition totals, 4-row-aligned partition starts (for the
+//                   TMA copies) and every unit's write cursor per bucket
+//   k_part_scatter  copy every row to its partition, tile by tile sorted in
+//                   shared memory so that stores are coalesced runs (row
+//                   order inside a partition does not matter: the sum is
+//                   exact)
+//
+// then k_part_plan turns the final partition sizes into tasks and work items
+// on the device (no host round trip) and launch_multi / launch_merge_items
+// (repro_batch.cu) aggregate them.
 #include <cuda_runtime.h>
 
 #include <algorithm>
 #include <cstdint>
 
 #include "multi_types.h"
+#include "repro_device.cuh"
 #include "repro.h"
 #include "repro_internal.h"
 
@@ -28,83 +40,187 @@ namespace rp {
 namespace {
 
 constexpr int kPartThreads = 512;
-constexpr int kScatterRows = 8;  // rows per thread per scatter tile
-constexpr int kMaxParts = 4096;
+constexpr int kScatterRows = 8;          // rows per thread per scatter tile
+constexpr int kMaxParts = 8192;          // final partitions
+constexpr int kOneLevelParts = 64;       // beyond this, two passes
+constexpr long long kChunkRows = 32768;  // rows per unit of the fine pass
 
-struct PartGeom {
-    int F;            // partitions
-    int shift;        // partition = key >> shift
-    int Gp;           // groups per partition (2^shift)
-    int C;            // CTAs of the partition passes
-    long long chunk;  // rows per CTA chunk (multiple of 4)
+// Geometry of one partition pass: a row with key k goes to bucket
+// (k >> shift) & bmask and is written with key k & kmask.
+struct PassGeom {
+    int B;           // buckets per unit
+    int shift;
+    unsigned bmask;
+    unsigned kmask;
+    int check;       // 1: keys outside [0, G) are flagged and dropped
+    int G;
+    int ustride, bstride;  // counts / offsets of unit u, bucket j at u * ustride + j * bstride
 };
 
-__global__ void __launch_bounds__(kPartThreads) k_part_hist(const int32_t* __restrict__ keys, long long n, int G,
-                                                            PartGeom pg, int* __restrict__ counts,
-                                                            unsigned* __restrict__ errors) {
-    extern __shared__ int s_hist[];
-    for (int p = threadIdx.x; p < pg.F; p += blockDim.x) s_hist[p] = 0;
-    __syncthreads();
-    const long long beg = blockIdx.x * pg.chunk;
-    const long long end = max(beg, min(n, beg + pg.chunk));  // CTAs past the data count nothing
-    bool bad = false;
-    // 4 keys per thread per step (beg is a multiple of 4 and keys 16-byte aligned)
-    const long long n4 = beg + ((end - beg) & ~3ll);
-    for (long long i = beg + 4 * (long long)threadIdx.x; i < n4; i += 4ll * blockDim.x) {
-        const int4 k = *reinterpret_cast<const int4*>(keys + i);
-        const int ks[4] = {k.x, k.y, k.z, k.w};
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            if ((unsigned)ks[q] < (unsigned)G) atomicAdd(&s_hist[ks[q] >> pg.shift], 1);
-            else bad = true;
-        }
+// Rows of a unit: a CTA's fixed chunk of the input, or an entry of a chunk
+// list (the fine pass over the coarse partitions).
+struct PartChunk {
+    long long beg, end;
+    int seg;  // partition the rows belong to
+    int pad;
+};
+
+struct Units {
+    long long chunk;          // rows per CTA chunk (chunks == nullptr)
+    long long n;              // rows of the input (chunks == nullptr)
+    const PartChunk* chunks;  // chunk list, or nullptr
+    const int* nchunks;       // its length (device)
+};
+
+__device__ __forceinline__ bool unit_rows(const Units& u, int unit, long long& beg, long long& end) {
+    if (u.chunks) {
+        if (unit >= *u.nchunks) return false;
+        beg = u.chunks[unit].beg;
+        end = u.chunks[unit].end;
+        return true;
     }
-    for (long long i = n4 + threadIdx.x; i < end; i += blockDim.x) {
-        const int k = keys[i];
-        if ((unsigned)k < (unsigned)G) atomicAdd(&s_hist[k >> pg.shift], 1);
-        else bad = true;
-    }
-    if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(errors, REPRO_ERR_KEY);
-    __syncthreads();
-    for (int p = threadIdx.x; p < pg.F; p += blockDim.x) counts[(size_t)p * pg.C + blockIdx.x] = s_hist[p];
+    beg = unit * u.chunk;
+    end = max(beg, min(u.n, beg + u.chunk));  // units past the data hold nothing
+    return true;
 }
 
-// One block: per partition its total and 4-aligned start; per (partition, CTA)
-// the CTA's first output row.
-__global__ void __launch_bounds__(1024) k_part_scan(const int* __restrict__ counts, PartGeom pg,
-                                                    int* __restrict__ offsets, long long* __restrict__ pstart,
-                                                    long long* __restrict__ pcount) {
-    __shared__ long long s_tot[1024];
-    const int per = (pg.F + blockDim.x - 1) / blockDim.x;  // partitions per thread (consecutive)
-    const int p0 = threadIdx.x * per;
-    long long mine = 0;
-    for (int p = p0; p < min(pg.F, p0 + per); ++p) {
+// A chunk list is walked grid-stride; a fixed chunking has one unit per CTA.
+__device__ __forceinline__ int unit_step(const Units& u) { return u.chunks ? (int)gridDim.x : 1 << 30; }
+
+__global__ void __launch_bounds__(kPartThreads) k_part_hist(const int32_t* __restrict__ keys, Units units,
+                                                            PassGeom pg, int* __restrict__ counts,
+                                                            unsigned* __restrict__ errors) {
+    extern __shared__ int s_hist[];
+    bool bad = false;
+    for (int unit = blockIdx.x;; unit += unit_step(units)) {
+        long long beg, end;
+        if (!unit_rows(units, unit, beg, end)) break;
+        for (int p = threadIdx.x; p < pg.B; p += blockDim.x) s_hist[p] = 0;
+        __syncthreads();
+        // 4 keys per thread per step (beg is a multiple of 4, keys 16-byte aligned)
+        const long long n4 = beg + ((end - beg) & ~3ll);
+        for (long long i = beg + 4 * (long long)threadIdx.x; i < n4; i += 4ll * blockDim.x) {
+            const int4 k = *reinterpret_cast<const int4*>(keys + i);
+            const int ks[4] = {k.x, k.y, k.z, k.w};
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                if (!pg.check || (unsigned)ks[q] < (unsigned)pg.G)
+                    atomicAdd(&s_hist[((unsigned)ks[q] >> pg.shift) & pg.bmask], 1);
+                else
+                    bad = true;
+            }
+        }
+        for (long long i = n4 + threadIdx.x; i < end; i += blockDim.x) {
+            const int k = keys[i];
+            if (!pg.check || (unsigned)k < (unsigned)pg.G)
+                atomicAdd(&s_hist[((unsigned)k >> pg.shift) & pg.bmask], 1);
+            else
+                bad = true;
+        }
+        __syncthreads();
+        for (int p = threadIdx.x; p < pg.B; p += blockDim.x)
+            counts[(size_t)unit * pg.ustride + (size_t)p * pg.bstride] = s_hist[p];
+        __syncthreads();
+        if (!units.chunks) break;
+    }
+    if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(errors, REPRO_ERR_KEY);
+}
+
+// Partitions of a scan: F = segments * B; segment s owns units
+// [cbase[s], cbase[s] + nunits[s]) (one segment of `units` units when cbase is
+// null); partition p = s * B + j.
+struct ScanGeom {
+    int F, B;
+    int ustride, bstride;
+    int units;
+    const int* cbase;
+    const int* nunits;
+};
+
+__device__ __forceinline__ void scan_segment(const ScanGeom& sg, int p, int& j, int& cb, int& nu) {
+    const int s = p / sg.B;
+    j = p - s * sg.B;
+    cb = sg.cbase ? sg.cbase[s] : 0;
+    nu = sg.cbase ? sg.nunits[s] : sg.units;
+}
+
+// One warp per partition: its row total.
+__global__ void __launch_bounds__(256) k_scan_totals(const int* __restrict__ counts, ScanGeom sg,
+                                                     long long* __restrict__ ptot) {
+    const int lane = threadIdx.x & 31;
+    const int nw = gridDim.x * (blockDim.x >> 5);
+    for (int p = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; p < sg.F; p += nw) {
+        int j, cb, nu;
+        scan_segment(sg, p, j, cb, nu);
         long long t = 0;
-        for (int c = 0; c < pg.C; ++c) t += counts[(size_t)p * pg.C + c];
-        pcount[p] = t;
-        mine += (t + 3) & ~3ll;
+        for (int k = lane; k < nu; k += 32) t += counts[(size_t)(cb + k) * sg.ustride + (size_t)j * sg.bstride];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+        if (lane == 0) ptot[p] = t;
     }
-    s_tot[threadIdx.x] = mine;
+}
+
+// One block: 4-row-aligned partition starts (exclusive scan over partitions).
+__global__ void __launch_bounds__(1024) k_scan_starts(const long long* __restrict__ ptot, int F,
+                                                      long long* __restrict__ pstart,
+                                                      long long* __restrict__ pcount) {
+    __shared__ long long s_w[33];
+    const int per = (F + blockDim.x - 1) / blockDim.x;
+    const int p0 = threadIdx.x * per, p1 = min(F, p0 + per);
+    long long local = 0;
+    for (int p = p0; p < p1; ++p) local += (ptot[p] + 3) & ~3ll;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    long long incl = local;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const long long y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    if (lane == 31) s_w[warp] = incl;
     __syncthreads();
-    // exclusive scan over the per-thread totals (1024 entries, simple and rare)
-    if (threadIdx.x == 0) {
-        long long run = 0;
-        for (int i = 0; i < (int)blockDim.x; ++i) {
-            const long long v = s_tot[i];
-            s_tot[i] = run;
-            run += v;
+    if (warp == 0) {
+        const int nw = blockDim.x >> 5;
+        const long long w = lane < nw ? s_w[lane] : 0;
+        long long wi = w;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const long long y = __shfl_up_sync(0xffffffffu, wi, o);
+            if (lane >= o) wi += y;
         }
+        if (lane < nw) s_w[lane] = wi - w;
     }
     __syncthreads();
-    long long run = s_tot[threadIdx.x];
-    for (int p = p0; p < min(pg.F, p0 + per); ++p) {
+    long long run = s_w[warp] + incl - local;
+    for (int p = p0; p < p1; ++p) {
         pstart[p] = run;
-        long long cur = run;
-        for (int c = 0; c < pg.C; ++c) {
-            offsets[(size_t)p * pg.C + c] = (int)cur;
-            cur += counts[(size_t)p * pg.C + c];
+        pcount[p] = ptot[p];
+        run += (ptot[p] + 3) & ~3ll;
+    }
+}
+
+// One warp per partition: every unit's first output row in it.
+__global__ void __launch_bounds__(256) k_scan_offsets(const int* __restrict__ counts, ScanGeom sg,
+                                                      const long long* __restrict__ pstart,
+                                                      int* __restrict__ offsets) {
+    const int lane = threadIdx.x & 31;
+    const int nw = gridDim.x * (blockDim.x >> 5);
+    for (int p = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; p < sg.F; p += nw) {
+        int j, cb, nu;
+        scan_segment(sg, p, j, cb, nu);
+        long long run = pstart[p];
+        for (int k0 = 0; k0 < nu; k0 += 32) {
+            const int k = k0 + lane;
+            const size_t at = (size_t)(cb + k) * sg.ustride + (size_t)j * sg.bstride;
+            const int v = k < nu ? counts[at] : 0;
+            int incl = v;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += y;
+            }
+            if (k < nu) offsets[at] = (int)(run + incl - v);
+            run += __shfl_sync(0xffffffffu, incl, 31);
         }
-        run += (pcount[p] + 3) & ~3ll;
     }
 }
 
@@ -165,93 +281,185 @@ __device__ int block_exclusive_scan(int* a, int n, int* warp_tot) {
     return total;
 }
 
-// Copy every row to its partition, one tile of kScatterRows * blockDim.x rows at a
-// time: every row takes its rank in its partition with one shared atomic, a
-// block scan gives each partition its place in the tile and one global slot
-// range per tile, rows are sorted in shared memory, and consecutive threads
-// then write consecutive runs (coalesced stores).
+// Copy every row of a unit to its bucket's cursor, one tile of
+// kScatterRows * blockDim.x rows at a time: every row takes its rank in its
+// bucket with one shared atomic, a block scan gives each bucket its place in
+// the tile and one global slot range per tile, rows are sorted in shared
+// memory, and consecutive threads then write consecutive runs (coalesced
+// stores).
 template <typename T>
 __global__ void __launch_bounds__(kPartThreads) k_part_scatter(const int32_t* __restrict__ keys,
-                                                               const T* __restrict__ vals, long long n, int G,
-                                                               PartGeom pg, const int* __restrict__ offsets,
+                                                               const T* __restrict__ vals, Units units,
+                                                               PassGeom pg, const int* __restrict__ offsets,
                                                                int32_t* __restrict__ okeys, T* __restrict__ ovals) {
     extern __shared__ __align__(16) unsigned char s_raw[];
     constexpr int RPT = kScatterRows;  // rows per thread per tile
     const int TILE = RPT * kPartThreads;
-    T* s_vals = reinterpret_cast<T*>(s_raw);                              // [TILE]
-    int* s_keys = reinterpret_cast<int*>(s_vals + TILE);                  // [TILE] global keys, sorted
-    int* s_cur = s_keys + TILE;                                           // [F] global write cursor
-    int* s_cnt = s_cur + pg.F;                                            // [F] rows per partition in the tile
-    int* s_gb = s_cnt + pg.F;                                             // [F] global base of the tile's run
-    int* s_wt = s_gb + pg.F;                                              // [33] scan scratch
-    for (int p = threadIdx.x; p < pg.F; p += blockDim.x) {
-        s_cur[p] = offsets[(size_t)p * pg.C + blockIdx.x];
-        s_cnt[p] = 0;
+    T* s_vals = reinterpret_cast<T*>(s_raw);              // [TILE]
+    int* s_keys = reinterpret_cast<int*>(s_vals + TILE);  // [TILE] keys, sorted by bucket
+    int* s_cur = s_keys + TILE;                           // [B] global write cursor
+    int* s_cnt = s_cur + pg.B;                            // [B] rows per bucket in the tile
+    int* s_gb = s_cnt + pg.B;                             // [B] global base of the tile's run
+    int* s_wt = s_gb + pg.B;                              // [33] scan scratch
+    for (int unit = blockIdx.x;; unit += unit_step(units)) {
+        long long beg, end;
+        if (!unit_rows(units, unit, beg, end)) break;
+        for (int p = threadIdx.x; p < pg.B; p += blockDim.x) {
+            s_cur[p] = offsets[(size_t)unit * pg.ustride + (size_t)p * pg.bstride];
+            s_cnt[p] = 0;
+        }
+        __syncthreads();
+        for (long long tb = beg; tb < end; tb += TILE) {
+            int k[RPT];
+            T v[RPT];
+            int rank[RPT];
+#pragma unroll
+            for (int h = 0; h < RPT / 4; ++h) {  // quads strided by the block: coalesced 16-byte loads
+                const long long r0 = tb + 4ll * (threadIdx.x + h * kPartThreads);
+                int* kq = &k[4 * h];
+                T* vq = &v[4 * h];
+                kq[0] = kq[1] = kq[2] = kq[3] = -1;
+                vq[0] = vq[1] = vq[2] = vq[3] = 0;
+                if (r0 + 3 < end) {
+                    const int4 k4 = *reinterpret_cast<const int4*>(keys + r0);
+                    kq[0] = k4.x; kq[1] = k4.y; kq[2] = k4.z; kq[3] = k4.w;
+                    RowQuad<T>::load(vals + r0, vq);
+                } else {
+#pragma unroll
+                    for (int j = 0; j < 4; ++j)
+                        if (r0 + j < end) {
+                            kq[j] = keys[r0 + j];
+                            vq[j] = vals[r0 + j];
+                        }
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < RPT; ++j) {
+                const bool ok = k[j] >= 0 && (!pg.check || k[j] < pg.G);
+                rank[j] = ok ? atomicAdd(&s_cnt[((unsigned)k[j] >> pg.shift) & pg.bmask], 1) : -1;
+            }
+            __syncthreads();
+            // reserve each bucket's run in global memory, then place of each bucket in the tile
+            for (int p = threadIdx.x; p < pg.B; p += blockDim.x) {
+                s_gb[p] = s_cur[p];
+                s_cur[p] += s_cnt[p];
+            }
+            const int nvalid = block_exclusive_scan(s_cnt, pg.B, s_wt);  // s_cnt now holds tile starts
+#pragma unroll
+            for (int j = 0; j < RPT; ++j)
+                if (rank[j] >= 0) {
+                    const int pos = s_cnt[((unsigned)k[j] >> pg.shift) & pg.bmask] + rank[j];
+                    s_keys[pos] = k[j];
+                    s_vals[pos] = v[j];
+                }
+            __syncthreads();
+            for (int i = threadIdx.x; i < nvalid; i += blockDim.x) {
+                const int kk = s_keys[i];
+                const int p = ((unsigned)kk >> pg.shift) & pg.bmask;
+                const int pos = s_gb[p] + (i - s_cnt[p]);
+                okeys[pos] = (int)((unsigned)kk & pg.kmask);
+                ovals[pos] = s_vals[i];
+            }
+            __syncthreads();
+            for (int p = threadIdx.x; p < pg.B; p += blockDim.x) s_cnt[p] = 0;
+            __syncthreads();
+        }
+        if (!units.chunks) break;
+    }
+}
+
+// One block: a chunk list over F partitions -- every partition cut into
+// chunks of CH rows (4-row-aligned starts) -- with, when asked, each
+// partition's first chunk and chunk count.  F <= 8 * blockDim.x.
+__global__ void __launch_bounds__(1024) k_seg_chunks(const long long* __restrict__ pstart,
+                                                     const long long* __restrict__ pcount, int F, long long CH,
+                                                     PartChunk* __restrict__ chunks, int* __restrict__ cbase,
+                                                     int* __restrict__ nunits, int* __restrict__ nchunks) {
+    __shared__ int s_w[33];
+    const int per = (F + blockDim.x - 1) / blockDim.x;
+    const int p0 = threadIdx.x * per, p1 = min(F, p0 + per);
+    int local = 0;
+    for (int p = p0; p < p1; ++p) local += (int)((pcount[p] + CH - 1) / CH);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int incl = local;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    if (lane == 31) s_w[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        const int nw = blockDim.x >> 5;
+        const int w = lane < nw ? s_w[lane] : 0;
+        int wi = w;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, wi, o);
+            if (lane >= o) wi += y;
+        }
+        if (lane < nw) s_w[lane] = wi - w;
+        if (lane == nw - 1) s_w[32] = wi;
     }
     __syncthreads();
-    const long long beg = blockIdx.x * pg.chunk;
-    const long long end = max(beg, min(n, beg + pg.chunk));
-    const int mask = pg.Gp - 1;
-    for (long long tb = beg; tb < end; tb += TILE) {
-        int k[RPT];
-        T v[RPT];
-        int rank[RPT];
-#pragma unroll
-        for (int h = 0; h < RPT / 4; ++h) {  // quads strided by the block: coalesced 16-byte loads
-            const long long r0 = tb + 4ll * (threadIdx.x + h * kPartThreads);
-            int* kq = &k[4 * h];
-            T* vq = &v[4 * h];
-            kq[0] = kq[1] = kq[2] = kq[3] = -1;
-            vq[0] = vq[1] = vq[2] = vq[3] = 0;
-            if (r0 + 3 < end) {
-                const int4 k4 = *reinterpret_cast<const int4*>(keys + r0);
-                kq[0] = k4.x; kq[1] = k4.y; kq[2] = k4.z; kq[3] = k4.w;
-                RowQuad<T>::load(vals + r0, vq);
-            } else {
-#pragma unroll
-                for (int j = 0; j < 4; ++j)
-                    if (r0 + j < end) {
-                        kq[j] = keys[r0 + j];
-                        vq[j] = vals[r0 + j];
-                    }
-            }
+    int cb = s_w[warp] + incl - local;
+    for (int p = p0; p < p1; ++p) {
+        const int nu = (int)((pcount[p] + CH - 1) / CH);
+        if (cbase) {
+            cbase[p] = cb;
+            nunits[p] = nu;
         }
-#pragma unroll
-        for (int j = 0; j < RPT; ++j)
-            rank[j] = (unsigned)k[j] < (unsigned)G ? atomicAdd(&s_cnt[k[j] >> pg.shift], 1) : -1;
+        const long long b0 = pstart[p], e0 = pstart[p] + pcount[p];
+        for (int k = 0; k < nu; ++k) chunks[cb + k] = PartChunk{b0 + k * CH, min(e0, b0 + (k + 1) * CH), p, 0};
+        cb += nu;
+    }
+    if (threadIdx.x == 0) *nchunks = s_w[32];
+}
+
+// Per group of every final partition its window: the largest K(b) over its
+// finite values (the window of Algorithm 2 / the max-abs pre-pass, computed
+// per partition; -1 where the group has none).  Work comes as chunks of one
+// partition's rows (so a partition holding a heavy key is shared by many
+// CTAs); each chunk takes its maxima in shared memory, then one global
+// atomicMax per group it saw.  Used when groups have few rows, so that the
+// aggregation never raises a window.
+template <typename T>
+__global__ void __launch_bounds__(512) k_part_window(const int32_t* __restrict__ okeys, const T* __restrict__ ovals,
+                                                     const PartChunk* __restrict__ chunks,
+                                                     const int* __restrict__ nchunks, int Gp, int G,
+                                                     int* __restrict__ win) {
+    extern __shared__ int s_win[];  // [Gp]
+    for (int c = blockIdx.x; c < *nchunks; c += gridDim.x) {
+        const PartChunk ch = chunks[c];
+        const int Gq = min(Gp, G - ch.seg * Gp);
+        for (int g = threadIdx.x; g < Gq; g += blockDim.x) s_win[g] = -1;
         __syncthreads();
-        // reserve each partition's run in global memory, then place of each partition in the tile
-        for (int p = threadIdx.x; p < pg.F; p += blockDim.x) {
-            s_gb[p] = s_cur[p];
-            s_cur[p] += s_cnt[p];
-        }
-        const int nvalid = block_exclusive_scan(s_cnt, pg.F, s_wt);  // s_cnt now holds tile starts
-#pragma unroll
-        for (int j = 0; j < RPT; ++j)
-            if (rank[j] >= 0) {
-                const int pos = s_cnt[k[j] >> pg.shift] + rank[j];
-                s_keys[pos] = k[j];
-                s_vals[pos] = v[j];
-            }
-        __syncthreads();
-        for (int i = threadIdx.x; i < nvalid; i += blockDim.x) {
-            const int kk = s_keys[i];
-            const int p = kk >> pg.shift;
-            const int pos = s_gb[p] + (i - s_cnt[p]);
-            okeys[pos] = kk & mask;
-            ovals[pos] = s_vals[i];
+        for (long long r = ch.beg + threadIdx.x; r < ch.end; r += blockDim.x) {
+            const Split sp = split_value(ovals[r]);
+            if (!sp.flag && sp.mant != 0) atomicMax(&s_win[okeys[r]], sp.kb);
         }
         __syncthreads();
-        for (int p = threadIdx.x; p < pg.F; p += blockDim.x) s_cnt[p] = 0;
+        int* w = win + (size_t)ch.seg * Gp;
+        for (int g = threadIdx.x; g < Gq; g += blockDim.x)
+            if (s_win[g] >= 0) atomicMax(&w[g], s_win[g]);
         __syncthreads();
     }
 }
+
+// Partition geometry the plan kernel reads: F final partitions of Gp groups
+// each (partition p holds keys [p Gp, (p + 1) Gp)).
+struct PartGeom {
+    int F;
+    int shift;
+    int Gp;
+};
 
 // One block: partitions -> tasks, work items, merge blocks, partial offsets.
 __global__ void __launch_bounds__(1024) k_part_plan(const long long* __restrict__ pstart,
                                                     const long long* __restrict__ pcount, PartGeom pg, int G, int R,
                                                     long long tpi, const int32_t* okeys, const void* ovals,
-                                                    size_t vsize, unsigned char* hdr, int L, MTask* __restrict__ tasks,
+                                                    size_t vsize, unsigned char* hdr, int L,
+                                                    const int* __restrict__ win, MTask* __restrict__ tasks,
                                                     MItem* __restrict__ items, int* nitems, MergeBlk* __restrict__ blks,
                                                     int* nblks) {
     __shared__ long long s_it[1024], s_pt[1024], s_bk[1024];
@@ -302,6 +510,7 @@ __global__ void __launch_bounds__(1024) k_part_plan(const long long* __restrict_
         t.G_hdr = G;
         t.hdr = hdr;
         t.recs = hdr + sizeof(repro_state_header) + (size_t)p * pg.Gp * rec;
+        t.win = win ? win + (size_t)p * pg.Gp : nullptr;
         tasks[p] = t;
         const long long nit = cnt == 0 ? 0 : (((cnt + R - 1) / R) + tpi - 1) / tpi;
         for (long long k = 0; k < nit; ++k) {
@@ -322,12 +531,27 @@ __global__ void __launch_bounds__(1024) k_part_plan(const long long* __restrict_
 }
 
 struct PartPlan {
-    PartGeom pg;
+    int levels;          // 1 or 2 partition passes
+    PassGeom p1, p2;     // first pass (coarse, or the only one); fine pass
+    int F;               // final partitions (ceil(G / Gp))
+    int Fs;              // final partitions the scan covers (F1 * F2 with two passes, else F)
+    int F1, F2;          // coarse partitions, buckets per coarse partition
+    int Gp;              // groups per final partition
+    int C;               // CTAs of the partition passes
+    long long chunk;     // rows per CTA chunk of the first pass
+    long long max_chunks;
     FusedPlanConfig cfg;
-    int ctas;          // CTAs of the multi-task kernel
-    long long tpi;     // tiles per work item
+    int ctas;            // CTAs of the multi-task kernel
+    long long tpi;       // tiles per work item
     long long max_items, max_blks, max_part_recs;
+    int windows;         // 1: compute every group's window before aggregating
+    long long max_wchunks;
 };
+
+// Rows per group below which the windows are computed first: with few rows
+// per group nearly every group raises its window inside the aggregation.
+constexpr long long kWindowRowsPerGroup = 64;
+constexpr long long kWindowChunkRows = 65536;
 
 // Candidate partition widths 2^shift: at most kMaxParts partitions and a
 // single-pass table that fits (with the 256 bytes of stage metadata).
@@ -338,15 +562,42 @@ bool shift_usable(int dtype, int L, long long G, int shift, FusedPlanConfig& cfg
     return fused_plan_config(dtype, L, 1 << shift, 256, cfg);
 }
 
+int ceil_log2(long long x) {
+    int b = 0;
+    while ((1ll << b) < x) ++b;
+    return b;
+}
+
 // The plan of one partitioned call, fully determined by the choice.
 bool make_part_plan(const PartChoice& pc, int L, long long G, long long n, PartPlan& pp) {
     const DeviceInfo& di = device_info();
+    if (pc.shift < 6 || pc.shift > 12) return false;
     const int Gp = 1 << pc.shift;
     const long long F = (G + Gp - 1) / Gp;
-    if (F > kMaxParts || pc.shift < 6 || pc.shift > 12) return false;
-    pp.pg.F = (int)F;
-    pp.pg.shift = pc.shift;
-    pp.pg.Gp = Gp;
+    if (F > kMaxParts) return false;
+    pp.Gp = Gp;
+    pp.F = (int)F;
+    pp.C = di.sms * 2;
+    pp.chunk = ((n + pp.C - 1) / pp.C + 3) & ~3ll;
+    if (pp.chunk < 4) pp.chunk = 4;
+    pp.levels = pc.shift1 > pc.shift ? 2 : 1;
+    if (pp.levels == 1) {
+        pp.F1 = pp.Fs = (int)F;
+        pp.F2 = 1;
+        pp.p1 = PassGeom{(int)F, pc.shift, 0xffffffffu, (unsigned)Gp - 1, 1, (int)G, 1, pp.C};
+        pp.max_chunks = 0;
+    } else {
+        const int F2 = 1 << (pc.shift1 - pc.shift);
+        const long long F1 = (G + (1ll << pc.shift1) - 1) >> pc.shift1;
+        if (F1 > 1024 || F1 * F2 > 2 * (long long)kMaxParts) return false;
+        pp.F1 = (int)F1;
+        pp.F2 = F2;
+        pp.Fs = (int)(F1 * F2);
+        // coarse: keys kept whole; fine: buckets of the next bits, keys made local
+        pp.p1 = PassGeom{(int)F1, pc.shift1, 0xffffffffu, 0xffffffffu, 1, (int)G, 1, pp.C};
+        pp.p2 = PassGeom{F2, pc.shift, (unsigned)F2 - 1, (unsigned)Gp - 1, 0, (int)G, F2, 1};
+        pp.max_chunks = (n + kChunkRows - 1) / kChunkRows + F1;
+    }
     pp.cfg = pc.cfg;
     pp.ctas = di.sms * pc.cfg.ctas_per_sm;
     const long long R = pc.cfg.R;
@@ -358,9 +609,9 @@ bool make_part_plan(const PartChoice& pc, int L, long long G, long long n, PartP
     pp.max_blks = max_split * ((Gp + 31) / 32);
     // only partitions with more than tpi tiles are split into several items
     pp.max_part_recs = (total_tiles / pp.tpi + 1 + max_split) * (long long)Gp;
-    pp.pg.C = di.sms * 2;
-    pp.pg.chunk = ((n + pp.pg.C - 1) / pp.pg.C + 3) & ~3ll;
-    if (pp.pg.chunk < 4) pp.pg.chunk = 4;
+    pp.windows = n < kWindowRowsPerGroup * G ? 1 : 0;
+    pp.max_wchunks = (n + kWindowChunkRows - 1) / kWindowChunkRows + F;
+    if (pp.F > 8 * 1024) return false;  // k_seg_chunks covers 8 partitions per thread
     (void)L;
     return true;
 }
@@ -368,27 +619,82 @@ bool make_part_plan(const PartChoice& pc, int L, long long G, long long n, PartP
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 struct PartScratch {
-    size_t okeys, ovals, counts, offsets, pstart, pcount, tasks, items, blks, parts, ints, total;
+    size_t akeys, avals;               // coarse output (two passes)
+    size_t okeys, ovals;               // final partitions
+    size_t counts1, offsets1, ptot1, pstart1, pcount1;
+    size_t chunks, cbase, nunits, counts2, offsets2;
+    size_t ptot, pstart, pcount;
+    size_t win, wchunks;
+    size_t tasks, items, blks, parts, ints, total;
 };
 
 PartScratch part_scratch_layout(const PartPlan& pp, long long n, int dtype, int L) {
-    PartScratch s;
+    PartScratch s{};
     const size_t vs = dtype == REPRO_F64 ? 8 : 4;
-    const size_t rows = (size_t)n + 4 * (size_t)pp.pg.F;
     size_t o = 0;
-    s.okeys = o; o = align256(o + rows * 4);
-    s.ovals = o; o = align256(o + rows * vs);
-    s.counts = o; o = align256(o + (size_t)pp.pg.F * pp.pg.C * 4);
-    s.offsets = o; o = align256(o + (size_t)pp.pg.F * pp.pg.C * 4);
-    s.pstart = o; o = align256(o + (size_t)pp.pg.F * 8);
-    s.pcount = o; o = align256(o + (size_t)pp.pg.F * 8);
-    s.tasks = o; o = align256(o + (size_t)pp.pg.F * sizeof(MTask));
-    s.items = o; o = align256(o + (size_t)pp.max_items * sizeof(MItem));
-    s.blks = o; o = align256(o + (size_t)std::max(1ll, pp.max_blks) * sizeof(MergeBlk));
-    s.parts = o; o = align256(o + (size_t)pp.max_part_recs * (8 + 16 * (size_t)L));
-    s.ints = o; o = align256(o + 4 * sizeof(int));
+    auto take = [&](size_t& at, size_t bytes) {
+        at = o;
+        o = align256(o + bytes);
+    };
+    const size_t rows = (size_t)n + 4 * (size_t)pp.Fs;
+    take(s.okeys, rows * 4);
+    take(s.ovals, rows * vs);
+    take(s.counts1, (size_t)pp.p1.B * pp.C * 4);
+    take(s.offsets1, (size_t)pp.p1.B * pp.C * 4);
+    if (pp.levels == 2) {
+        const size_t arows = (size_t)n + 4 * (size_t)pp.F1;
+        take(s.akeys, arows * 4);
+        take(s.avals, arows * vs);
+        take(s.ptot1, (size_t)pp.F1 * 8);
+        take(s.pstart1, (size_t)pp.F1 * 8);
+        take(s.pcount1, (size_t)pp.F1 * 8);
+        take(s.chunks, (size_t)pp.max_chunks * sizeof(PartChunk));
+        take(s.cbase, (size_t)pp.F1 * 4);
+        take(s.nunits, (size_t)pp.F1 * 4);
+        take(s.counts2, (size_t)pp.max_chunks * pp.F2 * 4);
+        take(s.offsets2, (size_t)pp.max_chunks * pp.F2 * 4);
+    }
+    take(s.ptot, (size_t)pp.Fs * 8);
+    take(s.pstart, (size_t)pp.Fs * 8);
+    take(s.pcount, (size_t)pp.Fs * 8);
+    if (pp.windows) {
+        take(s.win, (size_t)pp.F * pp.Gp * 4);
+        take(s.wchunks, (size_t)pp.max_wchunks * sizeof(PartChunk));
+    }
+    take(s.tasks, (size_t)pp.F * sizeof(MTask));
+    take(s.items, (size_t)pp.max_items * sizeof(MItem));
+    take(s.blks, (size_t)std::max(1ll, pp.max_blks) * sizeof(MergeBlk));
+    take(s.parts, (size_t)pp.max_part_recs * (8 + 16 * (size_t)L));
+    take(s.ints, 8 * sizeof(int));
     s.total = o;
     return s;
+}
+
+template <typename T>
+cudaError_t launch_scatter(const int32_t* keys, const void* vals, const Units& u, const PassGeom& pg, int grid,
+                           const int* offsets, int32_t* okeys, void* ovals, cudaStream_t s) {
+    const size_t smem = (size_t)kScatterRows * kPartThreads * (sizeof(T) + 4) + 3 * (size_t)pg.B * 4 + 33 * 4;
+    cudaError_t e = cudaFuncSetAttribute(k_part_scatter<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_part_scatter<T><<<grid, kPartThreads, smem, s>>>(keys, (const T*)vals, u, pg, offsets, okeys, (T*)ovals);
+    return cudaGetLastError();
+}
+
+// One pass: histogram, scan, scatter.  sg describes the units' segments.
+cudaError_t partition_pass(const int32_t* keys, const void* vals, int dtype, const Units& u, const PassGeom& pg,
+                           const ScanGeom& sg, int grid, int* counts, int* offsets, long long* ptot,
+                           long long* pstart, long long* pcount, int32_t* okeys, void* ovals, unsigned* errors,
+                           cudaStream_t s) {
+    k_part_hist<<<grid, kPartThreads, (size_t)pg.B * 4, s>>>(keys, u, pg, counts, errors);
+    const int sgrid = std::max(1, std::min(1024, (sg.F + 7) / 8));
+    k_scan_totals<<<sgrid, 256, 0, s>>>(counts, sg, ptot);
+    k_scan_starts<<<1, 1024, 0, s>>>(ptot, sg.F, pstart, pcount);
+    k_scan_offsets<<<sgrid, 256, 0, s>>>(counts, sg, pstart, offsets);
+    count_launches(5);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    return dtype == REPRO_F64 ? launch_scatter<double>(keys, vals, u, pg, grid, offsets, okeys, ovals, s)
+                              : launch_scatter<float>(keys, vals, u, pg, grid, offsets, okeys, ovals, s);
 }
 
 }  // namespace
@@ -396,32 +702,39 @@ PartScratch part_scratch_layout(const PartPlan& pp, long long n, int dtype, int 
 bool partition_choose(int dtype, int L, long long G, PartChoice& pc) {
     // forced by the tuner (this thread) > tuned cache > rule; each only if usable
     int forced = tune_forced_shift();
+    int shift = 0;
     if (forced && shift_usable(dtype, L, G, forced, pc.cfg)) {
-        pc.shift = forced;
-        return true;
-    }
-    int tuned = 0;
-    if (tune_lookup_shift(dtype, L, G, tuned) && shift_usable(dtype, L, G, tuned, pc.cfg)) {
-        pc.shift = tuned;
-        return true;
-    }
-    // rule: the widest power-of-two slice whose table keeps two CTAs per SM
-    // (then one), with at most kMaxParts partitions
-    for (int cps_goal = 2; cps_goal >= 1; --cps_goal)
-        for (int shift = 12; shift >= 6; --shift) {
-            FusedPlanConfig cfg;
-            if (!shift_usable(dtype, L, G, shift, cfg)) continue;
-            if (cfg.ctas_per_sm < cps_goal) continue;
-            pc.shift = shift;
-            pc.cfg = cfg;
-            return true;
+        shift = forced;
+    } else {
+        int tuned = 0;
+        if (tune_lookup_shift(dtype, L, G, tuned) && shift_usable(dtype, L, G, tuned, pc.cfg)) {
+            shift = tuned;
+        } else {
+            // rule: the widest power-of-two slice whose table keeps two CTAs
+            // per SM (then one), with at most kMaxParts partitions
+            for (int cps_goal = 2; cps_goal >= 1 && !shift; --cps_goal)
+                for (int sh = 12; sh >= 6; --sh) {
+                    FusedPlanConfig cfg;
+                    if (!shift_usable(dtype, L, G, sh, cfg) || cfg.ctas_per_sm < cps_goal) continue;
+                    shift = sh;
+                    pc.cfg = cfg;
+                    break;
+                }
         }
-    return false;
+    }
+    if (!shift) return false;
+    pc.shift = shift;
+    // one pass up to kOneLevelParts partitions, else two with about sqrt(F)
+    // buckets per coarse partition
+    const long long F = (G + (1ll << shift) - 1) >> shift;
+    pc.shift1 = 0;
+    if (F > kOneLevelParts) pc.shift1 = shift + (ceil_log2(F) + 1) / 2;
+    return true;
 }
 
 bool partitioned_supported(int dtype, int L, long long G, long long n, const void* keys, const void* vals) {
     if ((uintptr_t)keys % 16 || (uintptr_t)vals % 16) return false;
-    if (n <= 0 || n > (1ll << 31) - 4ll * kMaxParts) return false;
+    if (n <= 0 || n > (1ll << 31) - 8ll * kMaxParts - 4096) return false;
     PartChoice pc;
     return partition_choose(dtype, L, G, pc);
 }
@@ -436,45 +749,69 @@ cudaError_t launch_groupby_partitioned(const int32_t* keys, const void* vals, lo
                                        long long G, const PartChoice& pc, void* state, void* scratch,
                                        cudaStream_t s) {
     PartPlan pp;
-    if (!make_part_plan(pc, L, G, n, pp) || !fused_config_fits(dtype, L, pp.pg.Gp, 256, pc.cfg))
+    if (!make_part_plan(pc, L, G, n, pp) || !fused_config_fits(dtype, L, pp.Gp, 256, pc.cfg))
         return cudaErrorInvalidValue;
     const PartScratch ly = part_scratch_layout(pp, n, dtype, L);
     unsigned char* b = (unsigned char*)scratch;
     int32_t* okeys = (int32_t*)(b + ly.okeys);
     void* ovals = b + ly.ovals;
-    int* counts = (int*)(b + ly.counts);
-    int* offsets = (int*)(b + ly.offsets);
     long long* pstart = (long long*)(b + ly.pstart);
     long long* pcount = (long long*)(b + ly.pcount);
-    int* ints = (int*)(b + ly.ints);  // nitems, nblks, counter
+    int* ints = (int*)(b + ly.ints);  // nitems, nblks, counter, nchunks
     unsigned* errors = &reinterpret_cast<repro_state_header*>(state)->errors;
-    const size_t hsmem = (size_t)pp.pg.F * 4;
     cudaError_t e;
+    const Units whole{pp.chunk, n, nullptr, nullptr};
     prof_begin(PROF_PARTITION, s);
-    k_part_hist<<<pp.pg.C, kPartThreads, hsmem, s>>>(keys, n, (int)G, pp.pg, counts, errors);
-    k_part_scan<<<1, 1024, 0, s>>>(counts, pp.pg, offsets, pstart, pcount);
-    const size_t vsz = dtype == REPRO_F64 ? 8 : 4;
-    const size_t ssmem = (size_t)kScatterRows * kPartThreads * (vsz + 4) + 3 * (size_t)pp.pg.F * 4 + 33 * 4;
-    if (dtype == REPRO_F64) {
-        if ((e = cudaFuncSetAttribute(k_part_scatter<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)ssmem)) != cudaSuccess)
-            return e;
-        k_part_scatter<double><<<pp.pg.C, kPartThreads, ssmem, s>>>(keys, (const double*)vals, n, (int)G, pp.pg,
-                                                                     offsets, okeys, (double*)ovals);
+    if (pp.levels == 1) {
+        const ScanGeom sg{pp.Fs, pp.Fs, 1, pp.C, pp.C, nullptr, nullptr};
+        e = partition_pass(keys, vals, dtype, whole, pp.p1, sg, pp.C, (int*)(b + ly.counts1), (int*)(b + ly.offsets1),
+                           (long long*)(b + ly.ptot), pstart, pcount, okeys, ovals, errors, s);
     } else {
-        if ((e = cudaFuncSetAttribute(k_part_scatter<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)ssmem)) != cudaSuccess)
-            return e;
-        k_part_scatter<float><<<pp.pg.C, kPartThreads, ssmem, s>>>(keys, (const float*)vals, n, (int)G, pp.pg,
-                                                                    offsets, okeys, (float*)ovals);
+        int32_t* akeys = (int32_t*)(b + ly.akeys);
+        void* avals = b + ly.avals;
+        long long* pstart1 = (long long*)(b + ly.pstart1);
+        long long* pcount1 = (long long*)(b + ly.pcount1);
+        const ScanGeom sg1{pp.F1, pp.F1, 1, pp.C, pp.C, nullptr, nullptr};
+        e = partition_pass(keys, vals, dtype, whole, pp.p1, sg1, pp.C, (int*)(b + ly.counts1), (int*)(b + ly.offsets1),
+                           (long long*)(b + ly.ptot1), pstart1, pcount1, akeys, avals, errors, s);
+        if (e != cudaSuccess) return e;
+        PartChunk* chunks = (PartChunk*)(b + ly.chunks);
+        int* cbase = (int*)(b + ly.cbase);
+        int* nunits = (int*)(b + ly.nunits);
+        k_seg_chunks<<<1, 1024, 0, s>>>(pstart1, pcount1, pp.F1, kChunkRows, chunks, cbase, nunits, ints + 3);
+        count_launches(1);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        const Units fine{0, 0, chunks, ints + 3};
+        const ScanGeom sg2{pp.Fs, pp.F2, pp.F2, 1, 0, cbase, nunits};
+        e = partition_pass(akeys, avals, dtype, fine, pp.p2, sg2, pp.C, (int*)(b + ly.counts2), (int*)(b + ly.offsets2),
+                           (long long*)(b + ly.ptot), pstart, pcount, okeys, ovals, errors, s);
     }
     prof_end(PROF_PARTITION, s);
-    k_part_plan<<<1, 1024, 0, s>>>(pstart, pcount, pp.pg, (int)G, pp.cfg.R, pp.tpi, okeys, ovals,
-                                   dtype == REPRO_F64 ? 8 : 4, (unsigned char*)state, L, (MTask*)(b + ly.tasks),
+    if (e != cudaSuccess) return e;
+    int* win = nullptr;
+    if (pp.windows) {
+        win = (int*)(b + ly.win);
+        PartChunk* wch = (PartChunk*)(b + ly.wchunks);
+        if ((e = cudaMemsetAsync(win, 0xff, (size_t)pp.F * pp.Gp * 4, s)) != cudaSuccess) return e;  // -1
+        k_seg_chunks<<<1, 1024, 0, s>>>(pstart, pcount, pp.F, kWindowChunkRows, wch, nullptr, nullptr, ints + 4);
+        const int grid = device_info().sms * 4;
+        const size_t smem = (size_t)pp.Gp * 4;
+        if (dtype == REPRO_F64)
+            k_part_window<double><<<grid, 512, smem, s>>>(okeys, (const double*)ovals, wch, ints + 4, pp.Gp, (int)G,
+                                                          win);
+        else
+            k_part_window<float><<<grid, 512, smem, s>>>(okeys, (const float*)ovals, wch, ints + 4, pp.Gp, (int)G,
+                                                         win);
+        count_launches(2);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    PartGeom pg{pp.F, pc.shift, pp.Gp};
+    k_part_plan<<<1, 1024, 0, s>>>(pstart, pcount, pg, (int)G, pp.cfg.R, pp.tpi, okeys, ovals,
+                                   dtype == REPRO_F64 ? 8 : 4, (unsigned char*)state, L, win, (MTask*)(b + ly.tasks),
                                    (MItem*)(b + ly.items), ints, (MergeBlk*)(b + ly.blks), ints + 1);
-    count_launches(4);
+    count_launches(1);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    e = launch_multi(dtype, L, pp.cfg, pp.pg.Gp, b + ly.tasks, b + ly.items, (int)pp.max_items, ints, ints + 2,
+    e = launch_multi(dtype, L, pp.cfg, pp.Gp, b + ly.tasks, b + ly.items, (int)pp.max_items, ints, ints + 2,
                      b + ly.parts, pp.ctas, s);
     if (e != cudaSuccess) return e;
     if (pp.max_blks > 0)

@@ -308,14 +308,18 @@ def test_fused_variants_in_subprocess(env):
 
 # ------------------------------------------------- partitioned large-G path
 
-@pytest.mark.parametrize("G,dist,L", [(1 << 16, "zipf", 3), (1 << 16, "uniform", 2), (1 << 20, "uniform", 4),
-                                      (5000, "zipf", 3), (300_000, "uniform", 3)])
-def test_partitioned_path_matches_oracle(G, dist, L):
-    n = 1 << 22
+@pytest.mark.parametrize("G,dist,L,n", [
+    (1 << 16, "zipf", 3, 1 << 22), (1 << 16, "uniform", 2, 1 << 22),  # one partition pass
+    (5000, "zipf", 3, 1 << 22),
+    (1 << 20, "uniform", 4, 1 << 22), (300_000, "uniform", 3, 1 << 22),  # two passes
+    (3_000_000, "zipf", 2, 1 << 21),  # two passes, coarse partitions of uneven size
+    (1 << 24, "uniform", 4, 1 << 20),  # 8192 final partitions (most groups empty)
+])
+def test_partitioned_path_matches_oracle(G, dist, L, n):
     w = WL.sweep_cell(G, dist, L, n=n, seed=G + L, device=DEV)
     st, out = run_gpu(w.keys, w.values, w.G, w.L)
     assert st.check() == 0
-    ost, _ = oracle_state(_np(w.keys), _np(w.values), w.G, w.L, threads=8)
+    ost, _ = oracle_state(_np(w.keys), _np(w.values), w.G, w.L, threads=8 if G <= (1 << 20) else 1)
     assert_state_equal(st, ost)
     assert_bits_equal(_np(out), O.finalize(ost))
 
