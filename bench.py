@@ -275,8 +275,16 @@ def run_ours(args, rank, world, local_rank):
             # every row's key and value read once
             dom_bytes = n * (4 + 8)
             ach = dom_bytes / (p["ms_per_launch"] / 1e3) / 1e9
+            cfg_key = None
+            if tuned and tuned.get("path") == "single_pass":
+                cfg_key = "%d,%d,%d,%d,%d" % (tuned["stages"], tuned["tile_rows"], tuned["consumer_warps"],
+                                              tuned["ctas_per_sm"], tuned["table_copies"])
+            wkey = "n=%d G=%d %s L=%d" % (n, G, args.dist, L)
             roof = {"bound": "hbm", "kernel": name, "achieved": round(ach, 1), "peak": peaks["hbm_gbs"],
-                    "unit": "GB/s", "frac": round(ach / peaks["hbm_gbs"], 4), "traffic": None,
+                    "unit": "GB/s", "frac": round(ach / peaks["hbm_gbs"], 4),
+                    "traffic": measured_traffic("k_fused" if name == "fused" else name, wkey, cfg_key),
+                    "traffic_source": "profiles/traffic.json (ncu dram__bytes_read.sum + dram__bytes_write.sum, "
+                                      "same sources, workload and configuration; null otherwise)",
                     "peak_source": peaks["source"], "ms_per_launch": p["ms_per_launch"],
                     "launches_per_step": p["launches"] / args.steps}
         result = {
@@ -335,6 +343,41 @@ def verify_sampled(w, out, st):
     got = out[sample].cpu().numpy()
     ok = np.array_equal(got.view(np.int64), ref.view(np.int64))
     return {"groups": ngroups, "rows": int(k.size), "bit_exact": bool(ok)}
+
+
+# the sources each profiled kernel is compiled from
+KERNEL_SOURCES = {"k_fused": ["repro_fused.cu", "fused_device.cuh", "repro_device.cuh", "ptx.cuh"]}
+
+
+def kernel_source_hash(kernel):
+    """sha256 over the sources a kernel is compiled from: a DRAM traffic
+    figure is reported only for the kernel it was measured on."""
+    import hashlib
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1802_09883_gb300", "csrc")
+    for name in KERNEL_SOURCES.get(kernel, []):
+        h.update(name.encode())
+        with open(os.path.join(csrc, name), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def measured_traffic(kernel, workload_key, cfg_key):
+    """DRAM bytes per launch from profiles/traffic.json when that capture was
+    taken on these sources, this workload and this kernel configuration."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as fh:
+            entries = json.load(fh)
+    except Exception:
+        return None
+    if kernel not in KERNEL_SOURCES:
+        return None
+    src = kernel_source_hash(kernel)
+    for e in entries:
+        if (e.get("kernel") == kernel and e.get("workload") == workload_key and e.get("config") == cfg_key
+                and e.get("source_sha256") == src):
+            return e.get("dram_bytes_per_launch")
+    return None
 
 
 def load_peaks():

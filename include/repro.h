@@ -256,6 +256,49 @@ repro_status groupby_sum_fp32(const int32_t* keys, const float* values, int64_t 
                               int64_t num_groups, float* out, void* stream);
 
 /*
+ * SQL aggregates from reproducible sums.  The paper observes that with a
+ * reproducible SUM every SQL aggregate becomes reproducible: COUNT needs no
+ * floating point, AVG, VARIANCE and STDDEV are functions of SUM(x) and
+ * SUM(x^2) (Sec. I).  A stats state holds a repro state of x, one of x*x
+ * (each product rounded to nearest in the dtype) and an exact uint64 row
+ * count per group; repro_stats_state_bytes gives its size (16-byte aligned
+ * device memory, caller-owned).  repro_groupby_stats accumulates rows like
+ * repro_groupby_sum (keys outside [0, num_groups) are skipped and flag
+ * REPRO_ERR_KEY in the first part's header, read by repro_state_check);
+ * scratch: one value column.  repro_stats_merge adds one state into another
+ * (states of the same shape, not overlapping).
+ *
+ * repro_stats_finalize writes, per group g (any pointer may be NULL; value
+ * arrays are of the dtype, count int64):
+ *   count = rows (the presence column: count > 0),
+ *   sum = SUM(x) as repro_finalize, mean = sum / count,
+ *   D = SUMSQ - (sum * sum) / count, clamped at 0 (each operation rounded to
+ *   nearest in the dtype, in this order),
+ *   var_samp = D / (count - 1), var_pop = D / count, stddev_* = sqrt(var_*).
+ * Empty groups give NaN for mean and the variances, one row NaN for var_samp
+ * (SQL's NULL).  The count is converted to the dtype exactly below 2^53
+ * (2^24 for float), rounded above.
+ */
+typedef struct {
+    int64_t* count;
+    void* sum;
+    void* mean;
+    void* var_samp;
+    void* var_pop;
+    void* stddev_samp;
+    void* stddev_pop;
+} repro_stats_out;
+
+size_t repro_stats_state_bytes(repro_dtype dtype, int L, int64_t num_groups);
+repro_status repro_stats_init(void* state, repro_dtype dtype, int L, int64_t num_groups, void* stream);
+repro_status repro_groupby_stats(const int32_t* keys, const void* values, int64_t n, repro_dtype dtype, int L,
+                                 int64_t num_groups, void* state, void* stream);
+repro_status repro_stats_merge(void* dst, const void* src, repro_dtype dtype, int L, int64_t num_groups,
+                               void* stream);
+repro_status repro_stats_finalize(const void* state, repro_dtype dtype, int L, int64_t num_groups,
+                                  const repro_stats_out* out, void* stream);
+
+/*
  * Request server: continuous batching of aggregation queries.
  *
  * The paper aggregates one relation per query (Sec. II problem statement,

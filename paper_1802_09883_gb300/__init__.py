@@ -104,6 +104,12 @@ def lib(build_if_stale: bool = True):
         L.repro_tune_clear.argtypes = []
         L.repro_tune_clear.restype = None
         L.repro_batch_tune.argtypes = [vp, vp, ctypes.POINTER(ctypes.c_double)]
+        L.repro_stats_state_bytes.argtypes = [i32, i32, i64]
+        L.repro_stats_state_bytes.restype = ctypes.c_size_t
+        L.repro_stats_init.argtypes = [vp, i32, i32, i64, vp]
+        L.repro_groupby_stats.argtypes = [vp, vp, i64, i32, i32, i64, vp, vp]
+        L.repro_stats_merge.argtypes = [vp, vp, i32, i32, i64, vp]
+        L.repro_stats_finalize.argtypes = [vp, i32, i32, i64, vp, vp]
         for name in ("repro_state_init", "repro_groupby_sum", "repro_groupby_sum_noalloc", "repro_merge",
                      "repro_finalize", "repro_batch_prepare", "repro_batch_run", "repro_batch_destroy",
                      "repro_batch_reset", "repro_batch_set_outputs", "repro_batch_finalize",
@@ -111,7 +117,8 @@ def lib(build_if_stale: bool = True):
                      "repro_state_check", "groupby_sum_fp64", "groupby_sum_fp32", "repro_server_create",
                      "repro_server_submit", "repro_server_poll", "repro_server_wait", "repro_server_release",
                      "repro_server_stats_get", "repro_server_destroy", "repro_tune_groupby", "repro_tune_save",
-                     "repro_tune_load", "repro_batch_tune"):
+                     "repro_tune_load", "repro_batch_tune", "repro_stats_init", "repro_groupby_stats",
+                     "repro_stats_merge", "repro_stats_finalize"):
             getattr(L, name).restype = i32
         _lib = L
     return _lib
@@ -426,3 +433,67 @@ def tune_load(path: str):
 
 def tune_clear():
     lib().repro_tune_clear()
+
+
+class _StatsOut(ctypes.Structure):
+    _fields_ = [(name, ctypes.c_void_p) for name in
+                ("count", "sum", "mean", "var_samp", "var_pop", "stddev_samp", "stddev_pop")]
+
+
+STATS_FIELDS = ("count", "sum", "mean", "var_samp", "var_pop", "stddev_samp", "stddev_pop")
+
+
+class Stats:
+    """COUNT / SUM / AVG / VARIANCE / STDDEV per group from reproducible sums
+    of x and x*x plus exact row counts (a stats state in device memory)."""
+
+    def __init__(self, num_groups: int, L: int = 3, dtype=torch.float64, device=None):
+        if not torch.cuda.is_available():
+            raise RuntimeError("paper_1802_09883_gb300 needs a CUDA device")
+        self.G, self.L, self.dtype, self.code = int(num_groups), int(L), dtype, _dtype_code(dtype)
+        nbytes = int(lib().repro_stats_state_bytes(self.code, self.L, self.G))
+        if nbytes == 0:
+            raise ValueError("invalid L or num_groups")
+        dev = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+        self.tensor = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+        _check(lib().repro_stats_init(self.tensor.data_ptr(), self.code, self.L, self.G, _stream(dev)),
+               "repro_stats_init")
+
+    def add(self, keys: torch.Tensor, values: torch.Tensor):
+        _require_cuda(keys, "keys")
+        _require_cuda(values, "values")
+        if keys.dtype != torch.int32 or values.dtype != self.dtype or keys.numel() != values.numel():
+            raise ValueError("keys int32 and values of the state's dtype, same length")
+        keys, values = keys.contiguous(), values.contiguous()
+        _check(lib().repro_groupby_stats(keys.data_ptr(), values.data_ptr(), keys.numel(), self.code, self.L, self.G,
+                                         self.tensor.data_ptr(), _stream(self.tensor.device)), "repro_groupby_stats")
+        return self
+
+    def merge(self, other: "Stats"):
+        _check(lib().repro_stats_merge(self.tensor.data_ptr(), other.tensor.data_ptr(), self.code, self.L, self.G,
+                                       _stream(self.tensor.device)), "repro_stats_merge")
+        return self
+
+    def check(self) -> int:
+        err = ctypes.c_uint32(0)
+        _check(lib().repro_state_check(self.tensor.data_ptr(), ctypes.byref(err), _stream(self.tensor.device)),
+               "repro_state_check")
+        return err.value
+
+    def finalize(self) -> dict:
+        dev = self.tensor.device
+        res = {"count": torch.empty(self.G, dtype=torch.int64, device=dev)}
+        for name in STATS_FIELDS[1:]:
+            res[name] = torch.empty(self.G, dtype=self.dtype, device=dev)
+        out = _StatsOut(*[res[name].data_ptr() for name in STATS_FIELDS])
+        _check(lib().repro_stats_finalize(self.tensor.data_ptr(), self.code, self.L, self.G, ctypes.byref(out),
+                                          _stream(dev)), "repro_stats_finalize")
+        return res
+
+
+def groupby_stats(keys: torch.Tensor, values: torch.Tensor, num_groups: int, L: int = 3) -> dict:
+    """One-shot COUNT / SUM / AVG / VAR_SAMP / VAR_POP / STDDEV_* GROUP BY key."""
+    st = Stats(num_groups, L, values.dtype, device=values.device).add(keys, values)
+    res = st.finalize()
+    st.check()
+    return res
