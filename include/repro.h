@@ -145,6 +145,17 @@ repro_status repro_groupby_sum_cols(const uint8_t* key1, const uint8_t* key2, in
                                     int L, int64_t num_groups, void* const* states, void* stream);
 
 /*
+ * Reproducible SUM without GROUP BY (one group): values[0 .. n) are added
+ * into `state`, a state made with num_groups = 1 (its header is checked on
+ * the device; a mismatch sets REPRO_ERR_LAYOUT).  Same bits as
+ * repro_groupby_sum with an all-zero key column, without reading one: the
+ * single-pass kernel runs keyless when values are 16-byte aligned, else the
+ * grouped path runs on a zero key column in scratch.  Across ranks the
+ * states merge like any other (the paper's MPI_Reduce remark, Sec. III).
+ */
+repro_status repro_sum(const void* values, int64_t n, repro_dtype dtype, int L, void* state, void* stream);
+
+/*
  * repro_groupby_sum without any allocation.  The paper has no counterpart:
  * this is a deployment variant of repro_groupby_sum for callers that cannot
  * allocate device memory while they aggregate -- a host whose buffer

@@ -104,6 +104,7 @@ def lib(build_if_stale: bool = True):
         L.repro_tune_clear.argtypes = []
         L.repro_tune_clear.restype = None
         L.repro_batch_tune.argtypes = [vp, vp, ctypes.POINTER(ctypes.c_double)]
+        L.repro_sum.argtypes = [vp, i64, i32, i32, vp, vp]
         L.repro_stats_state_bytes.argtypes = [i32, i32, i64]
         L.repro_stats_state_bytes.restype = ctypes.c_size_t
         L.repro_stats_init.argtypes = [vp, i32, i32, i64, vp]
@@ -118,7 +119,7 @@ def lib(build_if_stale: bool = True):
                      "repro_server_submit", "repro_server_poll", "repro_server_wait", "repro_server_release",
                      "repro_server_stats_get", "repro_server_destroy", "repro_tune_groupby", "repro_tune_save",
                      "repro_tune_load", "repro_batch_tune", "repro_stats_init", "repro_groupby_stats",
-                     "repro_stats_merge", "repro_stats_finalize"):
+                     "repro_stats_merge", "repro_stats_finalize", "repro_sum"):
             getattr(L, name).restype = i32
         _lib = L
     return _lib
@@ -213,6 +214,18 @@ class State:
         _check(lib().repro_finalize(self.tensor.data_ptr(), self.code, self.L, self.G, out.data_ptr(),
                                     _stream(self.device)), "repro_finalize")
         return out
+
+    def add_values(self, values: torch.Tensor):
+        """Reproducible SUM of every value into this one-group state."""
+        if self.G != 1:
+            raise ValueError("add_values needs a state with num_groups = 1")
+        _require_cuda(values, "values")
+        if values.dtype != self.dtype:
+            raise ValueError("values must have the state's dtype")
+        values = values.contiguous()
+        _check(lib().repro_sum(values.data_ptr(), values.numel(), self.code, self.L, self.tensor.data_ptr(),
+                               _stream(self.device)), "repro_sum")
+        return self
 
     def error_word(self) -> int:
         """Synchronise and return the state's error word (REPRO_ERR_* bits)."""
@@ -497,3 +510,12 @@ def groupby_stats(keys: torch.Tensor, values: torch.Tensor, num_groups: int, L: 
     res = st.finalize()
     st.check()
     return res
+
+
+def scalar_sum(values: torch.Tensor, L: int = 3) -> torch.Tensor:
+    """Reproducible SUM of a float64/float32 tensor (no GROUP BY): a 0-dim
+    tensor of the same dtype, identical for any order or split of the values."""
+    st = State(1, L, values.dtype, device=values.device).add_values(values)
+    out = st.finalize()
+    st.check()
+    return out[0]

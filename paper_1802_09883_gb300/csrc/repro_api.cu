@@ -206,6 +206,25 @@ repro_status repro_groupby_sum_cols(const uint8_t* key1, const uint8_t* key2, in
     return REPRO_OK;
 }
 
+repro_status repro_sum(const void* values, int64_t n, repro_dtype dtype, int L, void* state, void* stream) {
+    if (!state || (uintptr_t)state % 16 || n < 0 || !valid_dtype(dtype) || !valid_shape(L, 1)) return REPRO_EINVAL;
+    if (n > 0 && (!values || (uintptr_t)values % (dtype == REPRO_F64 ? 8 : 4))) return REPRO_EINVAL;
+    if (n == 0) return REPRO_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    FusedPlanConfig cfg;
+    if (fused_supported(dtype, L, 1, nullptr, values) && fused_plan_config(dtype, L, 1, 0, cfg)) {
+        Scratch scratch(fused_scratch_bytes(cfg, L, 1, n), s);
+        if (scratch.err != cudaSuccess) return from_cuda(scratch.err);
+        return from_cuda(launch_groupby_fused(nullptr, values, n, dtype, L, 1, cfg, state, scratch.p, s));
+    }
+    // values not 16-byte aligned: the grouped path with an all-zero key column
+    Scratch keys(4 * (size_t)n, s);
+    if (keys.err != cudaSuccess) return from_cuda(keys.err);
+    cudaError_t e = cudaMemsetAsync(keys.p, 0, 4 * (size_t)n, s);
+    if (e != cudaSuccess) return from_cuda(e);
+    return (repro_status)groupby_dispatch((const int32_t*)keys.p, values, n, dtype, L, 1, state, s);
+}
+
 repro_status repro_merge(void* dst, const void* src, repro_dtype dtype, int L, int64_t num_groups, void* stream) {
     if (!dst || !src || !valid_dtype(dtype) || !valid_shape(L, num_groups)) return REPRO_EINVAL;
     if (dst == src || (uintptr_t)dst % 16 || (uintptr_t)src % 16) return REPRO_EINVAL;

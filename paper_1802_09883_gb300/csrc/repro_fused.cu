@@ -81,6 +81,11 @@ __global__ void __launch_bounds__(32 * (NCW + 1)) k_fused(FusedArgs a) {
         sF[g] = 0;
     }
     if (tid < 16) ctl[tid] = 0;
+    // without a key column every row belongs to group 0: the key ring holds
+    // zeros and the producer never copies into it
+    const bool keyless = a.keys == nullptr;
+    if (keyless)
+        for (int i = tid; i < S * R; i += blockDim.x) skeys[i] = 0;
     if (tid == 0) {
         for (int s = 0; s < S; ++s) {
             mbar_init(&full[s], 1);
@@ -98,7 +103,7 @@ __global__ void __launch_bounds__(32 * (NCW + 1)) k_fused(FusedArgs a) {
     if (tid >= NC) {
         // ---------------------------------------------------------- producer
         if (tid == NC) {
-            const uint32_t kb = (uint32_t)R * 4, vb = (uint32_t)R * sizeof(T);
+            const uint32_t kb = keyless ? 0u : (uint32_t)R * 4, vb = (uint32_t)R * sizeof(T);
             int issued = 0;
             for (int i = 0; i < ntile; ++i) {
                 const int s = i % S;
@@ -109,7 +114,7 @@ __global__ void __launch_bounds__(32 * (NCW + 1)) k_fused(FusedArgs a) {
                 }
                 const long long row0 = (t0 + i) * (long long)R;
                 mbar_arrive_expect_tx(&full[s], kb + vb);
-                bulk_g2s(skeys + (size_t)s * R, a.keys + row0, kb, &full[s]);
+                if (!keyless) bulk_g2s(skeys + (size_t)s * R, a.keys + row0, kb, &full[s]);
                 bulk_g2s(svals + (size_t)s * R, vals + row0, vb, &full[s]);
                 ++issued;
             }
@@ -184,7 +189,7 @@ __global__ void __launch_bounds__(32 * (NCW + 1)) k_fused(FusedArgs a) {
             named_bar_sync(1, NC);
         }
         int* cnt = &ctl[2 * (tcount % 3)];
-        const int32_t* tk = a.keys + tail0;
+        const int32_t* tk = keyless ? skeys : a.keys + tail0;  // fewer than R tail rows
         const T* tv = vals + tail0;
         for (int r = ctid; r < rows; r += NC)
             consume_row<T, L>(tk[r], tv[r], r, G, tab, copy, sK, sKp, sF, dlist, rlist, cnt, bad_key);
