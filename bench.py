@@ -48,9 +48,10 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-tune", action="store_true", help="skip the untimed autotuning before the warm-up")
     ap.add_argument("--verify", action="store_true", help="check sampled groups against the oracle")
-    ap.add_argument("--workload", default="sweep", choices=["sweep", "multicol", "batched", "serve"],
+    ap.add_argument("--workload", default="sweep", choices=["sweep", "multicol", "batched", "serve", "scalar", "stats"],
                     help="sweep: one grouped SUM (default); multicol: 4 SUM columns over two uint8 keys; "
-                         "batched: many aggregations in one launch; serve: the request server")
+                         "batched: many aggregations in one launch; serve: the request server; "
+                         "scalar: SUM without GROUP BY; stats: COUNT/SUM/AVG/VAR/STDDEV per group")
     ap.add_argument("--dtype", default="f64", choices=["f64", "f32"], help="multicol value type")
     ap.add_argument("--rows", type=int, default=0, help="multicol rows / serve table rows (0: default)")
     ap.add_argument("--tasks", type=int, default=4096, help="batched: number of aggregations")
@@ -679,6 +680,122 @@ def run_serve(args, local_rank):
     return res
 
 
+def run_scalar(args, local_rank):
+    """Reproducible SUM without GROUP BY over 2^28 float64 values (the sweep's
+    value recipe), against torch.sum in float64 on the same values."""
+    import torch
+
+    import paper_1802_09883_gb300 as R
+    from paper_1802_09883_gb300 import workloads as WL
+
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    lib = R.lib()
+    n = args.rows or (1 << 28)
+    w = WL.sweep_cell(16, "uniform", args.L, n=n, device=dev)
+    vals = w.values
+    del w
+    st = R.State(1, args.L, torch.float64, device=dev)
+    out = torch.empty(1, dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    tuned = None
+    if not args.no_tune:  # untimed; the keyless kernel shares the one-group configuration
+        zk = torch.zeros(n, dtype=torch.int32, device=dev)
+        tuned = R.tune(zk, vals, 1, args.L)
+        del zk
+
+    def step():
+        st.reset()
+        st.add_values(vals)
+        st.finalize(out)
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    st.check()
+    clocks = ClockSampler(local_rank)
+    _prof_start(lib)
+    l0 = lib.repro_launch_count()
+    clocks.start()
+    ms = _time(step, args.steps, stream)
+    clocks.stop()
+    launches = lib.repro_launch_count() - l0
+    prof = _prof_stop(lib)
+    ref = torch.empty((), dtype=torch.float64, device=dev)
+    torch.sum(vals, dim=0, out=ref)
+    base_ms = _time(lambda: torch.sum(vals, dim=0, out=ref), args.steps, stream)
+    peaks = load_peaks()
+    fused = prof.get("fused")
+    roof = None
+    if fused:
+        ach = n * 8 / (fused["ms_per_launch"] / 1e3) / 1e9
+        roof = {"bound": "hbm", "kernel": "fused (keyless)", "achieved": round(ach, 1), "peak": peaks["hbm_gbs"],
+                "unit": "GB/s", "frac": round(ach / peaks["hbm_gbs"], 4), "traffic": None,
+                "peak_source": peaks["source"], "ms_per_launch": fused["ms_per_launch"]}
+    res = _base_line(args, "repro SUM (no GROUP BY) values/s", n / (ms / 1e3), "values/s", ms, "f64",
+                     f"scalar SUM of {n} float64 values (exponents U[-40,40], 10% cancelling pairs), "
+                     f"repro<double,{args.L}>", {"n": n, "L": args.L, "l2": "inputs far larger than L2; no flush"})
+    res.update({"hbm_gbs_algorithmic": n * 8 / (ms / 1e3) / 1e9, "roofline": roof, "kernels": prof,
+                "fp64_baseline": {"kind": "torch.sum float64", "ms_per_step": base_ms,
+                                  "repro_over_fp64_time": ms / base_ms},
+                "e2e": None, "gpu_launches": int(launches), "clocks": clocks.summary(), "tuned": tuned})
+    return res
+
+
+def run_stats(args, local_rank):
+    """COUNT / SUM / AVG / VAR / STDDEV per group on the headline cell
+    (2^28 rows, G = 1024), against two FP64 GroupBys (x and x*x)."""
+    import torch
+
+    import paper_1802_09883_gb300 as R
+    from paper_1802_09883_gb300 import workloads as WL
+
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    lib = R.lib()
+    w = WL.sweep_cell(args.G, args.dist, args.L, n=args.n, device=dev)
+    n, G = w.n, w.G
+    st = R.Stats(G, args.L, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    outs = {}
+    if not args.no_tune:  # untimed
+        R.tune(w.keys, w.values, G, args.L)
+
+    def step():
+        nonlocal outs
+        lib.repro_stats_init(st.tensor.data_ptr(), st.code, st.L, st.G, stream.cuda_stream)
+        st.add(w.keys, w.values)
+        outs = st.finalize()
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    st.check()
+    clocks = ClockSampler(local_rank)
+    l0 = lib.repro_launch_count()
+    clocks.start()
+    ms = _time(step, args.steps, stream)
+    clocks.stop()
+    launches = lib.repro_launch_count() - l0
+    sq = w.values * w.values
+    fo1 = torch.empty(G, dtype=torch.float64, device=dev)
+    fo2 = torch.empty(G, dtype=torch.float64, device=dev)
+
+    def fp_step():
+        R.groupby_sum_fp64(w.keys, w.values, G, out=fo1)
+        R.groupby_sum_fp64(w.keys, sq, G, out=fo2)
+
+    fp_step()
+    fp_ms = _time(fp_step, args.steps, stream)
+    res = _base_line(args, "repro COUNT/SUM/AVG/VAR/STDDEV GroupBy rows/s", n / (ms / 1e3), "rows/s", ms, "f64",
+                     f"per-group statistics, {n} rows, {G} groups {args.dist}, repro<double,{args.L}> sums of x "
+                     f"and x*x", {"n": n, "G": G, "dist": args.dist, "L": args.L,
+                                  "l2": "inputs far larger than L2; no flush"})
+    res.update({"hbm_gbs_algorithmic": n * 12 / (ms / 1e3) / 1e9, "roofline": None,
+                "fp64_baseline": {"kind": "two groupby_sum_fp64 (x, x*x precomputed)", "ms_per_step": fp_ms,
+                                  "repro_over_fp64_time": ms / fp_ms},
+                "e2e": None, "gpu_launches": int(launches), "clocks": clocks.summary()})
+    return res
+
+
 # -------------------------------------------------------- CPU oracle timing
 
 def cpu_oracle_rate(G, dist, L, rows, threads):
@@ -757,7 +874,8 @@ def main():
         return
     if args.workload != "sweep":
         if rank == 0:
-            fn = {"multicol": run_multicol, "batched": run_batched, "serve": run_serve}[args.workload]
+            fn = {"multicol": run_multicol, "batched": run_batched, "serve": run_serve, "scalar": run_scalar,
+                  "stats": run_stats}[args.workload]
             print(json.dumps(fn(args, local_rank)), flush=True)
         return
     res = run_ours(args, rank, world, local_rank)
