@@ -558,6 +558,7 @@ def run_batched(args, local_rank):
     plan.set_outputs(outs)
     t_plan = time.time() - t_plan
     tune_ms = None if args.no_tune else plan.tune()  # untimed: item size for this batch
+    plan_info = plan.describe()
     side = torch.cuda.Stream(dev)
     side.wait_stream(torch.cuda.current_stream(dev))
     with torch.cuda.stream(side):
@@ -600,7 +601,6 @@ def run_batched(args, local_rank):
     peaks = load_peaks()
     algo = rows * 12 + groups * 8
     ach = algo / (ms / 1e3) / 1e9
-    slow = sum(1 for _, _, G in tasks if G > 9000)
     res = _base_line(args, "repro batched GroupBy-SUM rows/s (independent aggregations, one graph replay)",
                      rows / (ms / 1e3), "rows/s", ms, "f64",
                      f"batched: {len(tasks)} aggregations, rows log-uniform 1e3-1e7, groups log-uniform 1-1e5, "
@@ -616,8 +616,7 @@ def run_batched(args, local_rank):
                 "e2e": None, "e2e_note": "inputs of this workload are generated on the device (tens of GB)",
                 "gpu_launches": int(per_step_launches * args.steps), "clocks": clocks.summary(),
                 "verify": {"tasks_checked": len(sample), "bit_equal_to_single_task": bool(same)},
-                "plan": {"prepare_s": t_plan, "tasks_beyond_smem_table": slow, "generate_s": t_gen,
-                         "tuned_run_ms": tune_ms}})
+                "plan": dict(plan_info, prepare_s=t_plan, generate_s=t_gen, tuned_run_ms=tune_ms)})
     plan.close()
     return res
 

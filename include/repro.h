@@ -197,9 +197,13 @@ repro_status repro_groupby_sum_noalloc(const int32_t* keys, const void* values, 
  * single-pass path share the persistent launch: the plan cuts them into
  * work items of whole tiles (the item size is tuned to the batch: about four
  * items per CTA, at most 2^23 rows), largest first; an item that covers a
- * whole task merges straight into its state.  Other tasks run one after
- * the other inside repro_batch_run: through the partitioned path (large
- * group counts), or the two-pass path (rows not 16-byte aligned).
+ * whole task merges straight into its state.  Tasks with more groups
+ * than one shared-memory table holds (and 16-byte aligned rows, up to 2^19
+ * groups) share one batched partition pass -- one partitioning of all of
+ * them and one multi-task launch over their partitions -- on a side stream
+ * forked from `stream` and joined back; any other task (larger group
+ * counts, unaligned rows) runs its own partitioned or two-pass chain on
+ * eight more side streams.
  * All tasks use the same dtype and L; states must not overlap.
  */
 typedef struct {
@@ -216,6 +220,21 @@ repro_status repro_batch_prepare(const repro_task* tasks, int ntasks, repro_dtyp
                                  repro_batch_plan* plan);
 repro_status repro_batch_run(repro_batch_plan plan, void* stream);
 repro_status repro_batch_destroy(repro_batch_plan plan);
+/* How a prepared plan runs its tasks (a diagnostic; nothing is launched). */
+typedef struct {
+    int32_t tasks;             /* tasks of the plan (including empty ones) */
+    int32_t single_pass_tasks; /* in the one persistent launch */
+    int32_t partition_tasks;   /* in the batched partition pass */
+    int32_t lane_tasks;        /* each on its own side-stream chain */
+    int32_t items;             /* work items of the persistent launch */
+    int32_t merge_blocks;
+    int32_t items_per_cta;     /* item sizing target (repro_batch_tune may change it) */
+    int32_t partition_overlap; /* 1: the partition pass runs beside the persistent launch, 0: before it */
+    int64_t device_bytes;      /* device memory the plan holds */
+} repro_batch_info;
+
+repro_status repro_batch_describe(repro_batch_plan plan, repro_batch_info* out);
+
 /* Re-initialise every task's state (one launch; capturable). */
 repro_status repro_batch_reset(repro_batch_plan plan, void* stream);
 
@@ -430,7 +449,8 @@ repro_status repro_tune_load(const char* path);
 void repro_tune_clear(void);
 
 /* Time the plan with work items of several sizes (about 1, 2, 4, 8 and 16
-   items per CTA) and keep the fastest; *best_ms (may be NULL) receives its
+   items per CTA) and, when it has a batched partition pass, with that pass
+   beside the persistent launch and before it; keep the fastest; *best_ms (may be NULL) receives its
    median time per run.  Runs the plan several times on `stream` and
    synchronises; afterwards every task's state is re-initialised (as
    repro_batch_reset). */

@@ -80,6 +80,7 @@ def lib(build_if_stale: bool = True):
         L.repro_batch_run.argtypes = [vp, vp]
         L.repro_batch_destroy.argtypes = [vp]
         L.repro_batch_reset.argtypes = [vp, vp]
+        L.repro_batch_describe.argtypes = [vp, vp]
         L.repro_batch_set_outputs.argtypes = [vp, vp]
         L.repro_batch_finalize.argtypes = [vp, vp]
         L.repro_groupby_sum_batched.argtypes = [vp, i32, i32, i32, vp]
@@ -113,7 +114,7 @@ def lib(build_if_stale: bool = True):
         L.repro_stats_finalize.argtypes = [vp, i32, i32, i64, vp, vp]
         for name in ("repro_state_init", "repro_groupby_sum", "repro_groupby_sum_noalloc", "repro_merge",
                      "repro_finalize", "repro_batch_prepare", "repro_batch_run", "repro_batch_destroy",
-                     "repro_batch_reset", "repro_batch_set_outputs", "repro_batch_finalize",
+                     "repro_batch_reset", "repro_batch_set_outputs", "repro_batch_finalize", "repro_batch_describe",
                      "repro_groupby_sum_batched", "repro_groupby_sum_cols", "repro_release_cached_memory",
                      "repro_state_check", "groupby_sum_fp64", "groupby_sum_fp32", "repro_server_create",
                      "repro_server_submit", "repro_server_poll", "repro_server_wait", "repro_server_release",
@@ -297,6 +298,14 @@ class _Task(ctypes.Structure):
                 ("num_groups", ctypes.c_int64), ("state", ctypes.c_void_p)]
 
 
+class _BatchInfo(ctypes.Structure):
+    _fields_ = [("tasks", ctypes.c_int32), ("single_pass_tasks", ctypes.c_int32),
+                ("partition_tasks", ctypes.c_int32), ("lane_tasks", ctypes.c_int32), ("items", ctypes.c_int32),
+                ("merge_blocks", ctypes.c_int32), ("items_per_cta", ctypes.c_int32),
+                ("partition_overlap", ctypes.c_int32),
+                ("device_bytes", ctypes.c_int64)]
+
+
 class BatchPlan:
     """Many independent grouped SUMs in one persistent launch.
 
@@ -330,6 +339,13 @@ class BatchPlan:
     def run(self):
         _check(lib().repro_batch_run(self._plan, _stream(self.device)), "repro_batch_run")
         return self
+
+    def describe(self) -> dict:
+        """How the plan runs its tasks (single pass / batched partition pass /
+        side lanes), its items and the device memory it holds."""
+        info = _BatchInfo()
+        _check(lib().repro_batch_describe(self._plan, ctypes.byref(info)), "repro_batch_describe")
+        return {name: getattr(info, name) for name, _ in _BatchInfo._fields_}
 
     def tune(self) -> float:
         """Time item sizes for this plan and keep the fastest (the states are

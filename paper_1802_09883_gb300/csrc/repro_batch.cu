@@ -601,7 +601,22 @@ struct BatchPlan {
     cudaEvent_t fork = nullptr;
     size_t slow_each = 0;
     unsigned char* d_slow_scratch = nullptr;
+    // The aligned large-group tasks instead share one batched partition pass
+    // (one hist / scan / scatter and one multi-task launch) on its own lane.
+    BatchPartition bpart;
+    bool has_bpart = false;
+    bool bpart_overlap = true;  // on its own lane next to the persistent launch, else before it in stream order
+    int bpart_tasks = 0;
+    int single_tasks = 0;
+    size_t dev_bytes = 0;
+    unsigned char* d_bpart = nullptr;
+    cudaStream_t bpart_lane = nullptr;
+    cudaEvent_t bpart_join = nullptr;
 };
+
+// Largest group count routed to the batched partition pass (at most 128
+// partitions per task of width up to 4096).
+constexpr long long kBatchPartMaxGroups = 1 << 19;
 
 // Side streams for the tasks beyond the single-pass table.
 constexpr int kSlowLanes = 8;
@@ -661,6 +676,8 @@ repro_status repro_batch_prepare(const repro_task* tasks, int ntasks, repro_dtyp
     P.gcap_ = H.gcap;
     P.ctas = H.ctas;
     P.slow = H.slow;
+    for (int t = 0; t < ntasks; ++t) P.single_tasks += tasks[t].n > 0 ? 1 : 0;
+    P.single_tasks -= (int)H.slow.size();
     P.nitems = (int)H.items.size();
     P.nblks = (int)H.blks.size();
     P.ntasks = ntasks;
@@ -672,6 +689,28 @@ repro_status repro_batch_prepare(const repro_task* tasks, int ntasks, repro_dtyp
     }
     P.tasks.assign(tasks, tasks + ntasks);
     if (st == REPRO_OK) st = upload_items(P, H);
+    if (st == REPRO_OK && !P.slow.empty()) {
+        std::vector<BatchPartInput> bin;
+        std::vector<repro_task> rest;
+        for (const repro_task& k : P.slow) {
+            if (k.num_groups <= kBatchPartMaxGroups && (uintptr_t)k.keys % 16 == 0 && (uintptr_t)k.values % 16 == 0)
+                bin.push_back(BatchPartInput{k.keys, k.values, k.n, (int)k.num_groups, (unsigned char*)k.state});
+            else
+                rest.push_back(k);
+        }
+        if (!bin.empty() && P.bpart.plan(dtype, L, bin)) {
+            P.bpart_tasks = (int)bin.size();
+            P.dev_bytes += P.bpart.scratch_bytes();
+            cudaError_t e = cudaMalloc((void**)&P.d_bpart, P.bpart.scratch_bytes());
+            if (e == cudaSuccess) e = P.bpart.upload(P.d_bpart);
+            if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&P.bpart_lane, cudaStreamNonBlocking);
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&P.bpart_join, cudaEventDisableTiming);
+            if (e == cudaSuccess && !P.fork) e = cudaEventCreateWithFlags(&P.fork, cudaEventDisableTiming);
+            if (e != cudaSuccess) st = e == cudaErrorMemoryAllocation ? REPRO_ENOMEM : REPRO_ECUDA;
+            P.has_bpart = true;
+            P.slow = rest;
+        }
+    }
     if (st == REPRO_OK && !P.slow.empty()) {
         // tasks beyond the single-pass table: the partitioned path where it
         // applies, else the two-pass path
@@ -697,7 +736,7 @@ repro_status repro_batch_prepare(const repro_task* tasks, int ntasks, repro_dtyp
         P.slow_each = (need + 255) & ~(size_t)255;
         if (cudaMalloc((void**)&P.d_slow_scratch, P.slow_each * nl) != cudaSuccess) st = REPRO_ENOMEM;
         cudaError_t e = cudaSuccess;
-        if (st == REPRO_OK) e = cudaEventCreateWithFlags(&P.fork, cudaEventDisableTiming);
+        if (st == REPRO_OK && !P.fork) e = cudaEventCreateWithFlags(&P.fork, cudaEventDisableTiming);
         for (int l = 0; l < nl && st == REPRO_OK && e == cudaSuccess; ++l) {
             cudaStream_t ls = nullptr;
             cudaEvent_t je = nullptr;
@@ -723,10 +762,20 @@ repro_status repro_batch_run(repro_batch_plan plan, void* stream) {
     cudaError_t e = cudaSuccess;
     // fork: the side lanes start with the caller's stream as it stands here,
     // and run next to the persistent launch below
-    if (!P.slow.empty()) {
+    if (!P.slow.empty() || P.has_bpart) {
         if (cudaEventRecord(P.fork, s) != cudaSuccess) return REPRO_ECUDA;
         for (cudaStream_t ls : P.lanes)
             if (cudaStreamWaitEvent(ls, P.fork, 0) != cudaSuccess) return REPRO_ECUDA;
+    }
+    if (P.has_bpart) {
+        if (P.bpart_overlap) {
+            if (cudaStreamWaitEvent(P.bpart_lane, P.fork, 0) != cudaSuccess) return REPRO_ECUDA;
+            if (P.bpart.launch(P.d_bpart, P.bpart_lane) != cudaSuccess) return REPRO_ECUDA;
+        } else if (P.bpart.launch(P.d_bpart, s) != cudaSuccess) {
+            return REPRO_ECUDA;
+        }
+    }
+    if (!P.slow.empty()) {
         for (size_t i = 0; i < P.slow.size(); ++i) {
             const repro_task& k = P.slow[i];
             const int l = P.slow_lane[i];
@@ -754,6 +803,10 @@ repro_status repro_batch_run(repro_batch_plan plan, void* stream) {
     for (size_t l = 0; l < P.lanes.size(); ++l) {
         if (cudaEventRecord(P.joins[l], P.lanes[l]) != cudaSuccess) return REPRO_ECUDA;
         if (cudaStreamWaitEvent(s, P.joins[l], 0) != cudaSuccess) return REPRO_ECUDA;
+    }
+    if (P.has_bpart && P.bpart_overlap) {
+        if (cudaEventRecord(P.bpart_join, P.bpart_lane) != cudaSuccess) return REPRO_ECUDA;
+        if (cudaStreamWaitEvent(s, P.bpart_join, 0) != cudaSuccess) return REPRO_ECUDA;
     }
     return REPRO_OK;
 }
@@ -823,7 +876,10 @@ repro_status repro_batch_tune(repro_batch_plan plan, void* stream, double* best_
     repro_status st = REPRO_OK;
     double best = 0;
     int pick = P.items_per_cta;
-    for (int ipc : {1, 2, 4, 8, 16}) {
+    bool pick_overlap = P.bpart_overlap;
+    for (int trial = 0; trial < (P.has_bpart ? 10 : 5); ++trial) {
+        const int ipc = 1 << (trial % 5);
+        P.bpart_overlap = trial < 5;
         HostBatch H;
         st = plan_batch_host(P.tasks.data(), P.ntasks, P.dtype, P.L, kBatchPartBytes, H, ipc, &P.cfg);
         if (st == REPRO_OK) st = upload_items(P, H);
@@ -845,10 +901,12 @@ repro_status repro_batch_tune(repro_batch_plan plan, void* stream, double* best_
         if (best == 0 || med < best) {
             best = med;
             pick = ipc;
+            pick_overlap = P.bpart_overlap;
         }
     }
     cudaEventDestroy(a);
     cudaEventDestroy(b);
+    P.bpart_overlap = pick_overlap;
     if (st != REPRO_OK) return st;
     HostBatch H;
     st = plan_batch_host(P.tasks.data(), P.ntasks, P.dtype, P.L, kBatchPartBytes, H, pick, &P.cfg);
@@ -858,6 +916,23 @@ repro_status repro_batch_tune(repro_batch_plan plan, void* stream, double* best_
     if (st == REPRO_OK && cudaStreamSynchronize(s) != cudaSuccess) st = REPRO_ECUDA;
     if (best_ms) *best_ms = best;
     return st;
+}
+
+repro_status repro_batch_describe(repro_batch_plan plan, repro_batch_info* out) {
+    if (!plan || !out) return REPRO_EINVAL;
+    const BatchPlan& P = plan->p;
+    std::memset(out, 0, sizeof(*out));
+    out->tasks = P.ntasks;
+    out->partition_tasks = P.bpart_tasks;
+    out->lane_tasks = (int32_t)P.slow.size();
+    out->single_pass_tasks = P.single_tasks;
+    out->items = P.nitems;
+    out->merge_blocks = P.nblks;
+    out->items_per_cta = P.items_per_cta;
+    out->partition_overlap = P.has_bpart && P.bpart_overlap ? 1 : 0;
+    out->device_bytes = (int64_t)(P.dev_bytes + P.items_cap + P.blks_cap + P.parts_cap +
+                                  sizeof(MTask) * (size_t)P.ntasks + P.slow_each * P.lanes.size());
+    return REPRO_OK;
 }
 
 repro_status repro_batch_destroy(repro_batch_plan plan) {
@@ -873,6 +948,9 @@ repro_status repro_batch_destroy(repro_batch_plan plan) {
     for (cudaStream_t ls : P.lanes) cudaStreamDestroy(ls);
     for (cudaEvent_t je : P.joins) cudaEventDestroy(je);
     if (P.fork) cudaEventDestroy(P.fork);
+    cudaFree(P.d_bpart);
+    if (P.bpart_lane) cudaStreamDestroy(P.bpart_lane);
+    if (P.bpart_join) cudaEventDestroy(P.bpart_join);
     delete plan;
     return REPRO_OK;
 }

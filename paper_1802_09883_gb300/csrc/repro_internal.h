@@ -6,6 +6,7 @@
 
 #include <cstddef>
 #include <cstdint>
+#include <vector>
 
 namespace rp {
 
@@ -79,6 +80,31 @@ bool partitioned_supported(int dtype, int L, long long G, long long n, const voi
 size_t partitioned_scratch_bytes(const PartChoice& pc, int dtype, int L, long long G, long long n);
 cudaError_t launch_groupby_partitioned(const int32_t* keys, const void* vals, long long n, int dtype, int L,
                                        long long G, const PartChoice& pc, void* state, void* scratch, cudaStream_t s);
+
+// Many inputs partitioned in one pass and aggregated by one multi-task
+// launch (a batch's large-group tasks; repro_partition.cu).  plan() builds
+// the chunk list and tables on the host (false if the inputs do not qualify:
+// 16-byte aligned columns, at most 64 partitions per input), upload() copies
+// them into scratch (synchronous), launch() only enqueues kernels.
+struct BatchPartInput {
+    const int32_t* keys;
+    const void* vals;
+    long long n;
+    int G;
+    unsigned char* state;
+};
+struct BatchPartition {
+    struct Impl;
+    Impl* impl;
+    BatchPartition();
+    ~BatchPartition();
+    BatchPartition(const BatchPartition&) = delete;
+    BatchPartition& operator=(const BatchPartition&) = delete;
+    bool plan(int dtype, int L, const std::vector<BatchPartInput>& in);
+    size_t scratch_bytes() const;
+    cudaError_t upload(void* scratch) const;
+    cudaError_t launch(void* scratch, cudaStream_t s) const;
+};
 
 // Measured choices (repro_tune.cu).  The cache holds, per (dtype, L, group
 // count rounded up to a power of two), a single-pass configuration and a

@@ -29,6 +29,7 @@
 
 #include <algorithm>
 #include <cstdint>
+#include <vector>
 
 #include "multi_types.h"
 #include "repro_device.cuh"
@@ -65,18 +66,32 @@ struct PartChunk {
     int pad;
 };
 
+// One input of a batched partition pass (a task of a batch): chunks whose
+// seg is s read these columns, check keys against G and flag bad keys in
+// this error word.
+struct PartSeg {
+    const int32_t* keys;
+    const void* vals;
+    int G;
+    int pad;
+    unsigned* errors;
+};
+
 struct Units {
     long long chunk;          // rows per CTA chunk (chunks == nullptr)
     long long n;              // rows of the input (chunks == nullptr)
     const PartChunk* chunks;  // chunk list, or nullptr
     const int* nchunks;       // its length (device)
+    const PartSeg* segs;      // per chunk segment: its own input (batched pass), or nullptr
 };
 
-__device__ __forceinline__ bool unit_rows(const Units& u, int unit, long long& beg, long long& end) {
+__device__ __forceinline__ bool unit_rows(const Units& u, int unit, long long& beg, long long& end, int& seg) {
+    seg = 0;
     if (u.chunks) {
         if (unit >= *u.nchunks) return false;
         beg = u.chunks[unit].beg;
         end = u.chunks[unit].end;
+        seg = u.chunks[unit].seg;
         return true;
     }
     beg = unit * u.chunk;
@@ -87,14 +102,18 @@ __device__ __forceinline__ bool unit_rows(const Units& u, int unit, long long& b
 // A chunk list is walked grid-stride; a fixed chunking has one unit per CTA.
 __device__ __forceinline__ int unit_step(const Units& u) { return u.chunks ? (int)gridDim.x : 1 << 30; }
 
-__global__ void __launch_bounds__(kPartThreads) k_part_hist(const int32_t* __restrict__ keys, Units units,
+__global__ void __launch_bounds__(kPartThreads) k_part_hist(const int32_t* __restrict__ keys0, Units units,
                                                             PassGeom pg, int* __restrict__ counts,
-                                                            unsigned* __restrict__ errors) {
+                                                            unsigned* __restrict__ errors0) {
     extern __shared__ int s_hist[];
-    bool bad = false;
     for (int unit = blockIdx.x;; unit += unit_step(units)) {
         long long beg, end;
-        if (!unit_rows(units, unit, beg, end)) break;
+        int seg;
+        if (!unit_rows(units, unit, beg, end, seg)) break;
+        const int32_t* keys = units.segs ? units.segs[seg].keys : keys0;
+        const int Gk = units.segs ? units.segs[seg].G : pg.G;
+        unsigned* errors = units.segs ? units.segs[seg].errors : errors0;
+        bool bad = false;
         for (int p = threadIdx.x; p < pg.B; p += blockDim.x) s_hist[p] = 0;
         __syncthreads();
         // 4 keys per thread per step (beg is a multiple of 4, keys 16-byte aligned)
@@ -104,7 +123,7 @@ __global__ void __launch_bounds__(kPartThreads) k_part_hist(const int32_t* __res
             const int ks[4] = {k.x, k.y, k.z, k.w};
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
-                if (!pg.check || (unsigned)ks[q] < (unsigned)pg.G)
+                if (!pg.check || (unsigned)ks[q] < (unsigned)Gk)
                     atomicAdd(&s_hist[((unsigned)ks[q] >> pg.shift) & pg.bmask], 1);
                 else
                     bad = true;
@@ -112,18 +131,18 @@ __global__ void __launch_bounds__(kPartThreads) k_part_hist(const int32_t* __res
         }
         for (long long i = n4 + threadIdx.x; i < end; i += blockDim.x) {
             const int k = keys[i];
-            if (!pg.check || (unsigned)k < (unsigned)pg.G)
+            if (!pg.check || (unsigned)k < (unsigned)Gk)
                 atomicAdd(&s_hist[((unsigned)k >> pg.shift) & pg.bmask], 1);
             else
                 bad = true;
         }
+        if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(errors, REPRO_ERR_KEY);
         __syncthreads();
         for (int p = threadIdx.x; p < pg.B; p += blockDim.x)
             counts[(size_t)unit * pg.ustride + (size_t)p * pg.bstride] = s_hist[p];
         __syncthreads();
         if (!units.chunks) break;
     }
-    if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(errors, REPRO_ERR_KEY);
 }
 
 // Partitions of a scan: F = segments * B; segment s owns units
@@ -288,8 +307,8 @@ __device__ int block_exclusive_scan(int* a, int n, int* warp_tot) {
 // memory, and consecutive threads then write consecutive runs (coalesced
 // stores).
 template <typename T>
-__global__ void __launch_bounds__(kPartThreads) k_part_scatter(const int32_t* __restrict__ keys,
-                                                               const T* __restrict__ vals, Units units,
+__global__ void __launch_bounds__(kPartThreads) k_part_scatter(const int32_t* __restrict__ keys0,
+                                                               const T* __restrict__ vals0, Units units,
                                                                PassGeom pg, const int* __restrict__ offsets,
                                                                int32_t* __restrict__ okeys, T* __restrict__ ovals) {
     extern __shared__ __align__(16) unsigned char s_raw[];
@@ -303,7 +322,11 @@ __global__ void __launch_bounds__(kPartThreads) k_part_scatter(const int32_t* __
     int* s_wt = s_gb + pg.B;                              // [33] scan scratch
     for (int unit = blockIdx.x;; unit += unit_step(units)) {
         long long beg, end;
-        if (!unit_rows(units, unit, beg, end)) break;
+        int seg;
+        if (!unit_rows(units, unit, beg, end, seg)) break;
+        const int32_t* keys = units.segs ? units.segs[seg].keys : keys0;
+        const T* vals = units.segs ? static_cast<const T*>(units.segs[seg].vals) : vals0;
+        const int Gk = units.segs ? units.segs[seg].G : pg.G;
         for (int p = threadIdx.x; p < pg.B; p += blockDim.x) {
             s_cur[p] = offsets[(size_t)unit * pg.ustride + (size_t)p * pg.bstride];
             s_cnt[p] = 0;
@@ -335,7 +358,7 @@ __global__ void __launch_bounds__(kPartThreads) k_part_scatter(const int32_t* __
             }
 #pragma unroll
             for (int j = 0; j < RPT; ++j) {
-                const bool ok = k[j] >= 0 && (!pg.check || k[j] < pg.G);
+                const bool ok = k[j] >= 0 && (!pg.check || k[j] < Gk);
                 rank[j] = ok ? atomicAdd(&s_cnt[((unsigned)k[j] >> pg.shift) & pg.bmask], 1) : -1;
             }
             __syncthreads();
@@ -455,13 +478,35 @@ struct PartGeom {
 };
 
 // One block: partitions -> tasks, work items, merge blocks, partial offsets.
+// The owner of final partition p: one input (tt null: state hdr with G
+// groups, slice p) or, in a batched pass, task p / B of tt (slice p mod B).
+struct PartTask {
+    int G;
+    int pad;
+    unsigned char* hdr;
+};
+
+__device__ __forceinline__ void part_owner(int p, const PartTask* tt, int B, int G, unsigned char* hdr, int& j,
+                                           int& Gt, unsigned char*& h) {
+    if (tt) {
+        const int t = p / B;
+        j = p - t * B;
+        Gt = tt[t].G;
+        h = tt[t].hdr;
+    } else {
+        j = p;
+        Gt = G;
+        h = hdr;
+    }
+}
+
 __global__ void __launch_bounds__(1024) k_part_plan(const long long* __restrict__ pstart,
                                                     const long long* __restrict__ pcount, PartGeom pg, int G, int R,
                                                     long long tpi, const int32_t* okeys, const void* ovals,
                                                     size_t vsize, unsigned char* hdr, int L,
-                                                    const int* __restrict__ win, MTask* __restrict__ tasks,
-                                                    MItem* __restrict__ items, int* nitems, MergeBlk* __restrict__ blks,
-                                                    int* nblks) {
+                                                    const int* __restrict__ win, const PartTask* __restrict__ tt,
+                                                    int B, MTask* __restrict__ tasks, MItem* __restrict__ items,
+                                                    int* nitems, MergeBlk* __restrict__ blks, int* nblks) {
     __shared__ long long s_it[1024], s_pt[1024], s_bk[1024];
     const size_t rec = 8 + 16 * (size_t)L;
     const int per = (pg.F + blockDim.x - 1) / blockDim.x;
@@ -469,8 +514,11 @@ __global__ void __launch_bounds__(1024) k_part_plan(const long long* __restrict_
     long long it = 0, pt = 0, bk = 0;
     for (int p = p0; p < p1; ++p) {
         const long long cnt = pcount[p];
-        const int Gp = min(pg.Gp, G - p * pg.Gp);
-        const long long nit = cnt == 0 ? 0 : (((cnt + R - 1) / R) + tpi - 1) / tpi;
+        int j, Gt;
+        unsigned char* h;
+        part_owner(p, tt, B, G, hdr, j, Gt, h);
+        const int Gp = max(0, min(pg.Gp, Gt - j * pg.Gp));
+        const long long nit = cnt == 0 || Gp == 0 ? 0 : (((cnt + R - 1) / R) + tpi - 1) / tpi;
         it += nit;
         if (nit > 1) {
             pt += nit * Gp;
@@ -501,18 +549,21 @@ __global__ void __launch_bounds__(1024) k_part_plan(const long long* __restrict_
     bk = s_bk[threadIdx.x];
     for (int p = p0; p < p1; ++p) {
         const long long cnt = pcount[p];
-        const int Gp = min(pg.Gp, G - p * pg.Gp);
+        int j, Gt;
+        unsigned char* h;
+        part_owner(p, tt, B, G, hdr, j, Gt, h);
+        const int Gp = max(0, min(pg.Gp, Gt - j * pg.Gp));
         MTask t;
         t.keys = okeys + pstart[p];
         t.vals = static_cast<const unsigned char*>(ovals) + (size_t)pstart[p] * vsize;
         t.n = cnt;
         t.G = Gp;
-        t.G_hdr = G;
-        t.hdr = hdr;
-        t.recs = hdr + sizeof(repro_state_header) + (size_t)p * pg.Gp * rec;
+        t.G_hdr = Gt;
+        t.hdr = h;
+        t.recs = h + sizeof(repro_state_header) + (size_t)j * pg.Gp * rec;
         t.win = win ? win + (size_t)p * pg.Gp : nullptr;
         tasks[p] = t;
-        const long long nit = cnt == 0 ? 0 : (((cnt + R - 1) / R) + tpi - 1) / tpi;
+        const long long nit = cnt == 0 || Gp == 0 ? 0 : (((cnt + R - 1) / R) + tpi - 1) / tpi;
         for (long long k = 0; k < nit; ++k) {
             MItem m;
             m.task = p;
@@ -760,7 +811,7 @@ cudaError_t launch_groupby_partitioned(const int32_t* keys, const void* vals, lo
     int* ints = (int*)(b + ly.ints);  // nitems, nblks, counter, nchunks
     unsigned* errors = &reinterpret_cast<repro_state_header*>(state)->errors;
     cudaError_t e;
-    const Units whole{pp.chunk, n, nullptr, nullptr};
+    const Units whole{pp.chunk, n, nullptr, nullptr, nullptr};
     prof_begin(PROF_PARTITION, s);
     if (pp.levels == 1) {
         const ScanGeom sg{pp.Fs, pp.Fs, 1, pp.C, pp.C, nullptr, nullptr};
@@ -781,7 +832,7 @@ cudaError_t launch_groupby_partitioned(const int32_t* keys, const void* vals, lo
         k_seg_chunks<<<1, 1024, 0, s>>>(pstart1, pcount1, pp.F1, kChunkRows, chunks, cbase, nunits, ints + 3);
         count_launches(1);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
-        const Units fine{0, 0, chunks, ints + 3};
+        const Units fine{0, 0, chunks, ints + 3, nullptr};
         const ScanGeom sg2{pp.Fs, pp.F2, pp.F2, 1, 0, cbase, nunits};
         e = partition_pass(akeys, avals, dtype, fine, pp.p2, sg2, pp.C, (int*)(b + ly.counts2), (int*)(b + ly.offsets2),
                            (long long*)(b + ly.ptot), pstart, pcount, okeys, ovals, errors, s);
@@ -807,7 +858,8 @@ cudaError_t launch_groupby_partitioned(const int32_t* keys, const void* vals, lo
     }
     PartGeom pg{pp.F, pc.shift, pp.Gp};
     k_part_plan<<<1, 1024, 0, s>>>(pstart, pcount, pg, (int)G, pp.cfg.R, pp.tpi, okeys, ovals,
-                                   dtype == REPRO_F64 ? 8 : 4, (unsigned char*)state, L, win, (MTask*)(b + ly.tasks),
+                                   dtype == REPRO_F64 ? 8 : 4, (unsigned char*)state, L, win, nullptr, 0,
+                                   (MTask*)(b + ly.tasks),
                                    (MItem*)(b + ly.items), ints, (MergeBlk*)(b + ly.blks), ints + 1);
     count_launches(1);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
@@ -816,6 +868,169 @@ cudaError_t launch_groupby_partitioned(const int32_t* keys, const void* vals, lo
     if (e != cudaSuccess) return e;
     if (pp.max_blks > 0)
         e = launch_merge_items(L, dtype, b + ly.tasks, b + ly.blks, (int)pp.max_blks, ints + 1, b + ly.parts, s);
+    return e;
+}
+
+// ------------------------------------------------------------------
+// Batched partition pass: many inputs (a batch's large-group tasks), each
+// with its own columns, group count and state, partitioned by one hist /
+// scan / scatter over a chunk list of all of them, aggregated by one
+// multi-task launch.  Partition width and single-pass configuration are
+// common; B = the largest task's partition count, and final partition p
+// belongs to task p / B, slice p mod B.
+
+namespace {
+
+constexpr long long kBatchBuckets = 128;  // partitions per task of a batched pass
+
+struct BatchLayout {
+    size_t okeys, ovals, chunks, segs, ptask, cbase, nunits, counts, offsets, ptot, pstart, pcount;
+    size_t tasks, items, blks, parts, ints, total;
+};
+
+}  // namespace
+
+struct BatchPartition::Impl {
+    int dtype = 0, L = 0, T = 0, B = 0, F = 0, Gp = 0, ctas = 0;
+    PartChoice pc{};
+    long long rows_out = 0, tpi = 0, max_items = 0, max_blks = 0, max_part_recs = 0;
+    std::vector<PartChunk> chunks;
+    std::vector<PartSeg> segs;
+    std::vector<PartTask> ptask;
+    std::vector<int> cbase, nunits;
+    BatchLayout ly{};
+};
+
+BatchPartition::BatchPartition() : impl(new Impl) {}
+BatchPartition::~BatchPartition() { delete impl; }
+
+bool BatchPartition::plan(int dtype, int L, const std::vector<BatchPartInput>& in) {
+    Impl& P = *impl;
+    P = Impl{};
+    if (in.empty()) return false;
+    long long Gmax = 1, total_rows = 0;
+    for (const BatchPartInput& t : in) {
+        if ((uintptr_t)t.keys % 16 || (uintptr_t)t.vals % 16 || t.n <= 0 || t.G < 1) return false;
+        Gmax = std::max<long long>(Gmax, t.G);
+        total_rows += t.n;
+    }
+    if (total_rows > (1ll << 31) - 8ll * kMaxParts - 4096) return false;
+    if (!partition_choose(dtype, L, Gmax, P.pc)) return false;
+    // one pass: a chunk's rows spread over at most kBatchBuckets buckets of
+    // its own task (tiles of 4096 rows still write runs of 32+ rows); widen
+    // the partitions if the largest task needs it
+    const int need = ceil_log2((Gmax + kBatchBuckets - 1) / kBatchBuckets);
+    if (need > P.pc.shift) {
+        if (!shift_usable(dtype, L, Gmax, need, P.pc.cfg)) return false;
+        P.pc.shift = need;
+    }
+    P.pc.shift1 = 0;
+    P.dtype = dtype;
+    P.L = L;
+    P.T = (int)in.size();
+    P.Gp = 1 << P.pc.shift;
+    P.B = (int)((Gmax + P.Gp - 1) / P.Gp);
+    if (P.B > kBatchBuckets || (long long)P.T * P.B > (1ll << 24)) return false;
+    P.F = P.T * P.B;
+    for (int t = 0; t < P.T; ++t) {
+        const BatchPartInput& x = in[t];
+        P.cbase.push_back((int)P.chunks.size());
+        for (long long b = 0; b < x.n; b += kChunkRows)
+            P.chunks.push_back(PartChunk{b, std::min(x.n, b + kChunkRows), t, 0});
+        P.nunits.push_back((int)P.chunks.size() - P.cbase.back());
+        P.segs.push_back(PartSeg{x.keys, x.vals, x.G, 0, &reinterpret_cast<repro_state_header*>(x.state)->errors});
+        P.ptask.push_back(PartTask{x.G, 0, x.state});
+    }
+    const DeviceInfo& di = device_info();
+    P.ctas = di.sms * P.pc.cfg.ctas_per_sm;
+    const long long R = P.pc.cfg.R;
+    long long total_tiles = P.F;
+    for (const BatchPartInput& x : in) total_tiles += (x.n + R - 1) / R;
+    P.tpi = std::max(8ll, (total_tiles + 2ll * P.ctas - 1) / (2ll * P.ctas));
+    P.tpi = std::min(P.tpi, (1ll << 23) / R);
+    P.max_items = total_tiles / P.tpi + P.F + 1;
+    const long long max_split = std::min<long long>(P.F, total_tiles / P.tpi + 1);
+    P.max_blks = max_split * ((P.Gp + 31) / 32);
+    P.max_part_recs = (total_tiles / P.tpi + 1 + max_split) * (long long)P.Gp;
+    P.rows_out = total_rows + 4ll * P.F;
+    const size_t vs = dtype == REPRO_F64 ? 8 : 4;
+    const size_t nch = P.chunks.size();
+    BatchLayout& ly = P.ly;
+    size_t o = 0;
+    auto take = [&](size_t& at, size_t bytes) {
+        at = o;
+        o = align256(o + bytes);
+    };
+    take(ly.okeys, (size_t)P.rows_out * 4);
+    take(ly.ovals, (size_t)P.rows_out * vs);
+    take(ly.chunks, nch * sizeof(PartChunk));
+    take(ly.segs, (size_t)P.T * sizeof(PartSeg));
+    take(ly.ptask, (size_t)P.T * sizeof(PartTask));
+    take(ly.cbase, (size_t)P.T * 4);
+    take(ly.nunits, (size_t)P.T * 4);
+    take(ly.counts, nch * (size_t)P.B * 4);
+    take(ly.offsets, nch * (size_t)P.B * 4);
+    take(ly.ptot, (size_t)P.F * 8);
+    take(ly.pstart, (size_t)P.F * 8);
+    take(ly.pcount, (size_t)P.F * 8);
+    take(ly.tasks, (size_t)P.F * sizeof(MTask));
+    take(ly.items, (size_t)P.max_items * sizeof(MItem));
+    take(ly.blks, (size_t)std::max(1ll, P.max_blks) * sizeof(MergeBlk));
+    take(ly.parts, (size_t)P.max_part_recs * (8 + 16 * (size_t)L));
+    take(ly.ints, 8 * sizeof(int));
+    ly.total = o;
+    return true;
+}
+
+size_t BatchPartition::scratch_bytes() const { return impl->ly.total; }
+
+cudaError_t BatchPartition::upload(void* scratch) const {
+    const Impl& P = *impl;
+    unsigned char* b = (unsigned char*)scratch;
+    const int nch = (int)P.chunks.size();
+    cudaError_t e = cudaMemcpy(b + P.ly.chunks, P.chunks.data(), P.chunks.size() * sizeof(PartChunk),
+                               cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(b + P.ly.segs, P.segs.data(), P.segs.size() * sizeof(PartSeg), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(b + P.ly.ptask, P.ptask.data(), P.ptask.size() * sizeof(PartTask), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(b + P.ly.cbase, P.cbase.data(), P.cbase.size() * 4, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(b + P.ly.nunits, P.nunits.data(), P.nunits.size() * 4, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(b + P.ly.ints + 4 * sizeof(int), &nch, sizeof(int), cudaMemcpyHostToDevice);
+    return e;
+}
+
+cudaError_t BatchPartition::launch(void* scratch, cudaStream_t s) const {
+    const Impl& P = *impl;
+    unsigned char* b = (unsigned char*)scratch;
+    int* ints = (int*)(b + P.ly.ints);  // nitems, nblks, counter, -, nchunks
+    const Units u{0, 0, (const PartChunk*)(b + P.ly.chunks), ints + 4, (const PartSeg*)(b + P.ly.segs)};
+    const PassGeom pg{P.B, P.pc.shift, 0xffffffffu, (unsigned)P.Gp - 1, 1, 0, P.B, 1};
+    const ScanGeom sg{P.F, P.B, P.B, 1, 0, (const int*)(b + P.ly.cbase), (const int*)(b + P.ly.nunits)};
+    int32_t* okeys = (int32_t*)(b + P.ly.okeys);
+    void* ovals = b + P.ly.ovals;
+    long long* pstart = (long long*)(b + P.ly.pstart);
+    long long* pcount = (long long*)(b + P.ly.pcount);
+    prof_begin(PROF_PARTITION, s);
+    cudaError_t e = partition_pass(nullptr, nullptr, P.dtype, u, pg, sg, device_info().sms * 2, (int*)(b + P.ly.counts),
+                                   (int*)(b + P.ly.offsets), (long long*)(b + P.ly.ptot), pstart, pcount, okeys, ovals,
+                                   nullptr, s);
+    prof_end(PROF_PARTITION, s);
+    if (e != cudaSuccess) return e;
+    const PartGeom geo{P.F, P.pc.shift, P.Gp};
+    k_part_plan<<<1, 1024, 0, s>>>(pstart, pcount, geo, 0, P.pc.cfg.R, P.tpi, okeys, ovals,
+                                   P.dtype == REPRO_F64 ? 8 : 4, nullptr, P.L, nullptr,
+                                   (const PartTask*)(b + P.ly.ptask), P.B, (MTask*)(b + P.ly.tasks),
+                                   (MItem*)(b + P.ly.items), ints, (MergeBlk*)(b + P.ly.blks), ints + 1);
+    count_launches(1);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    e = launch_multi(P.dtype, P.L, P.pc.cfg, P.Gp, b + P.ly.tasks, b + P.ly.items, (int)P.max_items, ints, ints + 2,
+                     b + P.ly.parts, P.ctas, s);
+    if (e != cudaSuccess) return e;
+    if (P.max_blks > 0)
+        e = launch_merge_items(P.L, P.dtype, b + P.ly.tasks, b + P.ly.blks, (int)P.max_blks, ints + 1, b + P.ly.parts,
+                               s);
     return e;
 }
 

@@ -121,3 +121,37 @@ def test_batch_reset_and_finalize_in_one_launch_each():
             assert torch.equal(st.tensor, ref.tensor), rep
             assert torch.equal(o.view(torch.int64), ref.finalize().view(torch.int64)), rep
     plan.close()
+
+
+def test_many_large_group_tasks_share_one_partition_pass():
+    g = torch.Generator(device=DEV)
+    g.manual_seed(77)
+    rs = np.random.default_rng(77)
+    tasks = []
+    for i in range(40):
+        n = int(np.exp(rs.uniform(np.log(1), np.log(3e5))))
+        G = int(np.exp(rs.uniform(np.log(7000), np.log(131072))))
+        if i == 5:
+            G = 700_000  # beyond the batched pass: its own lane
+        keys = WL.uniform_keys(n, G, g, DEV)
+        vals = WL.random_values(n, -45, 45, g, DEV)
+        if i == 9 and n > 3:
+            keys[n // 2] = G + 1  # one bad key, in this task only
+        tasks.append((keys, vals, G))
+    states = [R.State(G, 3) for _, _, G in tasks]
+    plan = R.BatchPlan([(k, v, st) for (k, v, _), st in zip(tasks, states)])
+    info = plan.describe()
+    assert info["partition_tasks"] >= 30 and info["lane_tasks"] == 1, info
+    plan.run()
+    torch.cuda.synchronize()
+    plan.close()
+    for i, ((k, v, G), st) in enumerate(zip(tasks, states)):
+        ref = R.State(G, 3)
+        ref.add(k, v)
+        torch.cuda.synchronize()
+        assert torch.equal(st.tensor, ref.tensor), (i, k.numel(), G)
+        if i == 9 and k.numel() > 3:
+            with pytest.raises(R.ReproError):
+                st.check()
+        else:
+            assert st.check() == 0
