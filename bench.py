@@ -486,6 +486,19 @@ def run_multicol(args, local_rank):
 
     fp_step()
     fp_ms = _time(fp_step, args.steps, stream)
+    # DECIMAL baseline: the same four columns as exact scaled integers (p, d
+    # in hundredths; p * (1 - d), p * d in ten-thousandths), int64 sums per group
+    dec = [torch.round(cols[0].double() * 100).long(), torch.round(cols[1].double() * 100).long(),
+           torch.round(cols[2].double() * 10000).long(), torch.round(cols[3].double() * 10000).long()]
+    dec_out = [torch.empty(G, dtype=torch.int64, device=dev) for _ in dec]
+
+    def dec_step():
+        for c, o in zip(dec, dec_out):
+            R.groupby_sum_decimal64(gid, c, G, out=o)
+
+    dec_step()
+    dec_ms = _time(dec_step, args.steps, stream)
+    del dec
     # end to end from pinned host buffers
     k1h, k2h = k1.cpu().pin_memory(), k2.cpu().pin_memory()
     colsh = cols.cpu().pin_memory()
@@ -527,6 +540,8 @@ def run_multicol(args, local_rank):
     res.update({"hbm_gbs_algorithmic": algo / (ms / 1e3) / 1e9, "roofline": roof, "kernels": prof,
                 "fp64_baseline": {"kind": "fp64" if esz == 8 else "fp32", "ms_per_step": fp_ms,
                                   "repro_over_fp_time": ms / fp_ms},
+                "decimal_baseline": {"kind": "4 x groupby_sum_decimal64 (exact int64, scaled columns)",
+                                     "ms_per_step": dec_ms, "repro_over_decimal_time": ms / dec_ms},
                 "e2e": {"value": n / (e2e_ms / 1e3), "unit": "rows/s", "h2d_bytes_per_step": n * (2 + 4 * esz),
                         "d2h_bytes_per_step": 4 * G * esz, "ms_per_step": e2e_ms},
                 "gpu_launches": int(launches), "clocks": clocks.summary()})
@@ -722,6 +737,17 @@ def run_scalar(args, local_rank):
     ref = torch.empty((), dtype=torch.float64, device=dev)
     torch.sum(vals, dim=0, out=ref)
     base_ms = _time(lambda: torch.sum(vals, dim=0, out=ref), args.steps, stream)
+    # the unbuffered drop-in type (one value at a time per thread) on the same values
+    ub = R.State(1, args.L, torch.float64, device=dev)
+
+    def ub_step():
+        ub.reset()
+        ub.add_values_unbuffered(vals)
+
+    ub_step()
+    ub_ms = _time(ub_step, max(1, args.steps // 2), stream)
+    torch.cuda.synchronize()
+    same = torch.equal(ub.tensor, st.tensor)
     peaks = load_peaks()
     fused = prof.get("fused")
     roof = None
@@ -736,6 +762,8 @@ def run_scalar(args, local_rank):
     res.update({"hbm_gbs_algorithmic": n * 8 / (ms / 1e3) / 1e9, "roofline": roof, "kernels": prof,
                 "fp64_baseline": {"kind": "torch.sum float64", "ms_per_step": base_ms,
                                   "repro_over_fp64_time": ms / base_ms},
+                "unbuffered_dropin": {"ms_per_step": ub_ms, "over_buffered_time": ub_ms / ms,
+                                      "over_fp64_time": ub_ms / base_ms, "same_state_bytes": bool(same)},
                 "e2e": None, "gpu_launches": int(launches), "clocks": clocks.summary(), "tuned": tuned})
     return res
 

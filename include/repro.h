@@ -156,6 +156,27 @@ repro_status repro_groupby_sum_cols(const uint8_t* key1, const uint8_t* key2, in
 repro_status repro_sum(const void* values, int64_t n, repro_dtype dtype, int L, void* state, void* stream);
 
 /*
+ * The paper's unbuffered data type as a library routine (Sec. IV): the same
+ * SUM as repro_sum (same state bits), but every thread adds its rows one by
+ * one into its own repro_accum (include/repro_accum.cuh), and the CTAs merge
+ * their accumulators.  A comparison point for the cost of the naive type
+ * next to the buffered shared-memory tables.  state: num_groups = 1.
+ */
+repro_status repro_sum_unbuffered(const void* values, int64_t n, repro_dtype dtype, int L, void* state,
+                                  void* stream);
+
+/*
+ * DECIMAL baseline: SUM of int64 values (a fixed-point column as scaled
+ * integers, e.g. cents) per group into out[num_groups] (zeroed first),
+ * exact and order-independent by integer arithmetic (wraps around on
+ * int64 overflow).  Keys outside [0, num_groups) are skipped.  A comparison
+ * point: fixed-point types are the reproducible alternative the paper sets
+ * the floating-point method against (Sec. II, VI).
+ */
+repro_status groupby_sum_decimal64(const int32_t* keys, const int64_t* values, int64_t n, int64_t num_groups,
+                                   int64_t* out, void* stream);
+
+/*
  * repro_groupby_sum without any allocation.  The paper has no counterpart:
  * this is a deployment variant of repro_groupby_sum for callers that cannot
  * allocate device memory while they aggregate -- a host whose buffer

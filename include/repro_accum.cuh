@@ -1,0 +1,108 @@
+/*
+ * repro_accum.cuh -- the reproducible accumulator repro<T,L> as a drop-in
+ * device type (the paper's unbuffered data type, Sec. IV).
+ *
+ * A user kernel that sums with a `double` accumulator can sum with a
+ * repro_accum<double, L> instead: add() one value at a time, merge() two
+ * accumulators, value() the result.  Every add does the whole per-value work
+ * of Algorithm 2 on its own -- classify the value, raise the window when
+ * the value is above it (the level sums shift down, low levels drop), add
+ * its balanced digits to the exact level sums -- so the type costs several
+ * times a plain floating-point add (the paper measures the same "naive"
+ * slowdown on CPUs); the library's grouped kernels amortise that work over
+ * shared-memory tables instead.  Results are bit-identical to the library's
+ * (and to any order or split of the adds): the state is canonical.
+ *
+ * Layout of the value: window K (top level's grid index; -1 before the first
+ * finite nonzero value), flags (REPRO_FLAG_*), L exact 128-bit level sums,
+ * level j in units u(K - j) = 2^(g_min + (K - j) W).  store() writes it as a
+ * state record of include/repro.h (int32 K, uint32 flags, {lo, hi}[L]).
+ *
+ * Device-only; include with the library's device sources on the include
+ * path (-I include -I paper_1802_09883_gb300/csrc) and compile with
+ * -fmad=false like the library.
+ */
+#pragma once
+
+#include "repro.h"
+#include "repro_device.cuh"
+
+template <typename T, int L>
+struct repro_accum {
+    static_assert(L >= 1 && L <= 4, "L must be in 1..4");
+    int K;
+    unsigned flags;
+    __int128 bins[L];
+
+    __device__ __forceinline__ void init() {
+        K = -1;
+        flags = 0;
+#pragma unroll
+        for (int j = 0; j < L; ++j) bins[j] = 0;
+    }
+
+    // Move the window up to grid index k: level j takes the old level j - d.
+    __device__ __forceinline__ void raise(int k) {
+        const int d = k - K;
+#pragma unroll
+        for (int j = L - 1; j >= 0; --j) bins[j] = j - d >= 0 ? bins[j - d] : 0;
+        K = k;
+    }
+
+    __device__ __forceinline__ void add(T x) {
+        const rp::Split s = rp::split_value(x);
+        if (s.flag) {
+            flags |= s.flag;
+            return;
+        }
+        if (s.mant == 0) return;
+        if (s.kb > K) raise(s.kb);
+        long long top, mid, low;
+        rp::digits3<T>(s, top, mid, low);
+        const int j = K - s.kb;  // level of the value's top digit
+        if (j < L) bins[j] += top;
+        if (j + 1 < L && s.kb >= 1) bins[j + 1] += mid;
+        if (j + 2 < L && s.kb >= 2) bins[j + 2] += low;
+    }
+
+    __device__ __forceinline__ void merge(const repro_accum& o) {
+        flags |= o.flags;
+        if (o.K < 0) return;
+        if (o.K > K) raise(o.K);
+        const int d = K - o.K;
+#pragma unroll
+        for (int j = 0; j < L; ++j)
+            if (j - d >= 0) bins[j] += o.bins[j - d];
+    }
+
+    // Eq. (1): the level values rounded once each, folded from the lowest up.
+    __device__ __forceinline__ T value() const {
+        if ((flags & (REPRO_FLAG_NAN | REPRO_FLAG_RANGE)) ||
+            ((flags & REPRO_FLAG_POS_INF) && (flags & REPRO_FLAG_NEG_INF)))
+            return rp::quiet_nan<T>();
+        if (flags & REPRO_FLAG_POS_INF) return rp::inf_of<T>(false);
+        if (flags & REPRO_FLAG_NEG_INF) return rp::inf_of<T>(true);
+        T q = (T)0;
+        bool first = true;
+#pragma unroll
+        for (int j = L - 1; j >= 0; --j) {
+            if (K - j < 0) continue;
+            const __int128 t = bins[j];
+            const bool neg = t < 0;
+            const unsigned __int128 mag = neg ? (unsigned __int128)(-t) : (unsigned __int128)t;
+            const T v = rp::round_scaled<T>(neg, mag, rp::Traits<T>::GMIN + (K - j) * rp::Traits<T>::W);
+            q = first ? v : rp::t_add(q, v);
+            first = false;
+        }
+        return q;
+    }
+
+    // As a state record (8 + 16 L bytes, 8-byte aligned).
+    __device__ __forceinline__ void store(unsigned char* rec) const {
+        *reinterpret_cast<int*>(rec) = K;
+        *reinterpret_cast<unsigned*>(rec + 4) = flags;
+        long long* b = reinterpret_cast<long long*>(rec + 8);
+#pragma unroll
+        for (int j = 0; j < L; ++j) rp::bin_write(&b[2 * j], &b[2 * j + 1], bins[j]);
+    }
+};

@@ -106,6 +106,8 @@ def lib(build_if_stale: bool = True):
         L.repro_tune_clear.restype = None
         L.repro_batch_tune.argtypes = [vp, vp, ctypes.POINTER(ctypes.c_double)]
         L.repro_sum.argtypes = [vp, i64, i32, i32, vp, vp]
+        L.repro_sum_unbuffered.argtypes = [vp, i64, i32, i32, vp, vp]
+        L.groupby_sum_decimal64.argtypes = [vp, vp, i64, i64, vp, vp]
         L.repro_stats_state_bytes.argtypes = [i32, i32, i64]
         L.repro_stats_state_bytes.restype = ctypes.c_size_t
         L.repro_stats_init.argtypes = [vp, i32, i32, i64, vp]
@@ -120,7 +122,8 @@ def lib(build_if_stale: bool = True):
                      "repro_server_submit", "repro_server_poll", "repro_server_wait", "repro_server_release",
                      "repro_server_stats_get", "repro_server_destroy", "repro_tune_groupby", "repro_tune_save",
                      "repro_tune_load", "repro_batch_tune", "repro_stats_init", "repro_groupby_stats",
-                     "repro_stats_merge", "repro_stats_finalize", "repro_sum"):
+                     "repro_stats_merge", "repro_stats_finalize", "repro_sum", "repro_sum_unbuffered",
+                     "groupby_sum_decimal64"):
             getattr(L, name).restype = i32
         _lib = L
     return _lib
@@ -226,6 +229,18 @@ class State:
         values = values.contiguous()
         _check(lib().repro_sum(values.data_ptr(), values.numel(), self.code, self.L, self.tensor.data_ptr(),
                                _stream(self.device)), "repro_sum")
+        return self
+
+    def add_values_unbuffered(self, values: torch.Tensor):
+        """The same SUM as add_values through the per-row drop-in type."""
+        if self.G != 1:
+            raise ValueError("add_values_unbuffered needs a state with num_groups = 1")
+        _require_cuda(values, "values")
+        if values.dtype != self.dtype:
+            raise ValueError("values must have the state's dtype")
+        values = values.contiguous()
+        _check(lib().repro_sum_unbuffered(values.data_ptr(), values.numel(), self.code, self.L,
+                                          self.tensor.data_ptr(), _stream(self.device)), "repro_sum_unbuffered")
         return self
 
     def error_word(self) -> int:
@@ -535,3 +550,18 @@ def scalar_sum(values: torch.Tensor, L: int = 3) -> torch.Tensor:
     out = st.finalize()
     st.check()
     return out[0]
+
+
+def groupby_sum_decimal64(keys: torch.Tensor, values: torch.Tensor, num_groups: int,
+                          out: Optional[torch.Tensor] = None) -> torch.Tensor:
+    """DECIMAL baseline: exact int64 SUM per group of scaled-integer values."""
+    _require_cuda(keys, "keys")
+    _require_cuda(values, "values")
+    if values.dtype != torch.int64 or keys.dtype != torch.int32:
+        raise ValueError("keys int32, values int64")
+    keys, values = keys.contiguous(), values.contiguous()
+    if out is None:
+        out = torch.empty(num_groups, dtype=torch.int64, device=values.device)
+    _check(lib().groupby_sum_decimal64(keys.data_ptr(), values.data_ptr(), keys.numel(), num_groups, out.data_ptr(),
+                                       _stream(values.device)), "groupby_sum_decimal64")
+    return out

@@ -485,6 +485,23 @@ cudaError_t launch_groupby_fused(const int32_t* keys, const void* vals, long lon
     return cudaGetLastError();
 }
 
+cudaError_t launch_merge_partials(const void* parts, int C, long long G, void* state, int dtype, int L,
+                                  cudaStream_t s) {
+    const int blocks = (int)((G + 31) / 32);
+    const unsigned char* p = (const unsigned char*)parts;
+    unsigned char* st = (unsigned char*)state;
+    prof_begin(PROF_MERGE, s);
+    switch (L) {
+        case 1: k_merge_partials<1><<<blocks, 256, 0, s>>>(p, C, (int)G, st, dtype); break;
+        case 2: k_merge_partials<2><<<blocks, 256, 0, s>>>(p, C, (int)G, st, dtype); break;
+        case 3: k_merge_partials<3><<<blocks, 256, 0, s>>>(p, C, (int)G, st, dtype); break;
+        default: k_merge_partials<4><<<blocks, 256, 0, s>>>(p, C, (int)G, st, dtype); break;
+    }
+    prof_end(PROF_MERGE, s);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
 }  // namespace rp
 
 // ------------------------------------------- entry point without allocation

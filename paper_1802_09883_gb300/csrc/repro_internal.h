@@ -123,6 +123,9 @@ cudaError_t launch_merge_items(int L, int dtype, const void* tasks, const void* 
                                const void* partials, cudaStream_t s);
 
 cudaError_t launch_merge(void* dst, const void* src, int dtype, int L, long long G, cudaStream_t s);
+// state += C partial record arrays of G records each (parts[c * G + g]).
+cudaError_t launch_merge_partials(const void* parts, int C, long long G, void* state, int dtype, int L,
+                                  cudaStream_t s);
 cudaError_t launch_finalize(const void* state, int dtype, int L, long long G, void* out, cudaStream_t s);
 
 cudaError_t launch_groupby_fp64(const int32_t* keys, const double* vals, long long n, long long G, double* out,
