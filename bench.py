@@ -227,14 +227,10 @@ def run_ours(args, rank, world, local_rank):
         keys_h.copy_(w.keys)
         vals_h.copy_(w.values)
         out_h = torch.empty(G, dtype=torch.float64, pin_memory=True)
-        kd = torch.empty_like(w.keys)
-        vd = torch.empty_like(w.values)
 
-        def e2e_step():
-            kd.copy_(keys_h, non_blocking=True)
-            vd.copy_(vals_h, non_blocking=True)
+        def e2e_step():  # host columns in, result to host: copies overlapped with the aggregation
             st.reset()
-            st.add(kd, vd)
+            st.add_host(keys_h, vals_h)
             st.finalize(out)
             out_h.copy_(out, non_blocking=True)
 

@@ -131,6 +131,19 @@ repro_status repro_groupby_sum(const int32_t* keys, const void* values, int64_t 
                                void* stream);
 
 /*
+ * repro_groupby_sum on columns in page-locked HOST memory (cudaHostAlloc /
+ * pinned tensors; anything else is REPRO_EINVAL): the rows are staged in
+ * chunks of 2^24 through two device buffers from the library's pool, copied
+ * on a library-owned stream, each chunk aggregated on `stream` behind its
+ * copy while the next one is in flight (chunks merge exactly, so the state
+ * is that of one call on the whole input).  Asynchronous: the host columns
+ * must stay unchanged until `stream` has passed this call.  Not for stream
+ * capture (the copy stream is shared by all callers on a device).
+ */
+repro_status repro_groupby_sum_host(const int32_t* keys, const void* values, int64_t n, repro_dtype dtype, int L,
+                                    int64_t num_groups, void* state, void* stream);
+
+/*
  * Several SUM aggregates over one grouping given as two low-cardinality
  * uint8 key columns (SQL: SELECT SUM(c0), SUM(c1), ... GROUP BY k1, k2, the
  * shape of the paper's TPC-H Q1 aggregation, Sec. VI-E): the group of row i

@@ -106,6 +106,7 @@ def lib(build_if_stale: bool = True):
         L.repro_tune_clear.restype = None
         L.repro_batch_tune.argtypes = [vp, vp, ctypes.POINTER(ctypes.c_double)]
         L.repro_sum.argtypes = [vp, i64, i32, i32, vp, vp]
+        L.repro_groupby_sum_host.argtypes = [vp, vp, i64, i32, i32, i64, vp, vp]
         L.repro_sum_unbuffered.argtypes = [vp, i64, i32, i32, vp, vp]
         L.groupby_sum_decimal64.argtypes = [vp, vp, i64, i64, vp, vp]
         L.repro_stats_state_bytes.argtypes = [i32, i32, i64]
@@ -123,6 +124,7 @@ def lib(build_if_stale: bool = True):
                      "repro_server_stats_get", "repro_server_destroy", "repro_tune_groupby", "repro_tune_save",
                      "repro_tune_load", "repro_batch_tune", "repro_stats_init", "repro_groupby_stats",
                      "repro_stats_merge", "repro_stats_finalize", "repro_sum", "repro_sum_unbuffered",
+                     "repro_groupby_sum_host",
                      "groupby_sum_decimal64"):
             getattr(L, name).restype = i32
         _lib = L
@@ -229,6 +231,20 @@ class State:
         values = values.contiguous()
         _check(lib().repro_sum(values.data_ptr(), values.numel(), self.code, self.L, self.tensor.data_ptr(),
                                _stream(self.device)), "repro_sum")
+        return self
+
+    def add_host(self, keys: torch.Tensor, values: torch.Tensor):
+        """Accumulate pinned host columns: chunked copies overlapped with the
+        aggregation (the tensors must stay unchanged until the current
+        stream has passed this call)."""
+        if keys.is_cuda or values.is_cuda or not keys.is_pinned() or not values.is_pinned():
+            raise ValueError("keys and values must be pinned host tensors")
+        if keys.dtype != torch.int32 or values.dtype != self.dtype or keys.numel() != values.numel():
+            raise ValueError("keys int32 and values of the state's dtype, same length")
+        keys, values = keys.contiguous(), values.contiguous()
+        _check(lib().repro_groupby_sum_host(keys.data_ptr(), values.data_ptr(), keys.numel(), self.code, self.L,
+                                            self.G, self.tensor.data_ptr(), _stream(self.device)),
+               "repro_groupby_sum_host")
         return self
 
     def add_values_unbuffered(self, values: torch.Tensor):

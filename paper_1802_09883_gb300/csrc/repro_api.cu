@@ -5,6 +5,7 @@
 // enqueues the kernels of repro_kernels.cu on the caller's stream.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstdint>
 #include <map>
 #include <mutex>
@@ -131,6 +132,21 @@ using namespace rp;
 
 namespace rp {
 
+// Rows per staged chunk of repro_groupby_sum_host (two chunks in flight).
+constexpr long long kHostChunkRows = 1ll << 24;
+
+// A library stream per device for host-to-device copies.
+static cudaStream_t copy_stream(cudaError_t& err) {
+    static cudaStream_t streams[64] = {};
+    static std::mutex mu;
+    int dev = 0;
+    err = cudaGetDevice(&dev);
+    if (err != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+    std::lock_guard<std::mutex> lock(mu);
+    if (!streams[dev]) err = cudaStreamCreateWithFlags(&streams[dev], cudaStreamNonBlocking);
+    return err == cudaSuccess ? streams[dev] : nullptr;
+}
+
 int groupby_dispatch(const int32_t* keys, const void* values, long long n, int dtype, int L, long long num_groups,
                      void* state, cudaStream_t s) {
     // each path's configuration is chosen once and passed on, so the scratch
@@ -223,6 +239,61 @@ repro_status repro_sum(const void* values, int64_t n, repro_dtype dtype, int L, 
     cudaError_t e = cudaMemsetAsync(keys.p, 0, 4 * (size_t)n, s);
     if (e != cudaSuccess) return from_cuda(e);
     return (repro_status)groupby_dispatch((const int32_t*)keys.p, values, n, dtype, L, 1, state, s);
+}
+
+repro_status repro_groupby_sum_host(const int32_t* keys, const void* values, int64_t n, repro_dtype dtype, int L,
+                                    int64_t num_groups, void* state, void* stream) {
+    if (!state || (uintptr_t)state % 16 || n < 0 || !valid_dtype(dtype) || !valid_shape(L, num_groups))
+        return REPRO_EINVAL;
+    if (n == 0) return REPRO_OK;
+    if (!keys || !values) return REPRO_EINVAL;
+    for (const void* p : {(const void*)keys, values}) {  // page-locked host memory only: copies stay asynchronous
+        cudaPointerAttributes a{};
+        if (cudaPointerGetAttributes(&a, p) != cudaSuccess || a.type != cudaMemoryTypeHost) {
+            cudaGetLastError();
+            return REPRO_EINVAL;
+        }
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t vs = dtype == REPRO_F64 ? 8 : 4;
+    const long long chunk = std::min<long long>(n, kHostChunkRows);
+    cudaError_t e = cudaSuccess;
+    cudaStream_t cs = copy_stream(e);
+    if (!cs) return from_cuda(e);
+    // two staging buffers (keys then values, 16-byte aligned) in stream order on s
+    const size_t kbytes = ((size_t)chunk * 4 + 255) & ~(size_t)255;
+    Scratch buf0(kbytes + (size_t)chunk * vs, s), buf1(kbytes + (size_t)chunk * vs, s);
+    if (buf0.err != cudaSuccess) return from_cuda(buf0.err);
+    if (buf1.err != cudaSuccess) return from_cuda(buf1.err);
+    unsigned char* buf[2] = {(unsigned char*)buf0.p, (unsigned char*)buf1.p};
+    cudaEvent_t ready[2] = {nullptr, nullptr}, freed[2] = {nullptr, nullptr};
+    for (int i = 0; i < 2 && e == cudaSuccess; ++i) {
+        e = cudaEventCreateWithFlags(&ready[i], cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&freed[i], cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventRecord(freed[i], s);  // the buffers exist from here on s
+    }
+    repro_status st = from_cuda(e);
+    for (long long r0 = 0, i = 0; st == REPRO_OK && r0 < n; r0 += chunk, ++i) {
+        const int b = (int)(i & 1);
+        const long long rows = std::min<long long>(chunk, n - r0);
+        e = cudaStreamWaitEvent(cs, freed[b], 0);  // the chunk two back has been aggregated
+        if (e == cudaSuccess) e = cudaMemcpyAsync(buf[b], keys + r0, (size_t)rows * 4, cudaMemcpyHostToDevice, cs);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(buf[b] + kbytes, (const unsigned char*)values + (size_t)r0 * vs, (size_t)rows * vs,
+                                cudaMemcpyHostToDevice, cs);
+        if (e == cudaSuccess) e = cudaEventRecord(ready[b], cs);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(s, ready[b], 0);
+        st = from_cuda(e);
+        if (st == REPRO_OK)
+            st = (repro_status)groupby_dispatch((const int32_t*)buf[b], buf[b] + kbytes, rows, dtype, L, num_groups,
+                                                state, s);
+        if (st == REPRO_OK) st = from_cuda(cudaEventRecord(freed[b], s));
+    }
+    for (int i = 0; i < 2; ++i) {
+        if (ready[i]) cudaEventDestroy(ready[i]);
+        if (freed[i]) cudaEventDestroy(freed[i]);
+    }
+    return st;  // the staging buffers return to the pool in stream order on s
 }
 
 repro_status repro_merge(void* dst, const void* src, repro_dtype dtype, int L, int64_t num_groups, void* stream) {

@@ -53,3 +53,19 @@ def test_scalar_sum_specials_and_empty():
     st = R.State(4, 3)  # not a one-group state: refused on the host
     with pytest.raises(ValueError):
         st.add_values(v)
+
+
+def test_host_columns_match_device_columns():
+    g = torch.Generator(device=DEV)
+    g.manual_seed(23)
+    n, G = (1 << 25) + 12345, 1000  # three staged chunks, the last ragged
+    keys = WL.uniform_keys(n, G, g, DEV)
+    vals = WL.random_values(n, -40, 40, g, DEV)
+    dev_state = R.State(G, 3)
+    dev_state.add(keys, vals)
+    kh, vh = keys.cpu().pin_memory(), vals.cpu().pin_memory()
+    host_state = R.State(G, 3).add_host(kh, vh)
+    torch.cuda.synchronize()
+    assert torch.equal(dev_state.tensor, host_state.tensor)
+    with pytest.raises(ValueError):  # pageable host memory
+        R.State(G, 3).add_host(keys.cpu(), vals.cpu())
