@@ -81,6 +81,15 @@ size_t partitioned_scratch_bytes(const PartChoice& pc, int dtype, int L, long lo
 cudaError_t launch_groupby_partitioned(const int32_t* keys, const void* vals, long long n, int dtype, int L,
                                        long long G, const PartChoice& pc, void* state, void* scratch, cudaStream_t s);
 
+// Several value columns over one key column in one pass (repro_cols.cu):
+// four columns (NV = 4), or one column and its square (NV = 2, square:
+// vals[0] only, two states).  Supported only where the tables leave three
+// CTAs per SM.
+bool cols_supported(int dtype, int L, long long G, int NV, const int32_t* keys, const void* const* vals);
+size_t cols_scratch_bytes(int dtype, int L, long long G, int NV, long long n);
+cudaError_t launch_groupby_cols(const int32_t* keys, const void* const* vals, int NV, bool square, long long n,
+                                int dtype, int L, long long G, void* const* states, void* scratch, cudaStream_t s);
+
 // Many inputs partitioned in one pass and aggregated by one multi-task
 // launch (a batch's large-group tasks; repro_partition.cu).  plan() builds
 // the chunk list and tables on the host (false if the inputs do not qualify:

@@ -5,14 +5,17 @@
 // made reproducible: COUNT needs no floating point, AVG / VARIANCE / STDDEV
 // are functions of SUM(x) and SUM(x^2) (Sec. I).  A stats state is
 //   [repro state of x][repro state of x*x][uint64 count[G]]
-// (each part 16-byte aligned).  k_square_count reads every row once, writes
-// x*x (rounded to nearest in T) to scratch and counts rows per group (exact
-// integers, so atomics in any order agree); the two SUMs go through the
-// regular dispatcher.  k_stats_finalize evaluates the aggregates per group
-// in a fixed order of IEEE operations, so they are as reproducible as the
-// sums they read.
+// (each part 16-byte aligned).  When the group table fits the single-pass
+// layout, the two SUMs run in one pass of the two-column kernel
+// (repro_cols.cu; each x*x rounded to nearest in T, formed in shared
+// memory) and k_count counts rows per group (exact integers, so atomics in
+// any order agree).  Otherwise k_square_count writes x*x to scratch and
+// counts, and the two SUMs go through the regular dispatcher.
+// k_stats_finalize evaluates the aggregates per group in a fixed order of
+// IEEE operations, so they are as reproducible as the sums they read.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdint>
 
@@ -51,6 +54,32 @@ __global__ void __launch_bounds__(256) k_square_count(const int32_t* __restrict_
          i += (long long)gridDim.x * blockDim.x) {
         const T x = vals[i];
         sq[i] = x * x;  // one rounding to nearest (no contraction: built with -fmad=false)
+        const int g = keys[i];
+        if ((unsigned)g < (unsigned)G) {
+            if (smem)
+                atomicAdd(&s_cnt[g], 1u);
+            else
+                atomicAdd(&count[g], 1ull);
+        }
+    }
+    if (smem) {
+        __syncthreads();
+        for (int g = threadIdx.x; g < G; g += blockDim.x)
+            if (s_cnt[g]) atomicAdd(&count[g], (unsigned long long)s_cnt[g]);
+    }
+}
+
+// Rows per group only (the sums run in the two-column single pass).
+__global__ void __launch_bounds__(256) k_count(const int32_t* __restrict__ keys, long long n, int G,
+                                               unsigned long long* __restrict__ count) {
+    __shared__ unsigned s_cnt[kCountSmemGroups];
+    const bool smem = G <= kCountSmemGroups;
+    if (smem) {
+        for (int g = threadIdx.x; g < G; g += blockDim.x) s_cnt[g] = 0;
+        __syncthreads();
+    }
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
         const int g = keys[i];
         if ((unsigned)g < (unsigned)G) {
             if (smem)
@@ -156,6 +185,24 @@ repro_status repro_groupby_stats(const int32_t* keys, const void* values, int64_
     unsigned char* b = (unsigned char*)state;
     const size_t vs = dtype == REPRO_F64 ? 8 : 4;
     cudaError_t err = cudaSuccess;
+    unsigned long long* counts = reinterpret_cast<unsigned long long*>(b + ly.count);
+    const void* xv[2] = {values, values};
+    if (cols_supported(dtype, L, num_groups, 2, keys, xv)) {
+        // one pass for the sums of x and x*x (squares formed in shared memory), one for the counts
+        cudaMemPool_t pool0 = library_pool(err);
+        if (!pool0) return from_cuda(err);
+        void* part = nullptr;
+        err = cudaMallocFromPoolAsync(&part, std::max<size_t>(16, cols_scratch_bytes(dtype, L, num_groups, 2, n)),
+                                      pool0, s);
+        if (err != cudaSuccess) return from_cuda(err);
+        void* states[2] = {b, b + ly.sq};
+        err = launch_groupby_cols(keys, xv, 2, true, n, dtype, L, num_groups, states, part, s);
+        cudaFreeAsync(part, s);
+        if (err != cudaSuccess) return from_cuda(err);
+        k_count<<<device_info().sms * 8, 256, 0, s>>>(keys, n, (int)num_groups, counts);
+        count_launches(1);
+        return from_cuda(cudaGetLastError());
+    }
     cudaMemPool_t pool = library_pool(err);
     if (!pool) return from_cuda(err);
     void* sq = nullptr;

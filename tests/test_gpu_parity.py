@@ -379,3 +379,29 @@ def test_multicolumn_bad_composite_keys_flag_every_state():
         with pytest.raises(R.ReproError):
             st.check()
         assert _np(st.finalize()).tolist() == [4.0, 1.0, 0.0, 2.0]
+
+
+@pytest.mark.parametrize("ncols,G,n,dtype", [(3, 4, 1_000_003, torch.float64), (5, 16, 777_777, torch.float32),
+                                             (4, 3000, 500_001, torch.float64)])
+def test_multicolumn_groups_of_columns_equal_one_pass_per_column(ncols, G, n, dtype):
+    g = torch.Generator(device=DEV)
+    g.manual_seed(ncols * G)
+    card2 = 64 if G > 256 else 2
+    k1 = torch.randint(0, (G + card2 - 1) // card2, (n,), generator=g, device=DEV, dtype=torch.uint8)
+    k2 = torch.randint(0, card2, (n,), generator=g, device=DEV, dtype=torch.uint8)
+    cols = [WL.random_values(n, -50, 50, g, DEV, dtype) for _ in range(ncols)]
+    states = R.groupby_sum_cols(k1, k2, card2, cols, num_groups=G, L=3)
+    gid = k1.to(torch.int32) * card2 + k2.to(torch.int32)
+    ok = gid < G
+    for c, st in zip(cols, states):
+        ref = R.State(G, 3, dtype)
+        ref.add(torch.where(ok, gid, torch.zeros_like(gid))[ok], c[ok])
+        torch.cuda.synchronize()
+        if bool(ok.all()):
+            assert st.check() == 0
+        else:  # composite keys past num_groups were skipped and flagged
+            with pytest.raises(R.ReproError):
+                st.check()
+        K, fl, lo, hi = st.host_view()
+        rK, rfl, rlo, rhi = ref.host_view()
+        assert np.array_equal(K, rK) and np.array_equal(fl, rfl) and np.array_equal(lo, rlo) and np.array_equal(hi, rhi)
