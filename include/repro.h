@@ -375,8 +375,10 @@ repro_status repro_stats_finalize(const void* state, repro_dtype dtype, int L, i
  * device memory (state plus scratch, estimated at submit) fits the budget and
  * a slot is free.  It then runs iterations: each iteration takes the next
  * chunk_rows rows of every admitted query; chunks whose group table fits the
- * single-pass kernel go into one multi-task persistent launch, the others
- * through the partitioned path on one of four more streams.  Partial states stay on
+ * single-pass kernel go into one multi-task persistent launch; the chunks of
+ * queries that need partitioning go into one batched partition pass on a
+ * second stream (aligned columns, up to 2^19 groups) or, otherwise, through
+ * the partitioned path on one of three more streams.  Partial states stay on
  * the device between iterations.  After its last chunk a query is finalized
  * into its output and its state freed; a host callback stamps the completion
  * time.  At most max_inflight iterations are queued ahead of the device.

@@ -111,7 +111,12 @@ struct BatchPartition {
     BatchPartition& operator=(const BatchPartition&) = delete;
     bool plan(int dtype, int L, const std::vector<BatchPartInput>& in);
     size_t scratch_bytes() const;
+    // the host-built tables are the scratch's first table_bytes() bytes
+    size_t table_bytes() const;
+    void pack_tables(void* host) const;
     cudaError_t upload(void* scratch) const;
+    // pack into page-locked `pinned` (table_bytes() long, alive until the copy ran) and copy on s
+    cudaError_t upload_async(void* scratch, void* pinned, cudaStream_t s) const;
     cudaError_t launch(void* scratch, cudaStream_t s) const;
 };
 

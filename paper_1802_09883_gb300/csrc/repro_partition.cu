@@ -29,6 +29,7 @@
 
 #include <algorithm>
 #include <cstdint>
+#include <cstring>
 #include <vector>
 
 #include "multi_types.h"
@@ -884,8 +885,9 @@ namespace {
 constexpr long long kBatchBuckets = 128;  // partitions per task of a batched pass
 
 struct BatchLayout {
-    size_t okeys, ovals, chunks, segs, ptask, cbase, nunits, counts, offsets, ptot, pstart, pcount;
-    size_t tasks, items, blks, parts, ints, total;
+    size_t chunks, segs, ptask, cbase, nunits, ints, tables;  // host-built tables: bytes [0, tables)
+    size_t okeys, ovals, counts, offsets, ptot, pstart, pcount;
+    size_t tasks, items, blks, parts, total;
 };
 
 }  // namespace
@@ -961,13 +963,16 @@ bool BatchPartition::plan(int dtype, int L, const std::vector<BatchPartInput>& i
         at = o;
         o = align256(o + bytes);
     };
-    take(ly.okeys, (size_t)P.rows_out * 4);
-    take(ly.ovals, (size_t)P.rows_out * vs);
+    // the host-built tables first (one contiguous image, see pack_tables)
     take(ly.chunks, nch * sizeof(PartChunk));
     take(ly.segs, (size_t)P.T * sizeof(PartSeg));
     take(ly.ptask, (size_t)P.T * sizeof(PartTask));
     take(ly.cbase, (size_t)P.T * 4);
     take(ly.nunits, (size_t)P.T * 4);
+    take(ly.ints, 8 * sizeof(int));
+    ly.tables = o;
+    take(ly.okeys, (size_t)P.rows_out * 4);
+    take(ly.ovals, (size_t)P.rows_out * vs);
     take(ly.counts, nch * (size_t)P.B * 4);
     take(ly.offsets, nch * (size_t)P.B * 4);
     take(ly.ptot, (size_t)P.F * 8);
@@ -977,28 +982,36 @@ bool BatchPartition::plan(int dtype, int L, const std::vector<BatchPartInput>& i
     take(ly.items, (size_t)P.max_items * sizeof(MItem));
     take(ly.blks, (size_t)std::max(1ll, P.max_blks) * sizeof(MergeBlk));
     take(ly.parts, (size_t)P.max_part_recs * (8 + 16 * (size_t)L));
-    take(ly.ints, 8 * sizeof(int));
     ly.total = o;
     return true;
 }
 
 size_t BatchPartition::scratch_bytes() const { return impl->ly.total; }
 
-cudaError_t BatchPartition::upload(void* scratch) const {
+size_t BatchPartition::table_bytes() const { return impl->ly.tables; }
+
+void BatchPartition::pack_tables(void* host) const {
     const Impl& P = *impl;
-    unsigned char* b = (unsigned char*)scratch;
+    unsigned char* b = (unsigned char*)host;
+    std::memset(b, 0, P.ly.tables);
+    std::memcpy(b + P.ly.chunks, P.chunks.data(), P.chunks.size() * sizeof(PartChunk));
+    std::memcpy(b + P.ly.segs, P.segs.data(), P.segs.size() * sizeof(PartSeg));
+    std::memcpy(b + P.ly.ptask, P.ptask.data(), P.ptask.size() * sizeof(PartTask));
+    std::memcpy(b + P.ly.cbase, P.cbase.data(), P.cbase.size() * 4);
+    std::memcpy(b + P.ly.nunits, P.nunits.data(), P.nunits.size() * 4);
     const int nch = (int)P.chunks.size();
-    cudaError_t e = cudaMemcpy(b + P.ly.chunks, P.chunks.data(), P.chunks.size() * sizeof(PartChunk),
-                               cudaMemcpyHostToDevice);
-    if (e == cudaSuccess)
-        e = cudaMemcpy(b + P.ly.segs, P.segs.data(), P.segs.size() * sizeof(PartSeg), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess)
-        e = cudaMemcpy(b + P.ly.ptask, P.ptask.data(), P.ptask.size() * sizeof(PartTask), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemcpy(b + P.ly.cbase, P.cbase.data(), P.cbase.size() * 4, cudaMemcpyHostToDevice);
-    if (e == cudaSuccess)
-        e = cudaMemcpy(b + P.ly.nunits, P.nunits.data(), P.nunits.size() * 4, cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemcpy(b + P.ly.ints + 4 * sizeof(int), &nch, sizeof(int), cudaMemcpyHostToDevice);
-    return e;
+    std::memcpy(b + P.ly.ints + 4 * sizeof(int), &nch, sizeof(int));
+}
+
+cudaError_t BatchPartition::upload(void* scratch) const {
+    std::vector<unsigned char> img(impl->ly.tables);
+    pack_tables(img.data());
+    return cudaMemcpy(scratch, img.data(), img.size(), cudaMemcpyHostToDevice);
+}
+
+cudaError_t BatchPartition::upload_async(void* scratch, void* pinned, cudaStream_t s) const {
+    pack_tables(pinned);
+    return cudaMemcpyAsync(scratch, pinned, impl->ly.tables, cudaMemcpyHostToDevice, s);
 }
 
 cudaError_t BatchPartition::launch(void* scratch, cudaStream_t s) const {

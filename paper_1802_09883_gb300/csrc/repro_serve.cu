@@ -8,9 +8,11 @@
 //      the library pool, initialised in stream order);
 //   2. takes the next chunk of every admitted query: chunks of single-pass
 //      queries (table fits shared memory) become the tasks of one multi-task
-//      persistent launch per (dtype, L) on the batch stream; the other
-//      queries run their chunk through the partitioned path on one of four
-//      more streams (fixed per query, the least loaded at admission);
+//      persistent launch per (dtype, L) on the batch stream; the chunks of
+//      queries that need partitioning join one batched partition pass on a
+//      second stream (aligned columns, up to 2^19 groups) or, otherwise, run
+//      the partitioned path on one of three more streams (fixed per query,
+//      the least loaded at admission);
 //   3. finalizes queries that received their last chunk, copies each state's
 //      error word to a pinned slot, frees the state in stream order and
 //      enqueues a host callback that stamps the completion time and returns
@@ -63,9 +65,12 @@ size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 // allows (the planner makes items longer otherwise).
 constexpr size_t kServePartBytes = 256ull << 20;
 
-// Stream 0 runs the batched launches; streams 1 .. kLanes-1 run the queries
-// whose tables need the partitioned path, each query on one of them.
+// Stream 0 runs the batched single-pass launches; stream 1 the batched
+// partition pass of the queries whose tables need partitioning (aligned
+// columns, at most kPartLaneGroups groups); streams 2 .. kLanes-1 run the
+// remaining large queries, each query on one of them.
 constexpr int kLanes = 5;
+constexpr long long kPartLaneGroups = 1 << 19;
 
 struct Req {
     uint64_t id = 0;
@@ -81,8 +86,9 @@ struct Req {
     repro_status status = REPRO_OK;
     uint32_t errors = 0;
     long long pos = 0;   // rows issued so far
-    int lane = 0;        // 0: batch stream, else a partitioned-path stream
+    int lane = 0;        // 0: batch stream, 1: batched partition pass, else a partitioned-path stream
     bool large = false;  // needs the partitioned path
+    bool part_lane = false;  // its chunks join the batched partition pass
     void* state = nullptr;
     size_t need = 0;     // bytes charged to the budget while admitted
     int slot = -1;       // pinned error-word slot
@@ -240,15 +246,51 @@ struct Server {
         return e;
     }
 
+    // The batched partition pass over this iteration's chunks of the
+    // partition-lane queries: tables from a pinned arena, scratch from the
+    // pool in stream order, all on stream 1.  If the chunks do not qualify
+    // as one pass (they always should), each runs the dispatcher instead.
+    cudaError_t launch_part(int dtype, int L, const std::vector<BatchPartInput>& in, Iter& it) {
+        BatchPartition bp;
+        cudaStream_t s = stream[1];
+        if (!bp.plan(dtype, L, in)) {
+            for (const BatchPartInput& x : in)
+                if (groupby_dispatch(x.keys, x.vals, x.n, dtype, L, x.G, x.state, s) != REPRO_OK)
+                    return cudaErrorUnknown;
+            return cudaSuccess;
+        }
+        Arena* a = take_arena();
+        it.arenas.push_back(a);
+        cudaError_t e = cudaSuccess;
+        if (a->host_cap < bp.table_bytes()) {
+            if (a->host) cudaFreeHost(a->host);
+            a->host = nullptr;
+            a->host_cap = std::max(bp.table_bytes(), (size_t)256 << 10);
+            e = cudaHostAlloc((void**)&a->host, a->host_cap, cudaHostAllocDefault);
+            if (e != cudaSuccess) {
+                a->host_cap = 0;
+                return e;
+            }
+        }
+        void* scratch = nullptr;
+        e = cudaMallocFromPoolAsync(&scratch, bp.scratch_bytes(), pool, s);
+        if (e == cudaSuccess) e = bp.upload_async(scratch, a->host, s);
+        if (e == cudaSuccess) e = bp.launch(scratch, s);
+        if (scratch) cudaFreeAsync(scratch, s);
+        return e;
+    }
+
     // One iteration over the admitted queries; false after a launch error.
     bool issue(std::vector<Req*>& admitted_now) {
         cudaError_t e = cudaSuccess;
         for (Req* r : admitted_now) {
-            if (r->large) {  // the partitioned lane with the fewest rows left to issue
+            if (r->part_lane) {
+                r->lane = 1;
+            } else if (r->large) {  // the partitioned lane with the fewest rows left to issue
                 long long left[kLanes] = {};
                 for (Req* q : active) left[q->lane] += q->n - q->pos;
-                r->lane = 1;
-                for (int l = 2; l < kLanes; ++l)
+                r->lane = 2;
+                for (int l = 3; l < kLanes; ++l)
                     if (left[l] < left[r->lane]) r->lane = l;
             }
             cudaStream_t s = stream[r->lane];
@@ -265,6 +307,7 @@ struct Server {
         inflight.emplace_back();
         Iter& it = inflight.back();
         std::map<std::pair<int, int>, std::vector<repro_task>> batches;
+        std::map<std::pair<int, int>, std::vector<BatchPartInput>> parts;
         std::vector<Req*> fin[kLanes], keep;
         long long large_calls = 0;
         for (Req* r : active) {
@@ -274,6 +317,9 @@ struct Server {
                 const void* v = (const char*)r->vals + (size_t)r->pos * (r->dtype == REPRO_F64 ? 8 : 4);
                 if (r->lane == 0) {
                     batches[{r->dtype, r->L}].push_back(repro_task{k, v, rows, r->G, r->state});
+                } else if (r->lane == 1) {
+                    parts[{r->dtype, r->L}].push_back(
+                        BatchPartInput{k, v, rows, (int)r->G, (unsigned char*)r->state});
                 } else {
                     const int st_ = groupby_dispatch(k, v, rows, r->dtype, r->L, r->G, r->state, stream[r->lane]);
                     if (st_ != REPRO_OK) {
@@ -298,6 +344,10 @@ struct Server {
         for (auto& b : batches) {
             if (launch_batch(b.first.first, b.first.second, b.second, it) != cudaSuccess) return give_back(0);
             ++launches;
+        }
+        for (auto& b : parts) {
+            if (launch_part(b.first.first, b.first.second, b.second, it) != cudaSuccess) return give_back(0);
+            ++large_calls;
         }
         for (int l = 0; l < kLanes; ++l) {
             if (fin[l].empty()) continue;
@@ -509,6 +559,8 @@ repro_status repro_server_submit(repro_server srv, const int32_t* keys, const vo
     r->ready = (cudaEvent_t)ready_event;
     r->arrival_ns = arrival_ns > 0 ? arrival_ns : now_ns();
     r->large = !(n == 0 || fused_supported(dtype, L, num_groups, keys, values));
+    r->part_lane = r->large && num_groups <= kPartLaneGroups && (uintptr_t)keys % 16 == 0 &&
+                   (uintptr_t)values % 16 == 0;
     r->need = repro_state_bytes(dtype, L, num_groups);
     if (r->large) {
         const long long rows = std::min<long long>(n, S.cfg.chunk_rows);
