@@ -551,10 +551,15 @@ repro_status plan_batch_host(const repro_task* tasks, int ntasks, int dtype, int
 __global__ void k_batch_init(const MTask* __restrict__ tasks, int task0, int dtype, int L) {
     const MTask t = tasks[task0 + blockIdx.y];
     const StateView st{t.hdr, L, t.G_hdr};
-    if (blockIdx.x == 0 && threadIdx.x == 0) state_init_header(st, dtype);
-    for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < t.G_hdr;
-         g += (long long)gridDim.x * blockDim.x)
-        state_init_group(st, g);
+    const long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (tid == 0) state_init_header(st, dtype);
+    // all-zero records, cleared as one flat range (states are 16-byte aligned)
+    const unsigned long long bytes = (unsigned long long)t.G_hdr * (8ull + 16ull * (unsigned long long)L);
+    uint4* rec = reinterpret_cast<uint4*>(t.hdr + sizeof(repro_state_header));
+    for (long long i = tid; i < (long long)(bytes / 16); i += (long long)gridDim.x * blockDim.x)
+        rec[i] = make_uint4(0, 0, 0, 0);
+    if (tid == 0 && (bytes & 15))
+        *reinterpret_cast<unsigned long long*>(t.hdr + sizeof(repro_state_header) + bytes - 8) = 0ull;
 }
 
 // One launch finalizes every task with an output (eq. (1) per group).

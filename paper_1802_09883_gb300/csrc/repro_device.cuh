@@ -459,15 +459,6 @@ __device__ __forceinline__ void state_init_header(const StateView& st, int dtype
     for (int i = 0; i < 40; ++i) h->reserved[i] = 0;
 }
 
-__device__ __forceinline__ void state_init_group(const StateView& st, long long g) {
-    *st.K(g) = 0;
-    *st.flags(g) = 0;
-    for (int j = 0; j < st.L; ++j) {
-        *st.lo(g, j) = 0;
-        *st.hi(g, j) = 0;
-    }
-}
-
 // The result of one group (eq. (1)): the special values first, else
 // V_j = RN(T_j u_j) folded from the lowest level up, left-associative.
 template <typename T>

@@ -122,12 +122,14 @@ struct BatchPartition {
 
 // Measured choices (repro_tune.cu).  The cache holds, per (dtype, L, group
 // count rounded up to a power of two), a single-pass configuration and a
-// partition width; the tuner forces candidates on its own thread while it
-// times them.
+// partition width with its number of partition passes (levels: 1 or 2, 0 =
+// the rule's); the tuner forces candidates on its own thread while it times
+// them.
 bool tune_lookup_fused(int dtype, int L, long long G, FusedPlanConfig& cfg);
-bool tune_lookup_shift(int dtype, int L, long long G, int& shift);
+bool tune_lookup_shift(int dtype, int L, long long G, int& shift, int& levels);
 const FusedPlanConfig* tune_forced_fused();
-int tune_forced_shift();  // 0: none
+int tune_forced_shift();   // 0: none
+int tune_forced_levels();  // 0: the rule's
 
 // Multi-task single-pass kernel and its partial merge (repro_batch.cu); the
 // task / item / merge-block arrays are laid out as in multi_types.h.

@@ -22,11 +22,21 @@ namespace rp {
 
 // ------------------------------------------------------------------- kernels
 
+// Every record starts all zero (K = 0, no flags, zero level sums), so the
+// record area is cleared as one flat byte range with coalesced 16-byte stores
+// (the state is 16-byte aligned and the header 64 bytes); the header is
+// written by thread 0.
 __global__ void k_init_state(unsigned char* base, int dtype, int L, long long G) {
     StateView st{base, L, G};
     const long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    const long long nth = (long long)gridDim.x * blockDim.x;
     if (tid == 0) state_init_header(st, dtype);
-    for (long long g = tid; g < G; g += (long long)gridDim.x * blockDim.x) state_init_group(st, g);
+    const unsigned long long bytes = (unsigned long long)G * (8ull + 16ull * (unsigned long long)L);
+    uint4* rec = reinterpret_cast<uint4*>(base + sizeof(repro_state_header));
+    const long long n16 = (long long)(bytes / 16);
+    for (long long i = tid; i < n16; i += nth) rec[i] = make_uint4(0, 0, 0, 0);
+    if (tid == 0 && (bytes & 15))  // G odd: one 8-byte word left
+        *reinterpret_cast<unsigned long long*>(base + sizeof(repro_state_header) + bytes - 8) = 0ull;
 }
 
 // Max-abs pre-pass.  Kmax[g] (zeroed by the caller) receives max K(b) over
@@ -222,7 +232,8 @@ static int grid_for(long long work, int threads, int max_blocks) {
 
 cudaError_t launch_init_state(void* state, int dtype, int L, long long G, cudaStream_t s) {
     const int th = 256;
-    k_init_state<<<grid_for(G, th, device_info().sms * 8), th, 0, s>>>((unsigned char*)state, dtype, L, G);
+    const long long words = G * (8 + 16ll * L) / 16 + 1;
+    k_init_state<<<grid_for(words, th, device_info().sms * 4), th, 0, s>>>((unsigned char*)state, dtype, L, G);
     count_launches(1);
     return cudaGetLastError();
 }

@@ -44,8 +44,14 @@ namespace {
 constexpr int kPartThreads = 512;
 constexpr int kScatterRows = 8;          // rows per thread per scatter tile
 constexpr int kMaxParts = 8192;          // final partitions
-constexpr int kOneLevelParts = 64;       // beyond this, two passes
+constexpr int kOneLevelParts = 64;       // beyond this the rule takes two passes
+constexpr int kOneLevelMaxParts = 2048;  // one pass at most this wide
 constexpr long long kChunkRows = 32768;  // rows per unit of the fine pass
+// Work items per CTA the aggregation aims at: items are taken largest first
+// from a shared counter, so with about this many per CTA the last round
+// leaves few SMs idle; a partition longer than an item is split into several
+// (partial tables, merged afterwards).
+constexpr long long kItemsPerCta = 8;
 
 // Geometry of one partition pass: a row with key k goes to bucket
 // (k >> shift) & bmask and is written with key k & kmask.
@@ -117,10 +123,12 @@ __global__ void __launch_bounds__(kPartThreads) k_part_hist(const int32_t* __res
         bool bad = false;
         for (int p = threadIdx.x; p < pg.B; p += blockDim.x) s_hist[p] = 0;
         __syncthreads();
-        // 4 keys per thread per step (beg is a multiple of 4, keys 16-byte aligned)
+        // 4 keys per thread per load (beg is a multiple of 4, keys 16-byte
+        // aligned), four loads in flight per thread: one load at a time
+        // leaves too few bytes in flight per SM to reach HBM bandwidth
         const long long n4 = beg + ((end - beg) & ~3ll);
-        for (long long i = beg + 4 * (long long)threadIdx.x; i < n4; i += 4ll * blockDim.x) {
-            const int4 k = *reinterpret_cast<const int4*>(keys + i);
+        const long long step = 4ll * blockDim.x;
+        auto count4 = [&](const int4 k) {
             const int ks[4] = {k.x, k.y, k.z, k.w};
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
@@ -129,7 +137,16 @@ __global__ void __launch_bounds__(kPartThreads) k_part_hist(const int32_t* __res
                 else
                     bad = true;
             }
+        };
+        long long i = beg + 4 * (long long)threadIdx.x;
+        for (; i + 3 * step < n4; i += 4 * step) {
+            int4 k[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) k[u] = *reinterpret_cast<const int4*>(keys + i + u * step);
+#pragma unroll
+            for (int u = 0; u < 4; ++u) count4(k[u]);
         }
+        for (; i < n4; i += step) count4(*reinterpret_cast<const int4*>(keys + i));
         for (long long i = n4 + threadIdx.x; i < end; i += blockDim.x) {
             const int k = keys[i];
             if (!pg.check || (unsigned)k < (unsigned)Gk)
@@ -440,6 +457,22 @@ __global__ void __launch_bounds__(1024) k_seg_chunks(const long long* __restrict
     if (threadIdx.x == 0) *nchunks = s_w[32];
 }
 
+// Four consecutive values from a 16-byte aligned address.
+template <typename T>
+struct Vec4 {
+    T v[4];
+};
+
+__device__ __forceinline__ Vec4<double> load_vec4(const double* p) {
+    const double2 a = reinterpret_cast<const double2*>(p)[0], b = reinterpret_cast<const double2*>(p)[1];
+    return Vec4<double>{{a.x, a.y, b.x, b.y}};
+}
+
+__device__ __forceinline__ Vec4<float> load_vec4(const float* p) {
+    const float4 a = *reinterpret_cast<const float4*>(p);
+    return Vec4<float>{{a.x, a.y, a.z, a.w}};
+}
+
 // Per group of every final partition its window: the largest K(b) over its
 // finite values (the window of Algorithm 2 / the max-abs pre-pass, computed
 // per partition; -1 where the group has none).  Work comes as chunks of one
@@ -458,10 +491,31 @@ __global__ void __launch_bounds__(512) k_part_window(const int32_t* __restrict__
         const int Gq = min(Gp, G - ch.seg * Gp);
         for (int g = threadIdx.x; g < Gq; g += blockDim.x) s_win[g] = -1;
         __syncthreads();
-        for (long long r = ch.beg + threadIdx.x; r < ch.end; r += blockDim.x) {
-            const Split sp = split_value(ovals[r]);
-            if (!sp.flag && sp.mant != 0) atomicMax(&s_win[okeys[r]], sp.kb);
+        // rows 4 at a time (chunks start 4-row aligned), two groups of 4 in
+        // flight per thread; the shared maximum is read before it is raised
+        // (most rows of a group share its window)
+        auto see = [&](int k, T v) {
+            const Split sp = split_value(v);
+            if (!sp.flag && sp.mant != 0 && s_win[k] < sp.kb) atomicMax(&s_win[k], sp.kb);
+        };
+        auto see4 = [&](const int4 k, const Vec4<T>& v) {
+            see(k.x, v.v[0]);
+            see(k.y, v.v[1]);
+            see(k.z, v.v[2]);
+            see(k.w, v.v[3]);
+        };
+        const long long n4 = ch.beg + ((ch.end - ch.beg) & ~3ll);
+        const long long step = 4ll * blockDim.x;
+        long long r = ch.beg + 4ll * threadIdx.x;
+        for (; r + step < n4; r += 2 * step) {
+            const int4 ka = *reinterpret_cast<const int4*>(okeys + r);
+            const int4 kb = *reinterpret_cast<const int4*>(okeys + r + step);
+            const Vec4<T> va = load_vec4(ovals + r), vb = load_vec4(ovals + r + step);
+            see4(ka, va);
+            see4(kb, vb);
         }
+        if (r < n4) see4(*reinterpret_cast<const int4*>(okeys + r), load_vec4(ovals + r));
+        for (long long t = n4 + threadIdx.x; t < ch.end; t += blockDim.x) see(okeys[t], ovals[t]);
         __syncthreads();
         int* w = win + (size_t)ch.seg * Gp;
         for (int g = threadIdx.x; g < Gq; g += blockDim.x)
@@ -654,7 +708,7 @@ bool make_part_plan(const PartChoice& pc, int L, long long G, long long n, PartP
     pp.ctas = di.sms * pc.cfg.ctas_per_sm;
     const long long R = pc.cfg.R;
     const long long total_tiles = (n + R - 1) / R + F;
-    pp.tpi = std::max(8ll, (total_tiles + 2ll * pp.ctas - 1) / (2ll * pp.ctas));
+    pp.tpi = std::max(8ll, (total_tiles + kItemsPerCta * pp.ctas - 1) / (kItemsPerCta * pp.ctas));
     pp.tpi = std::min(pp.tpi, (1ll << 23) / R);
     pp.max_items = total_tiles / pp.tpi + F + 1;
     const long long max_split = std::min(F, total_tiles / pp.tpi + 1);
@@ -754,13 +808,15 @@ cudaError_t partition_pass(const int32_t* keys, const void* vals, int dtype, con
 bool partition_choose(int dtype, int L, long long G, PartChoice& pc) {
     // forced by the tuner (this thread) > tuned cache > rule; each only if usable
     int forced = tune_forced_shift();
-    int shift = 0;
+    int shift = 0, levels = 0;
     if (forced && shift_usable(dtype, L, G, forced, pc.cfg)) {
         shift = forced;
+        levels = tune_forced_levels();
     } else {
-        int tuned = 0;
-        if (tune_lookup_shift(dtype, L, G, tuned) && shift_usable(dtype, L, G, tuned, pc.cfg)) {
+        int tuned = 0, tuned_levels = 0;
+        if (tune_lookup_shift(dtype, L, G, tuned, tuned_levels) && shift_usable(dtype, L, G, tuned, pc.cfg)) {
             shift = tuned;
+            levels = tuned_levels;
         } else {
             // rule: the widest power-of-two slice whose table keeps two CTAs
             // per SM (then one), with at most kMaxParts partitions
@@ -776,11 +832,15 @@ bool partition_choose(int dtype, int L, long long G, PartChoice& pc) {
     }
     if (!shift) return false;
     pc.shift = shift;
-    // one pass up to kOneLevelParts partitions, else two with about sqrt(F)
-    // buckets per coarse partition
+    // rule: one pass up to kOneLevelParts partitions, else two with about
+    // sqrt(F) buckets per coarse partition; a measured choice may take one
+    // pass up to kOneLevelMaxParts (a wider scatter, one pass fewer over the
+    // rows) or two passes beyond kOneLevelParts
     const long long F = (G + (1ll << shift) - 1) >> shift;
-    pc.shift1 = 0;
-    if (F > kOneLevelParts) pc.shift1 = shift + (ceil_log2(F) + 1) / 2;
+    if (levels == 1 && F > kOneLevelMaxParts) levels = 0;
+    if (levels == 2 && F <= kOneLevelParts) levels = 0;
+    if (levels == 0) levels = F > kOneLevelParts ? 2 : 1;
+    pc.shift1 = levels == 2 ? shift + (ceil_log2(F) + 1) / 2 : 0;
     return true;
 }
 
@@ -948,7 +1008,7 @@ bool BatchPartition::plan(int dtype, int L, const std::vector<BatchPartInput>& i
     const long long R = P.pc.cfg.R;
     long long total_tiles = P.F;
     for (const BatchPartInput& x : in) total_tiles += (x.n + R - 1) / R;
-    P.tpi = std::max(8ll, (total_tiles + 2ll * P.ctas - 1) / (2ll * P.ctas));
+    P.tpi = std::max(8ll, (total_tiles + kItemsPerCta * P.ctas - 1) / (kItemsPerCta * P.ctas));
     P.tpi = std::min(P.tpi, (1ll << 23) / R);
     P.max_items = total_tiles / P.tpi + P.F + 1;
     const long long max_split = std::min<long long>(P.F, total_tiles / P.tpi + 1);

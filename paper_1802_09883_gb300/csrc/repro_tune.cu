@@ -32,10 +32,11 @@ using Key = std::tuple<int, int, int>;  // dtype, L, ceil(log2 G)
 
 std::mutex g_mu;
 std::map<Key, FusedPlanConfig> g_fused;
-std::map<Key, int> g_shift;
+std::map<Key, std::pair<int, int>> g_shift;  // partition shift, levels
 
 thread_local const FusedPlanConfig* t_force_fused = nullptr;
 thread_local int t_force_shift = 0;
+thread_local int t_force_levels = 0;
 thread_local bool t_ignore_cache = false;
 
 int gbucket(long long G) {
@@ -71,14 +72,16 @@ double time_median(const std::function<cudaError_t()>& run, cudaStream_t s, int 
 
 // RAII: force a choice on this thread while a candidate is timed.
 struct Force {
-    Force(const FusedPlanConfig* f, int shift, bool ignore_cache) {
+    Force(const FusedPlanConfig* f, int shift, bool ignore_cache, int levels = 0) {
         t_force_fused = f;
         t_force_shift = shift;
+        t_force_levels = levels;
         t_ignore_cache = ignore_cache;
     }
     ~Force() {
         t_force_fused = nullptr;
         t_force_shift = 0;
+        t_force_levels = 0;
         t_ignore_cache = false;
     }
 };
@@ -98,17 +101,19 @@ bool tune_lookup_fused(int dtype, int L, long long G, FusedPlanConfig& cfg) {
     return true;
 }
 
-bool tune_lookup_shift(int dtype, int L, long long G, int& shift) {
+bool tune_lookup_shift(int dtype, int L, long long G, int& shift, int& levels) {
     if (t_ignore_cache) return false;
     std::lock_guard<std::mutex> lk(g_mu);
     auto it = g_shift.find(key_of(dtype, L, G));
     if (it == g_shift.end()) return false;
-    shift = it->second;
+    shift = it->second.first;
+    levels = it->second.second;
     return true;
 }
 
 const FusedPlanConfig* tune_forced_fused() { return t_force_fused; }
 int tune_forced_shift() { return t_force_shift; }
+int tune_forced_levels() { return t_force_levels; }
 
 }  // namespace rp
 
@@ -194,12 +199,17 @@ repro_status repro_tune_groupby(const int32_t* keys, const void* values, int64_t
             Force f(nullptr, 0, true);
             if (!partition_choose(dtype, L, G, def)) return REPRO_ERANGE;
         }
+        // every width, each with one and with two partition passes where
+        // partition_choose allows that many
         std::vector<PartChoice> cands;
-        for (int shift = 6; shift <= 12; ++shift) {
-            Force f(nullptr, shift, true);
-            PartChoice pc{};
-            if (partition_choose(dtype, L, G, pc) && pc.shift == shift) cands.push_back(pc);
-        }
+        auto levels_of = [](const PartChoice& pc) { return pc.shift1 > pc.shift ? 2 : 1; };
+        for (int shift = 6; shift <= 12; ++shift)
+            for (int levels = 1; levels <= 2; ++levels) {
+                Force f(nullptr, shift, true, levels);
+                PartChoice pc{};
+                if (partition_choose(dtype, L, G, pc) && pc.shift == shift && levels_of(pc) == levels)
+                    cands.push_back(pc);
+            }
         size_t need = 16;
         for (const PartChoice& pc : cands) need = std::max(need, partitioned_scratch_bytes(pc, dtype, L, G, n));
         err = cudaMalloc(&state, sbytes);
@@ -209,7 +219,7 @@ repro_status repro_tune_groupby(const int32_t* keys, const void* values, int64_t
             return status_of(err);
         }
         double best = 0;
-        int pick = def.shift;
+        PartChoice pick = def;
         for (const PartChoice& pc : cands) {
             auto run = [&]() -> cudaError_t {
                 cudaError_t e = launch_init_state(state, dtype, L, G, s);
@@ -220,18 +230,19 @@ repro_status repro_tune_groupby(const int32_t* keys, const void* values, int64_t
             const double ms = time_median(run, s, 3, err);
             if (err != cudaSuccess) break;
             ++out->candidates;
-            if (pc.shift == def.shift) out->default_ms = ms;
+            if (pc.shift == def.shift && pc.shift1 == def.shift1) out->default_ms = ms;
             if (best == 0 || ms < best) {
                 best = ms;
-                pick = pc.shift;
+                pick = pc;
             }
         }
         cleanup();
         if (err != cudaSuccess) return status_of(err);
         out->best_ms = best;
-        out->partition_shift = pick;
+        out->partition_shift = pick.shift;
+        out->partition_levels = levels_of(pick);
         std::lock_guard<std::mutex> lk(g_mu);
-        g_shift[key_of(dtype, L, G)] = pick;
+        g_shift[key_of(dtype, L, G)] = {pick.shift, levels_of(pick)};
         return REPRO_OK;
     }
     out->path = 2;  // two-pass path: nothing to choose
@@ -243,15 +254,15 @@ repro_status repro_tune_save(const char* path) {
     FILE* f = fopen(path, "w");
     if (!f) return REPRO_EINVAL;
     std::lock_guard<std::mutex> lk(g_mu);
-    fprintf(f, "# repro tune cache v1: kind dtype L log2G values\n");
+    fprintf(f, "# repro tune cache v1: kind dtype L log2G values (part: shift levels)\n");
     for (const auto& kv : g_fused) {
         const FusedPlanConfig& c = kv.second;
         fprintf(f, "fused %d %d %d %d %d %d %d %d\n", std::get<0>(kv.first), std::get<1>(kv.first),
                 std::get<2>(kv.first), c.S, c.R, c.ncw, c.ctas_per_sm, c.copies);
     }
     for (const auto& kv : g_shift)
-        fprintf(f, "part %d %d %d %d\n", std::get<0>(kv.first), std::get<1>(kv.first), std::get<2>(kv.first),
-                kv.second);
+        fprintf(f, "part %d %d %d %d %d\n", std::get<0>(kv.first), std::get<1>(kv.first), std::get<2>(kv.first),
+                kv.second.first, kv.second.second);
     return fclose(f) == 0 ? REPRO_OK : REPRO_EINVAL;
 }
 
@@ -260,7 +271,7 @@ repro_status repro_tune_load(const char* path) {
     FILE* f = fopen(path, "r");
     if (!f) return REPRO_EINVAL;
     std::map<Key, FusedPlanConfig> fused;
-    std::map<Key, int> shift;
+    std::map<Key, std::pair<int, int>> shift;
     char line[256];
     bool ok = true;
     while (ok && fgets(line, sizeof line, f)) {
@@ -272,8 +283,10 @@ repro_status repro_tune_load(const char* path) {
             ok = sscanf(line, "%*s %d %d %d %d %d %d %d %d", &d, &L, &gb, &a[0], &a[1], &a[2], &a[3], &a[4]) == 8;
             if (ok) fused[Key{d, L, gb}] = FusedPlanConfig{a[0], a[1], a[2], a[3], a[4]};
         } else if (!strcmp(kind, "part")) {
-            ok = sscanf(line, "%*s %d %d %d %d", &d, &L, &gb, &a[0]) == 4 && a[0] >= 6 && a[0] <= 12;
-            if (ok) shift[Key{d, L, gb}] = a[0];
+            a[1] = 0;  // levels: optional, 0 = the rule's
+            ok = sscanf(line, "%*s %d %d %d %d %d", &d, &L, &gb, &a[0], &a[1]) >= 4 && a[0] >= 6 && a[0] <= 12 &&
+                 a[1] >= 0 && a[1] <= 2;
+            if (ok) shift[Key{d, L, gb}] = {a[0], a[1]};
         } else {
             ok = false;
         }

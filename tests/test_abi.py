@@ -72,18 +72,24 @@ def test_no_cpu_fallback():
 def test_tune_cache_round_trip_and_rejects_malformed(tmp_path):
     import paper_1802_09883_gb300 as R
     good = tmp_path / "tune.txt"
-    good.write_text("# a comment\nfused 0 3 10 3 2048 8 2 1\npart 0 3 20 11\nfused 1 2 5 2 1024 8 2 32\n")
+    good.write_text("# a comment\nfused 0 3 10 3 2048 8 2 1\npart 0 3 20 11\nfused 1 2 5 2 1024 8 2 32\n"
+                    "part 0 3 24 12 1\n")
     R.tune_clear()
     R.tune_load(str(good))
     out = tmp_path / "out.txt"
     R.tune_save(str(out))
     lines = sorted(l for l in out.read_text().splitlines() if not l.startswith("#"))
-    assert lines == sorted(["fused 0 3 10 3 2048 8 2 1", "part 0 3 20 11", "fused 1 2 5 2 1024 8 2 32"])
+    # a partition line without its pass count (levels) reads as 0: the rule's
+    assert lines == sorted(["fused 0 3 10 3 2048 8 2 1", "part 0 3 20 11 0", "fused 1 2 5 2 1024 8 2 32",
+                            "part 0 3 24 12 1"])
     bad = tmp_path / "bad.txt"
     bad.write_text("fused 0 3 10 3 2048\n")
     with pytest.raises(R.ReproError):
         R.tune_load(str(bad))
     bad.write_text("part 0 3 20 99\n")  # partition width out of range
+    with pytest.raises(R.ReproError):
+        R.tune_load(str(bad))
+    bad.write_text("part 0 3 20 11 3\n")  # more partition passes than exist
     with pytest.raises(R.ReproError):
         R.tune_load(str(bad))
     R.tune_clear()

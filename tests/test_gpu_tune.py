@@ -53,3 +53,26 @@ def test_batch_tune_keeps_results():
     for (k, v, G), st in zip(tasks, states):
         assert torch.equal(st.tensor, _state(k, v, G, 3).tensor)
     plan.close()
+
+
+@pytest.mark.parametrize("G", [1_000_003, 70_000])
+def test_every_partition_choice_gives_identical_state(G, tmp_path):
+    """Each partition width with one and with two partition passes (forced
+    through a loaded choice) gives the state bytes of the built-in rule."""
+    g = torch.Generator(device=DEV)
+    g.manual_seed(11)
+    n = (1 << 22) + 3  # ragged tail
+    keys = WL.uniform_keys(n, G, g, DEV)
+    vals = WL.random_values(n, -40, 40, g, DEV)
+    R.tune_clear()
+    ref = _state(keys, vals, G, 3)
+    bucket = (G - 1).bit_length()
+    f = tmp_path / "choice.txt"
+    for shift in range(6, 13):
+        for levels in (1, 2):
+            f.write_text(f"part 0 3 {bucket} {shift} {levels}\n")
+            R.tune_clear()
+            R.tune_load(str(f))
+            st = _state(keys, vals, G, 3)
+            assert torch.equal(ref.tensor, st.tensor), (shift, levels)
+    R.tune_clear()
