@@ -41,11 +41,19 @@ struct repro_accum {
         for (int j = 0; j < L; ++j) bins[j] = 0;
     }
 
+    // v[j] <- v[j - d] (zero where j < d), d >= 0, one level per step: the
+    // indices stay fixed, so the levels stay in registers.
+    __device__ __forceinline__ static void shift_down(__int128 (&v)[L], int d) {
+        for (int s = 0; s < d && s < L; ++s) {
+#pragma unroll
+            for (int j = L - 1; j > 0; --j) v[j] = v[j - 1];
+            v[0] = 0;
+        }
+    }
+
     // Move the window up to grid index k: level j takes the old level j - d.
     __device__ __forceinline__ void raise(int k) {
-        const int d = k - K;
-#pragma unroll
-        for (int j = L - 1; j >= 0; --j) bins[j] = j - d >= 0 ? bins[j - d] : 0;
+        shift_down(bins, k - K);
         K = k;
     }
 
@@ -59,20 +67,29 @@ struct repro_accum {
         if (s.kb > K) raise(s.kb);
         long long top, mid, low;
         rp::digits3<T>(s, top, mid, low);
-        const int j = K - s.kb;  // level of the value's top digit
-        if (j < L) bins[j] += top;
-        if (j + 1 < L && s.kb >= 1) bins[j + 1] += mid;
-        if (j + 2 < L && s.kb >= 2) bins[j + 2] += low;
+        // the digits at levels j, j + 1, j + 2 (j = K - K(b), the level of
+        // the top digit; grid indices below 0 and levels past L - 1 drop out)
+        __int128 a[L];
+#pragma unroll
+        for (int i = 0; i < L; ++i) a[i] = 0;
+        a[0] = top;
+        if (L > 1 && s.kb >= 1) a[L > 1 ? 1 : 0] = mid;
+        if (L > 2 && s.kb >= 2) a[L > 2 ? 2 : 0] = low;
+        shift_down(a, K - s.kb);
+#pragma unroll
+        for (int i = 0; i < L; ++i) bins[i] += a[i];
     }
 
     __device__ __forceinline__ void merge(const repro_accum& o) {
         flags |= o.flags;
         if (o.K < 0) return;
         if (o.K > K) raise(o.K);
-        const int d = K - o.K;
+        __int128 ob[L];
 #pragma unroll
-        for (int j = 0; j < L; ++j)
-            if (j - d >= 0) bins[j] += o.bins[j - d];
+        for (int j = 0; j < L; ++j) ob[j] = o.bins[j];
+        shift_down(ob, K - o.K);
+#pragma unroll
+        for (int j = 0; j < L; ++j) bins[j] += ob[j];
     }
 
     // Eq. (1): the level values rounded once each, folded from the lowest up.

@@ -33,13 +33,23 @@ struct MergeBlk {
     long long part;       // first record of the task's first partial table
 };
 
+// What the consumers of a stage need, written by the producer with the tile
+// (so the per-tile work reads no descriptor from global memory).
 struct StageMeta {
     int item;             // -1: no more work
     int rows;             // rows of this tile
     int rows_tma;         // rows delivered by TMA (a multiple of 4), the rest read from global
     int last;             // last tile of the item
     long long row0;       // first row of the tile within the task
+    int G;                // groups of the item's task
+    int first;            // first tile of the item
+    const int32_t* keys;  // the task's key and value columns at row0
+    const void* vals;
+    const int* win;       // the task's preset windows, or null
 };
+
+// Shared memory the multi-task kernel reserves for its stage records (S <= 8).
+constexpr size_t kMetaSmemBytes = sizeof(StageMeta) * 8;
 
 struct MultiArgs {
     const MTask* tasks;

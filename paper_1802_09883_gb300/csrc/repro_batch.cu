@@ -81,54 +81,85 @@ __device__ __forceinline__ void raise_and_add_multi(int nr, int nd, const int32_
     }
 }
 
+// v[j] <- v[j - d] (zero where j < d), d >= 0: one level per step with
+// fixed indices, so that v stays in registers.
+template <int L>
+__device__ __forceinline__ void shift_levels(__int128 (&v)[L], int d) {
+    for (int s = 0; s < d && s < L; ++s) {
+#pragma unroll
+        for (int j = L - 1; j > 0; --j) v[j] = v[j - 1];
+        v[0] = 0;
+    }
+}
+
 // Fold the CTA table into a record array (a partial table, or the task's
 // state when the item owns the task): records are aligned to the larger
 // window and their low levels dropped (operator+=(repro)); with `overwrite`
-// the old content is ignored.  Clears the table for the next item.
+// the old content is ignored.  Clears the table for the next item.  Each
+// thread takes NB groups at a time and reads their old records before it
+// writes any, so that NB record reads are in flight instead of one.
 template <int L>
 __device__ void flush_table(unsigned char* recs, int G, const Table& t, int* sK, int* sKp, unsigned* sF,
                             bool overwrite, int ctid, int NC) {
     constexpr size_t rec = 8 + 16 * L;
-    for (int g = ctid; g < G; g += NC) {
-        unsigned char* r = recs + (size_t)g * rec;
-        int* pK = reinterpret_cast<int*>(r);
-        unsigned* pF = reinterpret_cast<unsigned*>(r + 4);
-        long long* pb = reinterpret_cast<long long*>(r + 8);
-        const int Kt = sK[g];
-        const int Ks = overwrite ? Kt : *pK;
-        const int K = max(Kt, Ks);
-        __int128 acc[L];
+    constexpr int NB = 2;
+    for (int g0 = ctid; g0 < G; g0 += NB * NC) {
+        int Ks[NB];
+        unsigned Fo[NB];
+        __int128 old[NB][L];
 #pragma unroll
-        for (int j = 0; j < L; ++j) acc[j] = 0;
-        // table levels, aligned to K
-        __int128 tab[L];
+        for (int b = 0; b < NB; ++b) {
+            const int g = g0 + b * NC;
+            Ks[b] = 0;
+            Fo[b] = 0;
 #pragma unroll
-        for (int j = 0; j < L; ++j) {
-            tab[j] = 0;
-            for (int c = 0; c < t.C; ++c) {
-                const size_t i = t.at(g, j, c);
-                tab[j] += (__int128)table_value(t, i);
-                t.lo[i] = 0;
-                t.hi[i] = 0;
+            for (int j = 0; j < L; ++j) old[b][j] = 0;
+            if (g < G && !overwrite) {
+                const unsigned char* r = recs + (size_t)g * rec;
+                const long long* pb = reinterpret_cast<const long long*>(r + 8);
+                Ks[b] = *reinterpret_cast<const int*>(r);
+                Fo[b] = *reinterpret_cast<const unsigned*>(r + 4);
+#pragma unroll
+                for (int j = 0; j < L; ++j) old[b][j] = bin_read(&pb[2 * j], &pb[2 * j + 1]);
             }
         }
 #pragma unroll
-        for (int j = 0; j < L; ++j) {
-            const int jt = j - (K - Kt);
-            if (jt >= 0) acc[j] += tab[jt];
-            if (!overwrite) {
-                const int js = j - (K - Ks);
-                if (js >= 0) acc[j] += bin_read(&pb[2 * js], &pb[2 * js + 1]);
-            }
-        }
-        const unsigned f = (sF[g] & ~kQueued) | (overwrite ? 0u : *pF);
+        for (int b = 0; b < NB; ++b) {
+            const int g = g0 + b * NC;
+            if (g >= G) continue;
+            unsigned char* r = recs + (size_t)g * rec;
+            long long* pb = reinterpret_cast<long long*>(r + 8);
+            const int Kt = sK[g];
+            const int Kr = overwrite ? Kt : Ks[b];
+            const int K = max(Kt, Kr);
+            // table levels (all copies), aligned to K
+            __int128 tab[L];
 #pragma unroll
-        for (int j = 0; j < L; ++j) bin_write(&pb[2 * j], &pb[2 * j + 1], acc[j]);
-        *pK = K;
-        *pF = f;
-        sK[g] = kNoWindow;
-        sKp[g] = kNoWindow;
-        sF[g] = 0;
+            for (int j = 0; j < L; ++j) {
+                tab[j] = 0;
+                for (int c = 0; c < t.C; ++c) {
+                    const size_t i = t.at(g, j, c);
+                    tab[j] += (__int128)table_value(t, i);
+                    t.lo[i] = 0;
+                    t.hi[i] = 0;
+                }
+            }
+            // level j of the result takes level j - (K - Kt) of the table and
+            // j - (K - Kr) of the old record
+            shift_levels<L>(tab, K - Kt);
+            shift_levels<L>(old[b], K - Kr);
+            __int128 acc[L];
+#pragma unroll
+            for (int j = 0; j < L; ++j) acc[j] = overwrite ? tab[j] : tab[j] + old[b][j];
+            const unsigned f = (sF[g] & ~kQueued) | Fo[b];
+#pragma unroll
+            for (int j = 0; j < L; ++j) bin_write(&pb[2 * j], &pb[2 * j + 1], acc[j]);
+            *reinterpret_cast<int*>(r) = K;
+            *reinterpret_cast<unsigned*>(r + 4) = f;
+            sK[g] = kNoWindow;
+            sKp[g] = kNoWindow;
+            sF[g] = 0;
+        }
     }
 }
 
@@ -218,12 +249,22 @@ __global__ void __launch_bounds__(32 * (NCW + 1)) k_fused_multi(MultiArgs a, int
                         sm.item = -1;
                         sm.rows = sm.rows_tma = sm.last = 0;
                         sm.row0 = 0;
+                        sm.G = 0;
+                        sm.first = 0;
+                        sm.keys = nullptr;
+                        sm.vals = nullptr;
+                        sm.win = nullptr;
                     } else {
                         sm.item = w;
                         sm.row0 = it.row0 + t * R;
                         sm.rows = (int)min((long long)R, it.row1 - sm.row0);
                         sm.rows_tma = sm.rows & ~3;
                         sm.last = t == ntile - 1;
+                        sm.G = tk.G;
+                        sm.first = t == 0;
+                        sm.keys = tk.keys + sm.row0;
+                        sm.vals = reinterpret_cast<const T*>(tk.vals) + sm.row0;
+                        sm.win = tk.win;
                     }
                     meta[s] = sm;
                     const uint32_t kb = (uint32_t)sm.rows_tma * 4, vb = (uint32_t)sm.rows_tma * sizeof(T);
@@ -259,18 +300,16 @@ __global__ void __launch_bounds__(32 * (NCW + 1)) k_fused_multi(MultiArgs a, int
         if (*abort_flag) break;
         const StageMeta sm = meta[s];
         if (sm.item < 0) break;
-        const MItem it = a.items[sm.item];
-        const MTask tk = a.tasks[it.task];
-        const int G = tk.G;
-        if (tk.win && sm.row0 == it.row0) {  // known windows: no row of the item raises one
-            for (int g = ctid; g < G; g += NC) sK[g] = sKp[g] = (int)tk.win[g];
+        const int G = sm.G;
+        if (sm.win && sm.first) {  // known windows: no row of the item raises one
+            for (int g = ctid; g < G; g += NC) sK[g] = sKp[g] = __ldg(&sm.win[g]);
             named_bar_sync(1, NC);
         }
         int* cnt = &ctl[2 * (tcount % 3)];
         const int32_t* tk_s = skeys + (size_t)s * R;
         const T* tv_s = svals + (size_t)s * R;
-        const int32_t* gk = tk.keys + sm.row0;
-        const T* gv = reinterpret_cast<const T*>(tk.vals) + sm.row0;
+        const int32_t* gk = sm.keys;
+        const T* gv = static_cast<const T*>(sm.vals);
         sa.keys = smem_addr(tk_s);
         sa.vals = smem_addr(tv_s);
         for (int r = 4 * ctid; r < sm.rows_tma; r += 4 * NC)
@@ -293,6 +332,8 @@ __global__ void __launch_bounds__(32 * (NCW + 1)) k_fused_multi(MultiArgs a, int
         if ((ctid & 31) == 0) mbar_arrive(&empty[s]);
         ++tcount;
         if (sm.last) {
+            const MItem it = a.items[sm.item];
+            const MTask tk = a.tasks[it.task];
             unsigned* errors = &reinterpret_cast<repro_state_header*>(tk.hdr)->errors;
             const bool hdr_ok = task_header_ok(tk.hdr, dtype, L, tk.G_hdr);
             if (__any_sync(0xffffffffu, bad_key) && (ctid & 31) == 0) atomicOr(errors, REPRO_ERR_KEY);
@@ -497,9 +538,9 @@ repro_status plan_batch_host(const repro_task* tasks, int ntasks, int dtype, int
                            (unsigned char*)tasks[t].state + sizeof(repro_state_header), nullptr};
     if (fast.empty()) return REPRO_OK;
     if (fixed_cfg) {
-        if (!fused_config_fits(dtype, L, (int)gcap, sizeof(StageMeta) * 8, *fixed_cfg)) return REPRO_ERANGE;
+        if (!fused_config_fits(dtype, L, (int)gcap, kMetaSmemBytes, *fixed_cfg)) return REPRO_ERANGE;
         H.cfg = *fixed_cfg;
-    } else if (!fused_plan_config(dtype, L, (int)gcap, sizeof(StageMeta) * 8, H.cfg)) {
+    } else if (!fused_plan_config(dtype, L, (int)gcap, kMetaSmemBytes, H.cfg)) {
         return REPRO_ERANGE;
     }
     H.gcap = (int)gcap;

@@ -33,6 +33,7 @@
 #include <vector>
 
 #include "multi_types.h"
+#include "ptx.cuh"
 #include "repro_device.cuh"
 #include "repro.h"
 #include "repro_internal.h"
@@ -43,6 +44,7 @@ namespace {
 
 constexpr int kPartThreads = 512;
 constexpr int kScatterRows = 8;          // rows per thread per scatter tile
+constexpr uint64_t kCopyWaitNs = 2000000000ull;  // a scatter tile's copy is given up after 2 s
 constexpr int kMaxParts = 8192;          // final partitions
 constexpr int kOneLevelParts = 64;       // beyond this the rule takes two passes
 constexpr int kOneLevelMaxParts = 2048;  // one pass at most this wide
@@ -323,65 +325,123 @@ __device__ int block_exclusive_scan(int* a, int n, int* warp_tot) {
 // bucket with one shared atomic, a block scan gives each bucket its place in
 // the tile and one global slot range per tile, rows are sorted in shared
 // memory, and consecutive threads then write consecutive runs (coalesced
-// stores).
+// stores).  The next tile's rows are fetched by one TMA bulk copy into a
+// staging buffer while this one is ranked, sorted and written, so reads stay
+// in flight through the whole tile (unit starts are 4-row aligned, so every
+// copy starts 16-byte aligned; a tile's last rows % 4 are read directly).
 template <typename T>
 __global__ void __launch_bounds__(kPartThreads) k_part_scatter(const int32_t* __restrict__ keys0,
                                                                const T* __restrict__ vals0, Units units,
                                                                PassGeom pg, const int* __restrict__ offsets,
-                                                               int32_t* __restrict__ okeys, T* __restrict__ ovals) {
+                                                               int32_t* __restrict__ okeys, T* __restrict__ ovals,
+                                                               unsigned* errors0) {
     extern __shared__ __align__(16) unsigned char s_raw[];
     constexpr int RPT = kScatterRows;  // rows per thread per tile
-    const int TILE = RPT * kPartThreads;
-    T* s_vals = reinterpret_cast<T*>(s_raw);              // [TILE]
-    int* s_keys = reinterpret_cast<int*>(s_vals + TILE);  // [TILE] keys, sorted by bucket
-    int* s_cur = s_keys + TILE;                           // [B] global write cursor
+    constexpr int TILE = RPT * kPartThreads;
+    T* s_vals = reinterpret_cast<T*>(s_raw);              // [TILE] rows sorted by bucket
+    T* s_in_vals = s_vals + TILE;                         // [TILE] staging (TMA)
+    int* s_keys = reinterpret_cast<int*>(s_in_vals + TILE);  // [TILE] keys, sorted by bucket
+    int* s_in_keys = s_keys + TILE;                       // [TILE] staging (TMA)
+    uint64_t* bar = reinterpret_cast<uint64_t*>(s_in_keys + TILE);
+    int* s_cur = reinterpret_cast<int*>(bar + 1);         // [B] global write cursor
     int* s_cnt = s_cur + pg.B;                            // [B] rows per bucket in the tile
     int* s_gb = s_cnt + pg.B;                             // [B] global base of the tile's run
     int* s_wt = s_gb + pg.B;                              // [33] scan scratch
-    for (int unit = blockIdx.x;; unit += unit_step(units)) {
-        long long beg, end;
-        int seg;
-        if (!unit_rows(units, unit, beg, end, seg)) break;
-        const int32_t* keys = units.segs ? units.segs[seg].keys : keys0;
-        const T* vals = units.segs ? static_cast<const T*>(units.segs[seg].vals) : vals0;
+    const int tid = threadIdx.x;
+
+    // the tile sequence of this CTA: its units in order, each cut into tiles
+    auto seg_keys = [&](int seg) { return units.segs ? units.segs[seg].keys : keys0; };
+    auto seg_vals = [&](int seg) { return units.segs ? static_cast<const T*>(units.segs[seg].vals) : vals0; };
+    auto issue = [&](int seg, long long tb, long long end) {  // thread 0: the tile at tb
+        const int rows_tma = (int)min((long long)TILE, end - tb) & ~3;
+        mbar_arrive_expect_tx(bar, (uint32_t)rows_tma * (4 + sizeof(T)));
+        if (rows_tma > 0) {
+            bulk_g2s(s_in_keys, seg_keys(seg) + tb, (uint32_t)rows_tma * 4, bar);
+            bulk_g2s(s_in_vals, seg_vals(seg) + tb, (uint32_t)rows_tma * sizeof(T), bar);
+        }
+    };
+    if (tid == 0) {
+        mbar_init(bar, 1);
+        fence_barrier_init();
+    }
+    __syncthreads();
+    uint32_t phase = 0;
+    int unit = blockIdx.x;
+    long long beg, end;
+    int seg;
+    bool have = unit_rows(units, unit, beg, end, seg);
+    while (have && beg >= end && units.chunks) {  // the first unit with rows
+        unit += unit_step(units);
+        have = unit_rows(units, unit, beg, end, seg);
+    }
+    have = have && beg < end;
+    if (have && tid == 0) issue(seg, beg, end);
+    while (have) {
+        const int32_t* keys = seg_keys(seg);
+        const T* vals = seg_vals(seg);
         const int Gk = units.segs ? units.segs[seg].G : pg.G;
-        for (int p = threadIdx.x; p < pg.B; p += blockDim.x) {
+        for (int p = tid; p < pg.B; p += blockDim.x) {
             s_cur[p] = offsets[(size_t)unit * pg.ustride + (size_t)p * pg.bstride];
             s_cnt[p] = 0;
         }
         __syncthreads();
         for (long long tb = beg; tb < end; tb += TILE) {
+            const int rows = (int)min((long long)TILE, end - tb);
+            const int rows_tma = rows & ~3;
+            const bool ok = mbar_wait_bounded(bar, phase, kCopyWaitNs);
+            phase ^= 1;
+            if (__syncthreads_or(!ok)) {  // the copy never landed: flag it, wait once more, stop
+                if (tid == 0) {
+                    atomicOr(units.segs ? units.segs[seg].errors : errors0, REPRO_ERR_TIMEOUT);
+                    mbar_wait_bounded(bar, phase ^ 1, kCopyWaitNs);
+                }
+                return;
+            }
             int k[RPT];
             T v[RPT];
             int rank[RPT];
 #pragma unroll
-            for (int h = 0; h < RPT / 4; ++h) {  // quads strided by the block: coalesced 16-byte loads
-                const long long r0 = tb + 4ll * (threadIdx.x + h * kPartThreads);
+            for (int h = 0; h < RPT / 4; ++h) {  // quads strided by the block
+                const int r0 = 4 * (tid + h * kPartThreads);
                 int* kq = &k[4 * h];
                 T* vq = &v[4 * h];
                 kq[0] = kq[1] = kq[2] = kq[3] = -1;
                 vq[0] = vq[1] = vq[2] = vq[3] = 0;
-                if (r0 + 3 < end) {
-                    const int4 k4 = *reinterpret_cast<const int4*>(keys + r0);
+                if (r0 + 3 < rows_tma) {
+                    const int4 k4 = *reinterpret_cast<const int4*>(s_in_keys + r0);
                     kq[0] = k4.x; kq[1] = k4.y; kq[2] = k4.z; kq[3] = k4.w;
-                    RowQuad<T>::load(vals + r0, vq);
+                    RowQuad<T>::load(s_in_vals + r0, vq);
                 } else {
 #pragma unroll
                     for (int j = 0; j < 4; ++j)
-                        if (r0 + j < end) {
-                            kq[j] = keys[r0 + j];
-                            vq[j] = vals[r0 + j];
+                        if (r0 + j < rows) {
+                            kq[j] = keys[tb + r0 + j];
+                            vq[j] = vals[tb + r0 + j];
                         }
                 }
             }
 #pragma unroll
             for (int j = 0; j < RPT; ++j) {
-                const bool ok = k[j] >= 0 && (!pg.check || k[j] < Gk);
-                rank[j] = ok ? atomicAdd(&s_cnt[((unsigned)k[j] >> pg.shift) & pg.bmask], 1) : -1;
+                const bool okk = k[j] >= 0 && (!pg.check || k[j] < Gk);
+                rank[j] = okk ? atomicAdd(&s_cnt[((unsigned)k[j] >> pg.shift) & pg.bmask], 1) : -1;
             }
-            __syncthreads();
+            __syncthreads();  // staging read by all; counts complete
+            if (tid == 0) {   // fetch the next tile (this unit's, else the next unit's first)
+                fence_proxy_async_smem();
+                if (tb + TILE < end) {
+                    issue(seg, tb + TILE, end);
+                } else if (units.chunks) {
+                    long long b2, e2;
+                    int s2;
+                    for (int u2 = unit + unit_step(units); unit_rows(units, u2, b2, e2, s2); u2 += unit_step(units))
+                        if (b2 < e2) {
+                            issue(s2, b2, e2);
+                            break;
+                        }
+                }
+            }
             // reserve each bucket's run in global memory, then place of each bucket in the tile
-            for (int p = threadIdx.x; p < pg.B; p += blockDim.x) {
+            for (int p = tid; p < pg.B; p += blockDim.x) {
                 s_gb[p] = s_cur[p];
                 s_cur[p] += s_cnt[p];
             }
@@ -394,7 +454,7 @@ __global__ void __launch_bounds__(kPartThreads) k_part_scatter(const int32_t* __
                     s_vals[pos] = v[j];
                 }
             __syncthreads();
-            for (int i = threadIdx.x; i < nvalid; i += blockDim.x) {
+            for (int i = tid; i < nvalid; i += blockDim.x) {
                 const int kk = s_keys[i];
                 const int p = ((unsigned)kk >> pg.shift) & pg.bmask;
                 const int pos = s_gb[p] + (i - s_cnt[p]);
@@ -402,10 +462,15 @@ __global__ void __launch_bounds__(kPartThreads) k_part_scatter(const int32_t* __
                 ovals[pos] = s_vals[i];
             }
             __syncthreads();
-            for (int p = threadIdx.x; p < pg.B; p += blockDim.x) s_cnt[p] = 0;
+            for (int p = tid; p < pg.B; p += blockDim.x) s_cnt[p] = 0;
             __syncthreads();
         }
         if (!units.chunks) break;
+        // the next unit with rows (its first tile is already on its way)
+        do {
+            unit += unit_step(units);
+            have = unit_rows(units, unit, beg, end, seg);
+        } while (have && beg >= end);
     }
 }
 
@@ -555,6 +620,16 @@ __device__ __forceinline__ void part_owner(int p, const PartTask* tt, int B, int
     }
 }
 
+// Work items of a partition of cnt rows: its tiles shared out evenly over
+// floor(tiles / tpi) items (at least one), so that an item holds at least
+// tpi tiles -- a partition is split only when it holds two items' worth, and
+// every split costs a partial table and its merge.
+__device__ __forceinline__ long long part_items(long long cnt, int R, long long tpi) {
+    if (cnt == 0) return 0;
+    const long long tiles = (cnt + R - 1) / R;
+    return max(1ll, tiles / tpi);
+}
+
 __global__ void __launch_bounds__(1024) k_part_plan(const long long* __restrict__ pstart,
                                                     const long long* __restrict__ pcount, PartGeom pg, int G, int R,
                                                     long long tpi, const int32_t* okeys, const void* ovals,
@@ -573,7 +648,7 @@ __global__ void __launch_bounds__(1024) k_part_plan(const long long* __restrict_
         unsigned char* h;
         part_owner(p, tt, B, G, hdr, j, Gt, h);
         const int Gp = max(0, min(pg.Gp, Gt - j * pg.Gp));
-        const long long nit = cnt == 0 || Gp == 0 ? 0 : (((cnt + R - 1) / R) + tpi - 1) / tpi;
+        const long long nit = Gp == 0 ? 0 : part_items(cnt, R, tpi);
         it += nit;
         if (nit > 1) {
             pt += nit * Gp;
@@ -618,13 +693,14 @@ __global__ void __launch_bounds__(1024) k_part_plan(const long long* __restrict_
         t.recs = h + sizeof(repro_state_header) + (size_t)j * pg.Gp * rec;
         t.win = win ? win + (size_t)p * pg.Gp : nullptr;
         tasks[p] = t;
-        const long long nit = cnt == 0 || Gp == 0 ? 0 : (((cnt + R - 1) / R) + tpi - 1) / tpi;
+        const long long nit = Gp == 0 ? 0 : part_items(cnt, R, tpi);
+        const long long tiles = (cnt + R - 1) / R;
         for (long long k = 0; k < nit; ++k) {
             MItem m;
             m.task = p;
             m.excl = nit == 1;
-            m.row0 = k * tpi * R;
-            m.row1 = min(cnt, (k + 1) * tpi * R);
+            m.row0 = k * tiles / nit * R;
+            m.row1 = min(cnt, (k + 1) * tiles / nit * R);
             m.part = nit == 1 ? -1 : pt + k * Gp;
             items[it + k] = m;
         }
@@ -665,7 +741,7 @@ bool shift_usable(int dtype, int L, long long G, int shift, FusedPlanConfig& cfg
     if (shift < 6 || shift > 12) return false;
     const long long F = (G + (1ll << shift) - 1) >> shift;
     if (F > kMaxParts) return false;
-    return fused_plan_config(dtype, L, 1 << shift, 256, cfg);
+    return fused_plan_config(dtype, L, 1 << shift, kMetaSmemBytes, cfg);
 }
 
 int ceil_log2(long long x) {
@@ -713,7 +789,7 @@ bool make_part_plan(const PartChoice& pc, int L, long long G, long long n, PartP
     pp.max_items = total_tiles / pp.tpi + F + 1;
     const long long max_split = std::min(F, total_tiles / pp.tpi + 1);
     pp.max_blks = max_split * ((Gp + 31) / 32);
-    // only partitions with more than tpi tiles are split into several items
+    // only partitions of at least 2 tpi tiles are split into several items
     pp.max_part_recs = (total_tiles / pp.tpi + 1 + max_split) * (long long)Gp;
     pp.windows = n < kWindowRowsPerGroup * G ? 1 : 0;
     pp.max_wchunks = (n + kWindowChunkRows - 1) / kWindowChunkRows + F;
@@ -778,11 +854,13 @@ PartScratch part_scratch_layout(const PartPlan& pp, long long n, int dtype, int 
 
 template <typename T>
 cudaError_t launch_scatter(const int32_t* keys, const void* vals, const Units& u, const PassGeom& pg, int grid,
-                           const int* offsets, int32_t* okeys, void* ovals, cudaStream_t s) {
-    const size_t smem = (size_t)kScatterRows * kPartThreads * (sizeof(T) + 4) + 3 * (size_t)pg.B * 4 + 33 * 4;
+                           const int* offsets, int32_t* okeys, void* ovals, unsigned* errors, cudaStream_t s) {
+    // sorted rows + staging rows, the mbarrier, three per-bucket arrays, scan scratch
+    const size_t smem = 2 * (size_t)kScatterRows * kPartThreads * (sizeof(T) + 4) + 8 + 3 * (size_t)pg.B * 4 + 33 * 4;
     cudaError_t e = cudaFuncSetAttribute(k_part_scatter<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k_part_scatter<T><<<grid, kPartThreads, smem, s>>>(keys, (const T*)vals, u, pg, offsets, okeys, (T*)ovals);
+    k_part_scatter<T><<<grid, kPartThreads, smem, s>>>(keys, (const T*)vals, u, pg, offsets, okeys, (T*)ovals,
+                                                       errors);
     return cudaGetLastError();
 }
 
@@ -799,8 +877,8 @@ cudaError_t partition_pass(const int32_t* keys, const void* vals, int dtype, con
     count_launches(5);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    return dtype == REPRO_F64 ? launch_scatter<double>(keys, vals, u, pg, grid, offsets, okeys, ovals, s)
-                              : launch_scatter<float>(keys, vals, u, pg, grid, offsets, okeys, ovals, s);
+    return dtype == REPRO_F64 ? launch_scatter<double>(keys, vals, u, pg, grid, offsets, okeys, ovals, errors, s)
+                              : launch_scatter<float>(keys, vals, u, pg, grid, offsets, okeys, ovals, errors, s);
 }
 
 }  // namespace
@@ -861,7 +939,7 @@ cudaError_t launch_groupby_partitioned(const int32_t* keys, const void* vals, lo
                                        long long G, const PartChoice& pc, void* state, void* scratch,
                                        cudaStream_t s) {
     PartPlan pp;
-    if (!make_part_plan(pc, L, G, n, pp) || !fused_config_fits(dtype, L, pp.Gp, 256, pc.cfg))
+    if (!make_part_plan(pc, L, G, n, pp) || !fused_config_fits(dtype, L, pp.Gp, kMetaSmemBytes, pc.cfg))
         return cudaErrorInvalidValue;
     const PartScratch ly = part_scratch_layout(pp, n, dtype, L);
     unsigned char* b = (unsigned char*)scratch;
