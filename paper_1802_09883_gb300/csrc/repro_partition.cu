@@ -113,8 +113,11 @@ __device__ __forceinline__ int unit_step(const Units& u) { return u.chunks ? (in
 
 __global__ void __launch_bounds__(kPartThreads) k_part_hist(const int32_t* __restrict__ keys0, Units units,
                                                             PassGeom pg, int* __restrict__ counts,
-                                                            unsigned* __restrict__ errors0) {
-    extern __shared__ int s_hist[];
+                                                            unsigned* __restrict__ errors0,
+                                                            unsigned long long* __restrict__ ftot, int fshift,
+                                                            int Ff) {
+    extern __shared__ int s_hist[];  // [B] bucket counts, then [Ff] final-partition counts (ftot set)
+    int* s_fin = s_hist + pg.B;
     for (int unit = blockIdx.x;; unit += unit_step(units)) {
         long long beg, end;
         int seg;
@@ -124,21 +127,27 @@ __global__ void __launch_bounds__(kPartThreads) k_part_hist(const int32_t* __res
         unsigned* errors = units.segs ? units.segs[seg].errors : errors0;
         bool bad = false;
         for (int p = threadIdx.x; p < pg.B; p += blockDim.x) s_hist[p] = 0;
+        if (ftot)
+            for (int p = threadIdx.x; p < Ff; p += blockDim.x) s_fin[p] = 0;
         __syncthreads();
         // 4 keys per thread per load (beg is a multiple of 4, keys 16-byte
         // aligned), four loads in flight per thread: one load at a time
         // leaves too few bytes in flight per SM to reach HBM bandwidth
         const long long n4 = beg + ((end - beg) & ~3ll);
         const long long step = 4ll * blockDim.x;
-        auto count4 = [&](const int4 k) {
-            const int ks[4] = {k.x, k.y, k.z, k.w};
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                if (!pg.check || (unsigned)ks[q] < (unsigned)Gk)
-                    atomicAdd(&s_hist[((unsigned)ks[q] >> pg.shift) & pg.bmask], 1);
-                else
-                    bad = true;
+        auto count1 = [&](int k) {
+            if (!pg.check || (unsigned)k < (unsigned)Gk) {
+                atomicAdd(&s_hist[((unsigned)k >> pg.shift) & pg.bmask], 1);
+                if (ftot) atomicAdd(&s_fin[(unsigned)k >> fshift], 1);
+            } else {
+                bad = true;
             }
+        };
+        auto count4 = [&](const int4 k) {
+            count1(k.x);
+            count1(k.y);
+            count1(k.z);
+            count1(k.w);
         };
         long long i = beg + 4 * (long long)threadIdx.x;
         for (; i + 3 * step < n4; i += 4 * step) {
@@ -149,17 +158,14 @@ __global__ void __launch_bounds__(kPartThreads) k_part_hist(const int32_t* __res
             for (int u = 0; u < 4; ++u) count4(k[u]);
         }
         for (; i < n4; i += step) count4(*reinterpret_cast<const int4*>(keys + i));
-        for (long long i = n4 + threadIdx.x; i < end; i += blockDim.x) {
-            const int k = keys[i];
-            if (!pg.check || (unsigned)k < (unsigned)Gk)
-                atomicAdd(&s_hist[((unsigned)k >> pg.shift) & pg.bmask], 1);
-            else
-                bad = true;
-        }
+        for (long long i = n4 + threadIdx.x; i < end; i += blockDim.x) count1(keys[i]);
         if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(errors, REPRO_ERR_KEY);
         __syncthreads();
         for (int p = threadIdx.x; p < pg.B; p += blockDim.x)
             counts[(size_t)unit * pg.ustride + (size_t)p * pg.bstride] = s_hist[p];
+        if (ftot)
+            for (int p = threadIdx.x; p < Ff; p += blockDim.x)
+                if (s_fin[p]) atomicAdd(&ftot[p], (unsigned long long)s_fin[p]);
         __syncthreads();
         if (!units.chunks) break;
     }
@@ -199,10 +205,12 @@ __global__ void __launch_bounds__(256) k_scan_totals(const int* __restrict__ cou
     }
 }
 
-// One block: 4-row-aligned partition starts (exclusive scan over partitions).
+// One block: 4-row-aligned partition starts (exclusive scan over partitions);
+// with `cursor`, also every partition's write cursor (its start).
 __global__ void __launch_bounds__(1024) k_scan_starts(const long long* __restrict__ ptot, int F,
                                                       long long* __restrict__ pstart,
-                                                      long long* __restrict__ pcount) {
+                                                      long long* __restrict__ pcount,
+                                                      int* __restrict__ cursor) {
     __shared__ long long s_w[33];
     const int per = (F + blockDim.x - 1) / blockDim.x;
     const int p0 = threadIdx.x * per, p1 = min(F, p0 + per);
@@ -233,6 +241,7 @@ __global__ void __launch_bounds__(1024) k_scan_starts(const long long* __restric
     for (int p = p0; p < p1; ++p) {
         pstart[p] = run;
         pcount[p] = ptot[p];
+        if (cursor) cursor[p] = (int)run;
         run += (ptot[p] + 3) & ~3ll;
     }
 }
@@ -333,6 +342,7 @@ template <typename T>
 __global__ void __launch_bounds__(kPartThreads) k_part_scatter(const int32_t* __restrict__ keys0,
                                                                const T* __restrict__ vals0, Units units,
                                                                PassGeom pg, const int* __restrict__ offsets,
+                                                               int* __restrict__ cursor,
                                                                int32_t* __restrict__ okeys, T* __restrict__ ovals,
                                                                unsigned* errors0) {
     extern __shared__ __align__(16) unsigned char s_raw[];
@@ -381,7 +391,7 @@ __global__ void __launch_bounds__(kPartThreads) k_part_scatter(const int32_t* __
         const T* vals = seg_vals(seg);
         const int Gk = units.segs ? units.segs[seg].G : pg.G;
         for (int p = tid; p < pg.B; p += blockDim.x) {
-            s_cur[p] = offsets[(size_t)unit * pg.ustride + (size_t)p * pg.bstride];
+            s_cur[p] = offsets ? offsets[(size_t)unit * pg.ustride + (size_t)p * pg.bstride] : 0;
             s_cnt[p] = 0;
         }
         __syncthreads();
@@ -440,10 +450,16 @@ __global__ void __launch_bounds__(kPartThreads) k_part_scatter(const int32_t* __
                         }
                 }
             }
-            // reserve each bucket's run in global memory, then place of each bucket in the tile
+            // reserve each bucket's run in global memory (from the unit's own
+            // cursors, or from the partition's shared cursor: rows of a
+            // partition in any order), then place of each bucket in the tile
             for (int p = tid; p < pg.B; p += blockDim.x) {
-                s_gb[p] = s_cur[p];
-                s_cur[p] += s_cnt[p];
+                if (offsets) {
+                    s_gb[p] = s_cur[p];
+                    s_cur[p] += s_cnt[p];
+                } else {
+                    s_gb[p] = s_cnt[p] ? atomicAdd(&cursor[(size_t)seg * pg.B + p], s_cnt[p]) : 0;
+                }
             }
             const int nvalid = block_exclusive_scan(s_cnt, pg.B, s_wt);  // s_cnt now holds tile starts
 #pragma unroll
@@ -804,7 +820,7 @@ struct PartScratch {
     size_t akeys, avals;               // coarse output (two passes)
     size_t okeys, ovals;               // final partitions
     size_t counts1, offsets1, ptot1, pstart1, pcount1;
-    size_t chunks, cbase, nunits, counts2, offsets2;
+    size_t chunks, cursor;
     size_t ptot, pstart, pcount;
     size_t win, wchunks;
     size_t tasks, items, blks, parts, ints, total;
@@ -831,10 +847,7 @@ PartScratch part_scratch_layout(const PartPlan& pp, long long n, int dtype, int 
         take(s.pstart1, (size_t)pp.F1 * 8);
         take(s.pcount1, (size_t)pp.F1 * 8);
         take(s.chunks, (size_t)pp.max_chunks * sizeof(PartChunk));
-        take(s.cbase, (size_t)pp.F1 * 4);
-        take(s.nunits, (size_t)pp.F1 * 4);
-        take(s.counts2, (size_t)pp.max_chunks * pp.F2 * 4);
-        take(s.offsets2, (size_t)pp.max_chunks * pp.F2 * 4);
+        take(s.cursor, (size_t)pp.Fs * 4);
     }
     take(s.ptot, (size_t)pp.Fs * 8);
     take(s.pstart, (size_t)pp.Fs * 8);
@@ -854,31 +867,51 @@ PartScratch part_scratch_layout(const PartPlan& pp, long long n, int dtype, int 
 
 template <typename T>
 cudaError_t launch_scatter(const int32_t* keys, const void* vals, const Units& u, const PassGeom& pg, int grid,
-                           const int* offsets, int32_t* okeys, void* ovals, unsigned* errors, cudaStream_t s) {
+                           const int* offsets, int* cursor, int32_t* okeys, void* ovals, unsigned* errors,
+                           cudaStream_t s) {
     // sorted rows + staging rows, the mbarrier, three per-bucket arrays, scan scratch
     const size_t smem = 2 * (size_t)kScatterRows * kPartThreads * (sizeof(T) + 4) + 8 + 3 * (size_t)pg.B * 4 + 33 * 4;
     cudaError_t e = cudaFuncSetAttribute(k_part_scatter<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k_part_scatter<T><<<grid, kPartThreads, smem, s>>>(keys, (const T*)vals, u, pg, offsets, okeys, (T*)ovals,
-                                                       errors);
+    k_part_scatter<T><<<grid, kPartThreads, smem, s>>>(keys, (const T*)vals, u, pg, offsets, cursor, okeys,
+                                                       (T*)ovals, errors);
     return cudaGetLastError();
 }
 
+cudaError_t launch_hist(const int32_t* keys, const Units& u, const PassGeom& pg, int grid, int* counts,
+                        unsigned* errors, unsigned long long* ftot, int fshift, int Ff, cudaStream_t s) {
+    const size_t smem = ((size_t)pg.B + (ftot ? (size_t)Ff : 0)) * 4;
+    cudaError_t e = cudaFuncSetAttribute(k_part_hist, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_part_hist<<<grid, kPartThreads, smem, s>>>(keys, u, pg, counts, errors, ftot, fshift, Ff);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_scatter_t(int dtype, const int32_t* keys, const void* vals, const Units& u, const PassGeom& pg,
+                             int grid, const int* offsets, int* cursor, int32_t* okeys, void* ovals,
+                             unsigned* errors, cudaStream_t s) {
+    return dtype == REPRO_F64
+               ? launch_scatter<double>(keys, vals, u, pg, grid, offsets, cursor, okeys, ovals, errors, s)
+               : launch_scatter<float>(keys, vals, u, pg, grid, offsets, cursor, okeys, ovals, errors, s);
+}
+
 // One pass: histogram, scan, scatter.  sg describes the units' segments.
+// With ftot, the histogram also counts every row's final partition
+// (key >> fshift, Ff of them) into ftot (zeroed by the caller).
 cudaError_t partition_pass(const int32_t* keys, const void* vals, int dtype, const Units& u, const PassGeom& pg,
                            const ScanGeom& sg, int grid, int* counts, int* offsets, long long* ptot,
                            long long* pstart, long long* pcount, int32_t* okeys, void* ovals, unsigned* errors,
-                           cudaStream_t s) {
-    k_part_hist<<<grid, kPartThreads, (size_t)pg.B * 4, s>>>(keys, u, pg, counts, errors);
+                           cudaStream_t s, unsigned long long* ftot = nullptr, int fshift = 0, int Ff = 0) {
+    cudaError_t e = launch_hist(keys, u, pg, grid, counts, errors, ftot, fshift, Ff, s);
+    if (e != cudaSuccess) return e;
     const int sgrid = std::max(1, std::min(1024, (sg.F + 7) / 8));
     k_scan_totals<<<sgrid, 256, 0, s>>>(counts, sg, ptot);
-    k_scan_starts<<<1, 1024, 0, s>>>(ptot, sg.F, pstart, pcount);
+    k_scan_starts<<<1, 1024, 0, s>>>(ptot, sg.F, pstart, pcount, nullptr);
     k_scan_offsets<<<sgrid, 256, 0, s>>>(counts, sg, pstart, offsets);
-    count_launches(5);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    return dtype == REPRO_F64 ? launch_scatter<double>(keys, vals, u, pg, grid, offsets, okeys, ovals, errors, s)
-                              : launch_scatter<float>(keys, vals, u, pg, grid, offsets, okeys, ovals, errors, s);
+    count_launches(4);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    return launch_scatter_t(dtype, keys, vals, u, pg, grid, offsets, nullptr, okeys, ovals, errors, s);
 }
 
 }  // namespace
@@ -962,19 +995,27 @@ cudaError_t launch_groupby_partitioned(const int32_t* keys, const void* vals, lo
         long long* pstart1 = (long long*)(b + ly.pstart1);
         long long* pcount1 = (long long*)(b + ly.pcount1);
         const ScanGeom sg1{pp.F1, pp.F1, 1, pp.C, pp.C, nullptr, nullptr};
+        // the first histogram also counts the final partitions (key >> shift)
+        long long* ptot = (long long*)(b + ly.ptot);
+        if ((e = cudaMemsetAsync(ptot, 0, (size_t)pp.Fs * 8, s)) != cudaSuccess) return e;
         e = partition_pass(keys, vals, dtype, whole, pp.p1, sg1, pp.C, (int*)(b + ly.counts1), (int*)(b + ly.offsets1),
-                           (long long*)(b + ly.ptot1), pstart1, pcount1, akeys, avals, errors, s);
+                           (long long*)(b + ly.ptot1), pstart1, pcount1, akeys, avals, errors, s,
+                           reinterpret_cast<unsigned long long*>(ptot), pp.p2.shift, pp.Fs);
         if (e != cudaSuccess) return e;
         PartChunk* chunks = (PartChunk*)(b + ly.chunks);
-        int* cbase = (int*)(b + ly.cbase);
-        int* nunits = (int*)(b + ly.nunits);
-        k_seg_chunks<<<1, 1024, 0, s>>>(pstart1, pcount1, pp.F1, kChunkRows, chunks, cbase, nunits, ints + 3);
+        k_seg_chunks<<<1, 1024, 0, s>>>(pstart1, pcount1, pp.F1, kChunkRows, chunks, nullptr, nullptr, ints + 3);
+        count_launches(1);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        // so the fine pass needs no histogram of its own: the final
+        // partitions' starts and write cursors, then the chunks' rows
+        // scattered through the partitions' shared cursors
+        int* cursor = (int*)(b + ly.cursor);
+        k_scan_starts<<<1, 1024, 0, s>>>(ptot, pp.Fs, pstart, pcount, cursor);
         count_launches(1);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         const Units fine{0, 0, chunks, ints + 3, nullptr};
-        const ScanGeom sg2{pp.Fs, pp.F2, pp.F2, 1, 0, cbase, nunits};
-        e = partition_pass(akeys, avals, dtype, fine, pp.p2, sg2, pp.C, (int*)(b + ly.counts2), (int*)(b + ly.offsets2),
-                           (long long*)(b + ly.ptot), pstart, pcount, okeys, ovals, errors, s);
+        e = launch_scatter_t(dtype, akeys, avals, fine, pp.p2, pp.C, nullptr, cursor, okeys, ovals, errors, s);
+        count_launches(1);
     }
     prof_end(PROF_PARTITION, s);
     if (e != cudaSuccess) return e;
