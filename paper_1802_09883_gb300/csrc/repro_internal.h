@@ -126,7 +126,8 @@ struct BatchPartition {
 // the rule's); the tuner forces candidates on its own thread while it times
 // them.
 bool tune_lookup_fused(int dtype, int L, long long G, FusedPlanConfig& cfg);
-bool tune_lookup_shift(int dtype, int L, long long G, int& shift, int& levels);
+// cfg.S == 0: no measured aggregation configuration for that width
+bool tune_lookup_shift(int dtype, int L, long long G, int& shift, int& levels, FusedPlanConfig& cfg);
 const FusedPlanConfig* tune_forced_fused();
 int tune_forced_shift();   // 0: none
 int tune_forced_levels();  // 0: the rule's

@@ -925,9 +925,12 @@ bool partition_choose(int dtype, int L, long long G, PartChoice& pc) {
         levels = tune_forced_levels();
     } else {
         int tuned = 0, tuned_levels = 0;
-        if (tune_lookup_shift(dtype, L, G, tuned, tuned_levels) && shift_usable(dtype, L, G, tuned, pc.cfg)) {
+        FusedPlanConfig tuned_cfg{};
+        if (tune_lookup_shift(dtype, L, G, tuned, tuned_levels, tuned_cfg) &&
+            shift_usable(dtype, L, G, tuned, pc.cfg)) {
             shift = tuned;
             levels = tuned_levels;
+            if (tuned_cfg.S && fused_config_fits(dtype, L, 1 << tuned, kMetaSmemBytes, tuned_cfg)) pc.cfg = tuned_cfg;
         } else {
             // rule: the widest power-of-two slice whose table keeps two CTAs
             // per SM (then one), with at most kMaxParts partitions

@@ -23,6 +23,7 @@
 #include <vector>
 
 #include "repro.h"
+#include "multi_types.h"
 #include "repro_internal.h"
 
 namespace rp {
@@ -32,7 +33,13 @@ using Key = std::tuple<int, int, int>;  // dtype, L, ceil(log2 G)
 
 std::mutex g_mu;
 std::map<Key, FusedPlanConfig> g_fused;
-std::map<Key, std::pair<int, int>> g_shift;  // partition shift, levels
+// A partitioned choice: width, passes (0 = the rule's) and, when measured,
+// the aggregation kernel's configuration (S == 0: the rule's).
+struct PartTuned {
+    int shift, levels;
+    FusedPlanConfig cfg;
+};
+std::map<Key, PartTuned> g_shift;
 
 thread_local const FusedPlanConfig* t_force_fused = nullptr;
 thread_local int t_force_shift = 0;
@@ -101,13 +108,14 @@ bool tune_lookup_fused(int dtype, int L, long long G, FusedPlanConfig& cfg) {
     return true;
 }
 
-bool tune_lookup_shift(int dtype, int L, long long G, int& shift, int& levels) {
+bool tune_lookup_shift(int dtype, int L, long long G, int& shift, int& levels, FusedPlanConfig& cfg) {
     if (t_ignore_cache) return false;
     std::lock_guard<std::mutex> lk(g_mu);
     auto it = g_shift.find(key_of(dtype, L, G));
     if (it == g_shift.end()) return false;
-    shift = it->second.first;
-    levels = it->second.second;
+    shift = it->second.shift;
+    levels = it->second.levels;
+    cfg = it->second.cfg;
     return true;
 }
 
@@ -220,7 +228,7 @@ repro_status repro_tune_groupby(const int32_t* keys, const void* values, int64_t
         }
         double best = 0;
         PartChoice pick = def;
-        for (const PartChoice& pc : cands) {
+        auto time_choice = [&](const PartChoice& pc) -> double {
             auto run = [&]() -> cudaError_t {
                 cudaError_t e = launch_init_state(state, dtype, L, G, s);
                 return e == cudaSuccess
@@ -228,21 +236,63 @@ repro_status repro_tune_groupby(const int32_t* keys, const void* values, int64_t
                            : e;
             };
             const double ms = time_median(run, s, 3, err);
-            if (err != cudaSuccess) break;
-            ++out->candidates;
-            if (pc.shift == def.shift && pc.shift1 == def.shift1) out->default_ms = ms;
-            if (best == 0 || ms < best) {
-                best = ms;
-                pick = pc;
+            if (err == cudaSuccess) {
+                ++out->candidates;
+                if (best == 0 || ms < best) {
+                    best = ms;
+                    pick = pc;
+                }
             }
+            return ms;
+        };
+        // the partitioning first (with the rule's aggregation configuration)
+        for (const PartChoice& pc : cands) {
+            const double ms = time_choice(pc);
+            if (err != cudaSuccess) break;
+            if (pc.shift == def.shift && pc.shift1 == def.shift1) out->default_ms = ms;
+        }
+        // then the aggregation kernel's configuration for the chosen width
+        bool cfg_tuned = false;
+        std::vector<PartChoice> cfgs;
+        const PartChoice base = pick;
+        for (int S : {2, 3, 4})
+            for (int R : {1024, 2048})
+                for (int ncw : {8, 16})
+                    for (int cps : {1, 2, 3, 4}) {
+                        const FusedPlanConfig c{S, R, ncw, cps, 1};
+                        if (c.S == base.cfg.S && c.R == base.cfg.R && c.ncw == base.cfg.ncw &&
+                            c.ctas_per_sm == base.cfg.ctas_per_sm && c.copies == base.cfg.copies)
+                            continue;
+                        if (!fused_config_fits(dtype, L, 1 << base.shift, kMetaSmemBytes, c)) continue;
+                        PartChoice pc = base;
+                        pc.cfg = c;
+                        cfgs.push_back(pc);
+                    }
+        size_t need2 = need;
+        for (const PartChoice& pc : cfgs) need2 = std::max(need2, partitioned_scratch_bytes(pc, dtype, L, G, n));
+        if (err == cudaSuccess && need2 > need) {
+            cudaFree(scratch);
+            scratch = nullptr;
+            err = cudaMalloc(&scratch, need2);
+        }
+        for (const PartChoice& pc : cfgs) {
+            if (err != cudaSuccess) break;
+            const double before = best;
+            time_choice(pc);
+            if (best < before) cfg_tuned = true;
         }
         cleanup();
         if (err != cudaSuccess) return status_of(err);
         out->best_ms = best;
         out->partition_shift = pick.shift;
         out->partition_levels = levels_of(pick);
+        out->stages = pick.cfg.S;
+        out->tile_rows = pick.cfg.R;
+        out->consumer_warps = pick.cfg.ncw;
+        out->ctas_per_sm = pick.cfg.ctas_per_sm;
+        out->table_copies = pick.cfg.copies;
         std::lock_guard<std::mutex> lk(g_mu);
-        g_shift[key_of(dtype, L, G)] = {pick.shift, levels_of(pick)};
+        g_shift[key_of(dtype, L, G)] = PartTuned{pick.shift, levels_of(pick), cfg_tuned ? pick.cfg : FusedPlanConfig{}};
         return REPRO_OK;
     }
     out->path = 2;  // two-pass path: nothing to choose
@@ -254,15 +304,19 @@ repro_status repro_tune_save(const char* path) {
     FILE* f = fopen(path, "w");
     if (!f) return REPRO_EINVAL;
     std::lock_guard<std::mutex> lk(g_mu);
-    fprintf(f, "# repro tune cache v1: kind dtype L log2G values (part: shift levels)\n");
+    fprintf(f, "# repro tune cache v1: kind dtype L log2G values (part: shift levels [S R ncw cps copies])\n");
     for (const auto& kv : g_fused) {
         const FusedPlanConfig& c = kv.second;
         fprintf(f, "fused %d %d %d %d %d %d %d %d\n", std::get<0>(kv.first), std::get<1>(kv.first),
                 std::get<2>(kv.first), c.S, c.R, c.ncw, c.ctas_per_sm, c.copies);
     }
-    for (const auto& kv : g_shift)
-        fprintf(f, "part %d %d %d %d %d\n", std::get<0>(kv.first), std::get<1>(kv.first), std::get<2>(kv.first),
-                kv.second.first, kv.second.second);
+    for (const auto& kv : g_shift) {
+        const PartTuned& t = kv.second;
+        fprintf(f, "part %d %d %d %d %d", std::get<0>(kv.first), std::get<1>(kv.first), std::get<2>(kv.first),
+                t.shift, t.levels);
+        if (t.cfg.S) fprintf(f, " %d %d %d %d %d", t.cfg.S, t.cfg.R, t.cfg.ncw, t.cfg.ctas_per_sm, t.cfg.copies);
+        fprintf(f, "\n");
+    }
     return fclose(f) == 0 ? REPRO_OK : REPRO_EINVAL;
 }
 
@@ -271,22 +325,26 @@ repro_status repro_tune_load(const char* path) {
     FILE* f = fopen(path, "r");
     if (!f) return REPRO_EINVAL;
     std::map<Key, FusedPlanConfig> fused;
-    std::map<Key, std::pair<int, int>> shift;
+    std::map<Key, PartTuned> shift;
     char line[256];
     bool ok = true;
     while (ok && fgets(line, sizeof line, f)) {
         if (line[0] == '#' || line[0] == '\n') continue;
         char kind[16] = {};
-        int d, L, gb, a[5];
+        int d, L, gb, a[7];
         if (sscanf(line, "%15s", kind) != 1) continue;
         if (!strcmp(kind, "fused")) {
             ok = sscanf(line, "%*s %d %d %d %d %d %d %d %d", &d, &L, &gb, &a[0], &a[1], &a[2], &a[3], &a[4]) == 8;
             if (ok) fused[Key{d, L, gb}] = FusedPlanConfig{a[0], a[1], a[2], a[3], a[4]};
         } else if (!strcmp(kind, "part")) {
-            a[1] = 0;  // levels: optional, 0 = the rule's
-            ok = sscanf(line, "%*s %d %d %d %d %d", &d, &L, &gb, &a[0], &a[1]) >= 4 && a[0] >= 6 && a[0] <= 12 &&
-                 a[1] >= 0 && a[1] <= 2;
-            if (ok) shift[Key{d, L, gb}] = {a[0], a[1]};
+            // shift [levels (0 = the rule's) [S R ncw cps copies]]
+            int c[5] = {0, 0, 0, 0, 0};
+            a[1] = 0;
+            const int got = sscanf(line, "%*s %d %d %d %d %d %d %d %d %d %d", &d, &L, &gb, &a[0], &a[1], &c[0], &c[1],
+                                   &c[2], &c[3], &c[4]);
+            ok = (got == 4 || got == 5 || got == 10) && a[0] >= 6 && a[0] <= 12 && a[1] >= 0 && a[1] <= 2;
+            if (ok && got == 10) ok = c[0] >= 1 && c[1] >= 1 && c[2] >= 1 && c[3] >= 1 && c[4] >= 1;
+            if (ok) shift[Key{d, L, gb}] = PartTuned{a[0], a[1], FusedPlanConfig{c[0], c[1], c[2], c[3], c[4]}};
         } else {
             ok = false;
         }

@@ -76,3 +76,24 @@ def test_every_partition_choice_gives_identical_state(G, tmp_path):
             st = _state(keys, vals, G, 3)
             assert torch.equal(ref.tensor, st.tensor), (shift, levels)
     R.tune_clear()
+
+
+def test_partition_aggregation_configurations_give_identical_state(tmp_path):
+    """The aggregation kernel's configuration recorded with a partition
+    choice changes speed only."""
+    g = torch.Generator(device=DEV)
+    g.manual_seed(12)
+    G, n = 300_000, (1 << 22) + 1
+    keys = WL.uniform_keys(n, G, g, DEV)
+    vals = WL.random_values(n, -40, 40, g, DEV)
+    R.tune_clear()
+    ref = _state(keys, vals, G, 3)
+    bucket = (G - 1).bit_length()
+    f = tmp_path / "choice.txt"
+    for cfg in ["2 1024 8 1 1", "3 2048 16 1 1", "4 1024 8 2 1", "2 2048 8 3 1"]:
+        f.write_text(f"part 0 3 {bucket} 10 0 {cfg}\n")
+        R.tune_clear()
+        R.tune_load(str(f))
+        st = _state(keys, vals, G, 3)
+        assert torch.equal(ref.tensor, st.tensor), cfg
+    R.tune_clear()
