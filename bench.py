@@ -45,6 +45,8 @@ def parse():
     ap.add_argument("--dist", default="uniform", choices=["uniform", "zipf"])
     ap.add_argument("--L", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--oracle-threads", type=int, default=0,
+                    help="host threads of the CPU oracle (reference arm, cpu_baseline); 0: all cores")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-tune", action="store_true", help="skip the untimed autotuning before the warm-up")
     ap.add_argument("--verify", action="store_true", help="check sampled groups against the oracle")
@@ -839,8 +841,12 @@ def cpu_oracle_rate(G, dist, L, rows, threads):
     return rows / dt, dt
 
 
+def oracle_threads(args):
+    return args.oracle_threads if args.oracle_threads > 0 else (os.cpu_count() or 1)
+
+
 def cpu_baseline(args):
-    threads = os.cpu_count() or 1
+    threads = oracle_threads(args)
     rows = 1 << 22
     rate, dt = cpu_oracle_rate(args.G, args.dist, args.L, rows, threads)
     # grow the sample towards ~10 s of CPU work (threads x wall)
@@ -856,7 +862,7 @@ def cpu_baseline(args):
 def run_reference(args, rank):
     if rank != 0:
         return None
-    threads = os.cpu_count() or 1
+    threads = oracle_threads(args)
     from oracle import oracle as O
 
     O.build()
