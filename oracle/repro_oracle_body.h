@@ -46,8 +46,8 @@ static void ONAME(init)(OSTATE* st) {
     st->S[0] = ONAME(fresh)(0);
 }
 
-/* Algorithm 2, lines "check extractor validity": drop the last level, demote
-   the others, start a new first level one grid index higher. */
+/* Algorithm 2, its check of the extractor's validity: drop the last level,
+   demote the others, start a new first level one grid index higher. */
 static void ONAME(raise)(OSTATE* st, int L) {
     OT top = st->S[0];
     for (int l = L - 1; l >= 1; --l) {

@@ -1,24 +1,27 @@
 // repro_partition.cu -- grouped SUM for group counts beyond one shared-memory
-// table: partition the rows by key range first (Algorithm 4, line 1:
+// table: partition the rows by key range first (Algorithm 4's
 // ParallelPartition on the key with fan-out F), then aggregate every
 // partition as its own task with the multi-task single-pass kernel, each
 // owning a disjoint slice of the caller's state (Algorithm 4's private
 // tables; the slices make the merge into the shared table a plain write).
 //
-// Up to 64 partitions the rows are partitioned in one pass.  Beyond that a
-// single pass would write runs of only a few rows per partition per tile
-// (scattered stores), so the rows are partitioned twice, as the paper's
-// multi-pass radix partitioning does for large fan-outs: a coarse pass by the
-// high key bits, then, inside every coarse partition, a fine pass by the
-// next bits.  Each pass:
+// Up to 64 partitions the rows are partitioned in one pass (a measured
+// choice may take one pass up to 2048).  Beyond that a single pass would
+// write runs of only a few rows per partition per tile (scattered stores),
+// so the rows are partitioned twice, as the paper's multi-pass radix
+// partitioning does for large fan-outs: a coarse pass by the high key bits,
+// then, inside every coarse partition, a fine pass by the next bits.  A pass:
 //
-//   k_part_hist     per unit (a CTA's chunk of rows, or a chunk of one
-//                   coarse partition), rows per bucket (and bad keys)
+//   k_part_hist     per unit (a CTA's chunk of rows), rows per bucket (and
+//                   bad keys); before two passes also every row's final
+//                   partition, so that the fine pass needs no histogram
 //   k_scan_totals / k_scan_starts / k_scan_offsets
 //                   partition totals, 4-row-aligned partition starts (for the
 //                   TMA copies) and every unit's write cursor per bucket
 //   k_part_scatter  copy every row to its partition, tile by tile sorted in
-//                   shared memory so that stores are coalesced runs (row
+//                   shared memory so that stores are coalesced runs, the
+//                   next tile arriving by TMA meanwhile; the fine pass
+//                   reserves its runs from per-partition shared cursors (row
 //                   order inside a partition does not matter: the sum is
 //                   exact)
 //
@@ -538,22 +541,6 @@ __global__ void __launch_bounds__(1024) k_seg_chunks(const long long* __restrict
     if (threadIdx.x == 0) *nchunks = s_w[32];
 }
 
-// Four consecutive values from a 16-byte aligned address.
-template <typename T>
-struct Vec4 {
-    T v[4];
-};
-
-__device__ __forceinline__ Vec4<double> load_vec4(const double* p) {
-    const double2 a = reinterpret_cast<const double2*>(p)[0], b = reinterpret_cast<const double2*>(p)[1];
-    return Vec4<double>{{a.x, a.y, b.x, b.y}};
-}
-
-__device__ __forceinline__ Vec4<float> load_vec4(const float* p) {
-    const float4 a = *reinterpret_cast<const float4*>(p);
-    return Vec4<float>{{a.x, a.y, a.z, a.w}};
-}
-
 // Per group of every final partition its window: the largest K(b) over its
 // finite values (the window of Algorithm 2 / the max-abs pre-pass, computed
 // per partition; -1 where the group has none).  Work comes as chunks of one
@@ -579,11 +566,13 @@ __global__ void __launch_bounds__(512) k_part_window(const int32_t* __restrict__
             const Split sp = split_value(v);
             if (!sp.flag && sp.mant != 0 && s_win[k] < sp.kb) atomicMax(&s_win[k], sp.kb);
         };
-        auto see4 = [&](const int4 k, const Vec4<T>& v) {
-            see(k.x, v.v[0]);
-            see(k.y, v.v[1]);
-            see(k.z, v.v[2]);
-            see(k.w, v.v[3]);
+        auto see4 = [&](const int4 k, const T* p) {  // p: four values, 16-byte aligned
+            T v[4];
+            RowQuad<T>::load(p, v);
+            see(k.x, v[0]);
+            see(k.y, v[1]);
+            see(k.z, v[2]);
+            see(k.w, v[3]);
         };
         const long long n4 = ch.beg + ((ch.end - ch.beg) & ~3ll);
         const long long step = 4ll * blockDim.x;
@@ -591,11 +580,19 @@ __global__ void __launch_bounds__(512) k_part_window(const int32_t* __restrict__
         for (; r + step < n4; r += 2 * step) {
             const int4 ka = *reinterpret_cast<const int4*>(okeys + r);
             const int4 kb = *reinterpret_cast<const int4*>(okeys + r + step);
-            const Vec4<T> va = load_vec4(ovals + r), vb = load_vec4(ovals + r + step);
-            see4(ka, va);
-            see4(kb, vb);
+            T va[4], vb[4];
+            RowQuad<T>::load(ovals + r, va);
+            RowQuad<T>::load(ovals + r + step, vb);
+            see(ka.x, va[0]);
+            see(ka.y, va[1]);
+            see(ka.z, va[2]);
+            see(ka.w, va[3]);
+            see(kb.x, vb[0]);
+            see(kb.y, vb[1]);
+            see(kb.z, vb[2]);
+            see(kb.w, vb[3]);
         }
-        if (r < n4) see4(*reinterpret_cast<const int4*>(okeys + r), load_vec4(ovals + r));
+        if (r < n4) see4(*reinterpret_cast<const int4*>(okeys + r), ovals + r);
         for (long long t = n4 + threadIdx.x; t < ch.end; t += blockDim.x) see(okeys[t], ovals[t]);
         __syncthreads();
         int* w = win + (size_t)ch.seg * Gp;
