@@ -455,8 +455,9 @@ repro_status repro_server_destroy(repro_server srv);
  * (Sec. V-C, Sec. VI).  repro_tune_groupby times every configuration that
  * fits on the caller's inputs -- for the single-pass path its stages, rows
  * per tile, consumer warps, CTAs per SM and table copies; for the
- * partitioned path its partition width (fan-out) and the number of
- * partition passes -- and records the fastest
+ * partitioned path its partition width (fan-out), the number of partition
+ * passes, the aggregation kernel's configuration and its work items per CTA
+ * -- and records the fastest
  * for (dtype, L, num_groups rounded up to a power of two); later calls in that
  * bucket use it.  It allocates its own state and scratch, runs each
  * candidate a few times on `stream` and synchronises; the inputs are only
@@ -472,7 +473,7 @@ typedef struct {
     double best_ms;          /* median time of one call with the choice */
     double default_ms;       /* the same with the built-in rule's choice */
     int32_t partition_levels; /* partitioned choice: partition passes over the rows (1 or 2) */
-    int32_t reserved;
+    int32_t partition_items_per_cta; /* partitioned choice: work items per CTA (0: the built-in default) */
 } repro_tune_result;
 
 repro_status repro_tune_groupby(const int32_t* keys, const void* values, int64_t n, repro_dtype dtype, int L,

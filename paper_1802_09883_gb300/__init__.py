@@ -466,7 +466,8 @@ class _TuneResult(ctypes.Structure):
     _fields_ = [("path", ctypes.c_int32), ("candidates", ctypes.c_int32), ("stages", ctypes.c_int32),
                 ("tile_rows", ctypes.c_int32), ("consumer_warps", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32),
                 ("table_copies", ctypes.c_int32), ("partition_shift", ctypes.c_int32), ("best_ms", ctypes.c_double),
-                ("default_ms", ctypes.c_double), ("partition_levels", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("default_ms", ctypes.c_double), ("partition_levels", ctypes.c_int32),
+                ("partition_items_per_cta", ctypes.c_int32)]
 
 
 def tune(keys: torch.Tensor, values: torch.Tensor, num_groups: int, L: int = 3) -> dict:
@@ -478,7 +479,7 @@ def tune(keys: torch.Tensor, values: torch.Tensor, num_groups: int, L: int = 3) 
     r = _TuneResult()
     _check(lib().repro_tune_groupby(keys.data_ptr(), values.data_ptr(), keys.numel(), _dtype_code(values.dtype), L,
                                     num_groups, _stream(values.device), ctypes.byref(r)), "repro_tune_groupby")
-    out = {name: getattr(r, name) for name, _ in _TuneResult._fields_ if name != "reserved"}
+    out = {name: getattr(r, name) for name, _ in _TuneResult._fields_}
     out["path"] = ("single_pass", "partitioned", "two_pass")[r.path]
     return out
 

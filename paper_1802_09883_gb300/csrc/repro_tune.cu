@@ -38,6 +38,7 @@ std::map<Key, FusedPlanConfig> g_fused;
 struct PartTuned {
     int shift, levels;
     FusedPlanConfig cfg;
+    int ipc;  // work items per CTA, 0: the built-in default
 };
 std::map<Key, PartTuned> g_shift;
 
@@ -108,7 +109,7 @@ bool tune_lookup_fused(int dtype, int L, long long G, FusedPlanConfig& cfg) {
     return true;
 }
 
-bool tune_lookup_shift(int dtype, int L, long long G, int& shift, int& levels, FusedPlanConfig& cfg) {
+bool tune_lookup_shift(int dtype, int L, long long G, int& shift, int& levels, FusedPlanConfig& cfg, int& ipc) {
     if (t_ignore_cache) return false;
     std::lock_guard<std::mutex> lk(g_mu);
     auto it = g_shift.find(key_of(dtype, L, G));
@@ -116,6 +117,7 @@ bool tune_lookup_shift(int dtype, int L, long long G, int& shift, int& levels, F
     shift = it->second.shift;
     levels = it->second.levels;
     cfg = it->second.cfg;
+    ipc = it->second.ipc;
     return true;
 }
 
@@ -281,6 +283,26 @@ repro_status repro_tune_groupby(const int32_t* keys, const void* values, int64_t
             time_choice(pc);
             if (best < before) cfg_tuned = true;
         }
+        // then the work items per CTA for the chosen width and configuration
+        bool ipc_tuned = false;
+        {
+            const PartChoice base2 = pick;
+            for (int ipc : {1, 4, 8}) {
+                if (err != cudaSuccess) break;
+                PartChoice pc = base2;
+                pc.ipc = ipc;
+                const size_t nb = partitioned_scratch_bytes(pc, dtype, L, G, n);
+                if (nb > need2) {
+                    cudaFree(scratch);
+                    scratch = nullptr;
+                    if ((err = cudaMalloc(&scratch, nb)) != cudaSuccess) break;
+                    need2 = nb;
+                }
+                const double before = best;
+                time_choice(pc);
+                if (best < before) ipc_tuned = true;
+            }
+        }
         cleanup();
         if (err != cudaSuccess) return status_of(err);
         out->best_ms = best;
@@ -291,8 +313,11 @@ repro_status repro_tune_groupby(const int32_t* keys, const void* values, int64_t
         out->consumer_warps = pick.cfg.ncw;
         out->ctas_per_sm = pick.cfg.ctas_per_sm;
         out->table_copies = pick.cfg.copies;
+        out->partition_items_per_cta = pick.ipc;
         std::lock_guard<std::mutex> lk(g_mu);
-        g_shift[key_of(dtype, L, G)] = PartTuned{pick.shift, levels_of(pick), cfg_tuned ? pick.cfg : FusedPlanConfig{}};
+        g_shift[key_of(dtype, L, G)] = PartTuned{pick.shift, levels_of(pick),
+                                                 cfg_tuned || ipc_tuned ? pick.cfg : FusedPlanConfig{},
+                                                 ipc_tuned ? pick.ipc : 0};
         return REPRO_OK;
     }
     out->path = 2;  // two-pass path: nothing to choose
@@ -304,7 +329,7 @@ repro_status repro_tune_save(const char* path) {
     FILE* f = fopen(path, "w");
     if (!f) return REPRO_EINVAL;
     std::lock_guard<std::mutex> lk(g_mu);
-    fprintf(f, "# repro tune cache v1: kind dtype L log2G values (part: shift levels [S R ncw cps copies])\n");
+    fprintf(f, "# repro tune cache v1: kind dtype L log2G values (part: shift levels [S R ncw cps copies [ipc]])\n");
     for (const auto& kv : g_fused) {
         const FusedPlanConfig& c = kv.second;
         fprintf(f, "fused %d %d %d %d %d %d %d %d\n", std::get<0>(kv.first), std::get<1>(kv.first),
@@ -315,6 +340,7 @@ repro_status repro_tune_save(const char* path) {
         fprintf(f, "part %d %d %d %d %d", std::get<0>(kv.first), std::get<1>(kv.first), std::get<2>(kv.first),
                 t.shift, t.levels);
         if (t.cfg.S) fprintf(f, " %d %d %d %d %d", t.cfg.S, t.cfg.R, t.cfg.ncw, t.cfg.ctas_per_sm, t.cfg.copies);
+        if (t.cfg.S && t.ipc) fprintf(f, " %d", t.ipc);
         fprintf(f, "\n");
     }
     return fclose(f) == 0 ? REPRO_OK : REPRO_EINVAL;
@@ -337,14 +363,17 @@ repro_status repro_tune_load(const char* path) {
             ok = sscanf(line, "%*s %d %d %d %d %d %d %d %d", &d, &L, &gb, &a[0], &a[1], &a[2], &a[3], &a[4]) == 8;
             if (ok) fused[Key{d, L, gb}] = FusedPlanConfig{a[0], a[1], a[2], a[3], a[4]};
         } else if (!strcmp(kind, "part")) {
-            // shift [levels (0 = the rule's) [S R ncw cps copies]]
+            // shift [levels (0 = the rule's) [S R ncw cps copies [items per CTA]]]
             int c[5] = {0, 0, 0, 0, 0};
+            int ipc = 0;
             a[1] = 0;
-            const int got = sscanf(line, "%*s %d %d %d %d %d %d %d %d %d %d", &d, &L, &gb, &a[0], &a[1], &c[0], &c[1],
-                                   &c[2], &c[3], &c[4]);
-            ok = (got == 4 || got == 5 || got == 10) && a[0] >= 6 && a[0] <= 12 && a[1] >= 0 && a[1] <= 2;
-            if (ok && got == 10) ok = c[0] >= 1 && c[1] >= 1 && c[2] >= 1 && c[3] >= 1 && c[4] >= 1;
-            if (ok) shift[Key{d, L, gb}] = PartTuned{a[0], a[1], FusedPlanConfig{c[0], c[1], c[2], c[3], c[4]}};
+            const int got = sscanf(line, "%*s %d %d %d %d %d %d %d %d %d %d %d", &d, &L, &gb, &a[0], &a[1], &c[0],
+                                   &c[1], &c[2], &c[3], &c[4], &ipc);
+            ok = (got == 4 || got == 5 || got == 10 || got == 11) && a[0] >= 6 && a[0] <= 12 && a[1] >= 0 &&
+                 a[1] <= 2;
+            if (ok && got >= 10) ok = c[0] >= 1 && c[1] >= 1 && c[2] >= 1 && c[3] >= 1 && c[4] >= 1;
+            if (ok && got == 11) ok = ipc >= 1 && ipc <= 64;
+            if (ok) shift[Key{d, L, gb}] = PartTuned{a[0], a[1], FusedPlanConfig{c[0], c[1], c[2], c[3], c[4]}, ipc};
         } else {
             ok = false;
         }

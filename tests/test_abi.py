@@ -73,7 +73,7 @@ def test_tune_cache_round_trip_and_rejects_malformed(tmp_path):
     import paper_1802_09883_gb300 as R
     good = tmp_path / "tune.txt"
     good.write_text("# a comment\nfused 0 3 10 3 2048 8 2 1\npart 0 3 20 11\nfused 1 2 5 2 1024 8 2 32\n"
-                    "part 0 3 24 12 1\npart 1 2 18 9 2 3 2048 16 1 1\n")
+                    "part 0 3 24 12 1\npart 1 2 18 9 2 3 2048 16 1 1\npart 0 2 17 10 1 2 1024 8 2 1 4\n")
     R.tune_clear()
     R.tune_load(str(good))
     out = tmp_path / "out.txt"
@@ -82,7 +82,7 @@ def test_tune_cache_round_trip_and_rejects_malformed(tmp_path):
     # a partition line without its pass count (levels) reads as 0: the rule's
     # ... and one with the aggregation configuration keeps it
     assert lines == sorted(["fused 0 3 10 3 2048 8 2 1", "part 0 3 20 11 0", "fused 1 2 5 2 1024 8 2 32",
-                            "part 0 3 24 12 1", "part 1 2 18 9 2 3 2048 16 1 1"])
+                            "part 0 3 24 12 1", "part 1 2 18 9 2 3 2048 16 1 1", "part 0 2 17 10 1 2 1024 8 2 1 4"])
     bad = tmp_path / "bad.txt"
     bad.write_text("fused 0 3 10 3 2048\n")
     with pytest.raises(R.ReproError):
@@ -94,6 +94,9 @@ def test_tune_cache_round_trip_and_rejects_malformed(tmp_path):
     with pytest.raises(R.ReproError):
         R.tune_load(str(bad))
     bad.write_text("part 0 3 20 11 2 3 2048\n")  # a partial configuration
+    with pytest.raises(R.ReproError):
+        R.tune_load(str(bad))
+    bad.write_text("part 0 3 20 11 2 3 2048 8 2 1 0\n")  # zero work items per CTA
     with pytest.raises(R.ReproError):
         R.tune_load(str(bad))
     R.tune_clear()
