@@ -16,6 +16,8 @@ struct MTask {
     unsigned char* hdr;   // the state's header (checks, error word)
     unsigned char* recs;  // the task's first group record
     const int* win;       // per group its window (K of its largest |value|, -1: none), or null
+    int hint;             // 1: win is only a lower bound, raised by every item of the task at its end
+    int pad;
 };
 
 struct MItem {
@@ -46,6 +48,8 @@ struct StageMeta {
     const int32_t* keys;  // the task's key and value columns at row0
     const void* vals;
     const int* win;       // the task's preset windows, or null
+    int hint;             // win is a lower bound that other CTAs raise meanwhile
+    int pad;
 };
 
 // Shared memory the multi-task kernel reserves for its stage records (S <= 8).

@@ -97,10 +97,12 @@ __device__ __forceinline__ void shift_levels(__int128 (&v)[L], int d) {
 // window and their low levels dropped (operator+=(repro)); with `overwrite`
 // the old content is ignored.  Clears the table for the next item.  Each
 // thread takes NB groups at a time and reads their old records before it
-// writes any, so that NB record reads are in flight instead of one.
+// writes any, so that NB record reads are in flight instead of one.  With
+// `hint`, every window the table reached is also raised there for the
+// task's later items.
 template <int L>
 __device__ void flush_table(unsigned char* recs, int G, const Table& t, int* sK, int* sKp, unsigned* sF,
-                            bool overwrite, int ctid, int NC) {
+                            bool overwrite, int ctid, int NC, int* hint) {
     constexpr size_t rec = 8 + 16 * L;
     constexpr int NB = 2;
     for (int g0 = ctid; g0 < G; g0 += NB * NC) {
@@ -130,6 +132,7 @@ __device__ void flush_table(unsigned char* recs, int G, const Table& t, int* sK,
             unsigned char* r = recs + (size_t)g * rec;
             long long* pb = reinterpret_cast<long long*>(r + 8);
             const int Kt = sK[g];
+            if (hint && Kt >= 0) atomicMax(&hint[g], Kt);
             const int Kr = overwrite ? Kt : Ks[b];
             const int K = max(Kt, Kr);
             // table levels (all copies), aligned to K
@@ -254,6 +257,7 @@ __global__ void __launch_bounds__(32 * (NCW + 1)) k_fused_multi(MultiArgs a, int
                         sm.keys = nullptr;
                         sm.vals = nullptr;
                         sm.win = nullptr;
+                        sm.hint = 0;
                     } else {
                         sm.item = w;
                         sm.row0 = it.row0 + t * R;
@@ -265,6 +269,7 @@ __global__ void __launch_bounds__(32 * (NCW + 1)) k_fused_multi(MultiArgs a, int
                         sm.keys = tk.keys + sm.row0;
                         sm.vals = reinterpret_cast<const T*>(tk.vals) + sm.row0;
                         sm.win = tk.win;
+                        sm.hint = tk.hint;
                     }
                     meta[s] = sm;
                     const uint32_t kb = (uint32_t)sm.rows_tma * 4, vb = (uint32_t)sm.rows_tma * sizeof(T);
@@ -301,8 +306,15 @@ __global__ void __launch_bounds__(32 * (NCW + 1)) k_fused_multi(MultiArgs a, int
         const StageMeta sm = meta[s];
         if (sm.item < 0) break;
         const int G = sm.G;
-        if (sm.win && sm.first) {  // known windows: no row of the item raises one
-            for (int g = ctid; g < G; g += NC) sK[g] = sKp[g] = __ldg(&sm.win[g]);
+        if (sm.win && sm.first) {
+            // exact windows (no row of the item raises one), or a lower bound
+            // that earlier items of the task left (few rows raise one): either
+            // is at most the group's final window, which is all a window
+            // needs (a digit does not depend on the window it is taken in)
+            if (sm.hint)
+                for (int g = ctid; g < G; g += NC) sK[g] = sKp[g] = *reinterpret_cast<const volatile int*>(sm.win + g);
+            else
+                for (int g = ctid; g < G; g += NC) sK[g] = sKp[g] = __ldg(&sm.win[g]);
             named_bar_sync(1, NC);
         }
         int* cnt = &ctl[2 * (tcount % 3)];
@@ -341,7 +353,8 @@ __global__ void __launch_bounds__(32 * (NCW + 1)) k_fused_multi(MultiArgs a, int
             if (ctid == 0 && !hdr_ok) atomicOr(errors, REPRO_ERR_LAYOUT);
             unsigned char* dst = it.excl ? tk.recs : a.partials + (size_t)it.part * rec_bytes(L);
             if (hdr_ok || !it.excl)
-                flush_table<L>(dst, G, tab, sK, sKp, sF, !it.excl, ctid, NC);
+                flush_table<L>(dst, G, tab, sK, sKp, sF, !it.excl, ctid, NC,
+                               tk.hint ? const_cast<int*>(tk.win) : nullptr);
             else
                 clear_table<L>(G, tab, sK, sKp, sF, ctid, NC);
             named_bar_sync(1, NC);
@@ -535,7 +548,7 @@ repro_status plan_batch_host(const repro_task* tasks, int ntasks, int dtype, int
     for (int t = 0; t < ntasks; ++t)
         H.tasks[t] = MTask{tasks[t].keys, tasks[t].values, tasks[t].n, (int)tasks[t].num_groups,
                            (int)tasks[t].num_groups, (unsigned char*)tasks[t].state,
-                           (unsigned char*)tasks[t].state + sizeof(repro_state_header), nullptr};
+                           (unsigned char*)tasks[t].state + sizeof(repro_state_header), nullptr, 0, 0};
     if (fast.empty()) return REPRO_OK;
     if (fixed_cfg) {
         if (!fused_config_fits(dtype, L, (int)gcap, kMetaSmemBytes, *fixed_cfg)) return REPRO_ERANGE;

@@ -68,12 +68,15 @@ cudaError_t launch_groupby_fused(const int32_t* keys, const void* vals, long lon
 
 // Large group counts: partition by key range, then the multi-task kernel
 // over the partitions (repro_partition.cu).  A choice fixes the partition
-// width 2^shift, the coarse width 2^shift1 of a first pass (0: one pass) and
-// the multi-task kernel's configuration.
+// width 2^shift, the coarse width 2^shift1 of a first pass (0: one pass),
+// the multi-task kernel's configuration and the work items per CTA it aims
+// at (0: the built-in default).  More items balance the CTAs' ends better;
+// fewer restart each CTA's table (and its windows) less often.
 struct PartChoice {
-    int shift;
-    int shift1;
-    FusedPlanConfig cfg;
+    int shift = 0;
+    int shift1 = 0;
+    FusedPlanConfig cfg{};
+    int ipc = 0;
 };
 bool partition_choose(int dtype, int L, long long G, PartChoice& pc);
 bool partitioned_supported(int dtype, int L, long long G, long long n, const void* keys, const void* vals);
@@ -126,8 +129,9 @@ struct BatchPartition {
 // the rule's); the tuner forces candidates on its own thread while it times
 // them.
 bool tune_lookup_fused(int dtype, int L, long long G, FusedPlanConfig& cfg);
-// cfg.S == 0: no measured aggregation configuration for that width
-bool tune_lookup_shift(int dtype, int L, long long G, int& shift, int& levels, FusedPlanConfig& cfg);
+// cfg.S == 0: no measured aggregation configuration for that width; ipc 0:
+// no measured items per CTA
+bool tune_lookup_shift(int dtype, int L, long long G, int& shift, int& levels, FusedPlanConfig& cfg, int& ipc);
 const FusedPlanConfig* tune_forced_fused();
 int tune_forced_shift();   // 0: none
 int tune_forced_levels();  // 0: the rule's

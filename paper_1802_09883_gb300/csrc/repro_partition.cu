@@ -52,11 +52,12 @@ constexpr int kMaxParts = 8192;          // final partitions
 constexpr int kOneLevelParts = 64;       // beyond this the rule takes two passes
 constexpr int kOneLevelMaxParts = 2048;  // one pass at most this wide
 constexpr long long kChunkRows = 32768;  // rows per unit of the fine pass
-// Work items per CTA the aggregation aims at: items are taken largest first
-// from a shared counter, so with about this many per CTA the last round
-// leaves few SMs idle; a partition longer than an item is split into several
-// (partial tables, merged afterwards).
-constexpr long long kItemsPerCta = 8;
+// Work items per CTA the aggregation aims at by default: items come from a
+// shared counter, so with several per CTA the last round leaves few SMs
+// idle; but every item restarts the CTA's table and windows (first touches
+// and raises again), and a partition longer than an item is split into
+// several (partial tables, merged afterwards).  The tuner measures 1-8.
+constexpr long long kItemsPerCta = 2;
 
 // Geometry of one partition pass: a row with key k goes to bucket
 // (k >> shift) & bmask and is written with key k & kmask.
@@ -647,7 +648,7 @@ __global__ void __launch_bounds__(1024) k_part_plan(const long long* __restrict_
                                                     const long long* __restrict__ pcount, PartGeom pg, int G, int R,
                                                     long long tpi, const int32_t* okeys, const void* ovals,
                                                     size_t vsize, unsigned char* hdr, int L,
-                                                    const int* __restrict__ win, const PartTask* __restrict__ tt,
+                                                    const int* win, int win_hint, const PartTask* __restrict__ tt,
                                                     int B, MTask* __restrict__ tasks, MItem* __restrict__ items,
                                                     int* nitems, MergeBlk* __restrict__ blks, int* nblks) {
     __shared__ long long s_it[1024], s_pt[1024], s_bk[1024];
@@ -705,6 +706,8 @@ __global__ void __launch_bounds__(1024) k_part_plan(const long long* __restrict_
         t.hdr = h;
         t.recs = h + sizeof(repro_state_header) + (size_t)j * pg.Gp * rec;
         t.win = win ? win + (size_t)p * pg.Gp : nullptr;
+        t.hint = win ? win_hint : 0;
+        t.pad = 0;
         tasks[p] = t;
         const long long nit = Gp == 0 ? 0 : part_items(cnt, R, tpi);
         const long long tiles = (cnt + R - 1) / R;
@@ -797,7 +800,8 @@ bool make_part_plan(const PartChoice& pc, int L, long long G, long long n, PartP
     pp.ctas = di.sms * pc.cfg.ctas_per_sm;
     const long long R = pc.cfg.R;
     const long long total_tiles = (n + R - 1) / R + F;
-    pp.tpi = std::max(8ll, (total_tiles + kItemsPerCta * pp.ctas - 1) / (kItemsPerCta * pp.ctas));
+    const long long ipc = pc.ipc > 0 ? pc.ipc : kItemsPerCta;
+    pp.tpi = std::max(8ll, (total_tiles + ipc * pp.ctas - 1) / (ipc * pp.ctas));
     pp.tpi = std::min(pp.tpi, (1ll << 23) / R);
     pp.max_items = total_tiles / pp.tpi + F + 1;
     const long long max_split = std::min(F, total_tiles / pp.tpi + 1);
@@ -849,10 +853,8 @@ PartScratch part_scratch_layout(const PartPlan& pp, long long n, int dtype, int 
     take(s.ptot, (size_t)pp.Fs * 8);
     take(s.pstart, (size_t)pp.Fs * 8);
     take(s.pcount, (size_t)pp.Fs * 8);
-    if (pp.windows) {
-        take(s.win, (size_t)pp.F * pp.Gp * 4);
-        take(s.wchunks, (size_t)pp.max_wchunks * sizeof(PartChunk));
-    }
+    take(s.win, (size_t)pp.F * pp.Gp * 4);  // exact windows, or their lower bounds
+    if (pp.windows) take(s.wchunks, (size_t)pp.max_wchunks * sizeof(PartChunk));
     take(s.tasks, (size_t)pp.F * sizeof(MTask));
     take(s.items, (size_t)pp.max_items * sizeof(MItem));
     take(s.blks, (size_t)std::max(1ll, pp.max_blks) * sizeof(MergeBlk));
@@ -917,17 +919,19 @@ bool partition_choose(int dtype, int L, long long G, PartChoice& pc) {
     // forced by the tuner (this thread) > tuned cache > rule; each only if usable
     int forced = tune_forced_shift();
     int shift = 0, levels = 0;
+    pc.ipc = 0;
     if (forced && shift_usable(dtype, L, G, forced, pc.cfg)) {
         shift = forced;
         levels = tune_forced_levels();
     } else {
-        int tuned = 0, tuned_levels = 0;
+        int tuned = 0, tuned_levels = 0, tuned_ipc = 0;
         FusedPlanConfig tuned_cfg{};
-        if (tune_lookup_shift(dtype, L, G, tuned, tuned_levels, tuned_cfg) &&
+        if (tune_lookup_shift(dtype, L, G, tuned, tuned_levels, tuned_cfg, tuned_ipc) &&
             shift_usable(dtype, L, G, tuned, pc.cfg)) {
             shift = tuned;
             levels = tuned_levels;
             if (tuned_cfg.S && fused_config_fits(dtype, L, 1 << tuned, kMetaSmemBytes, tuned_cfg)) pc.cfg = tuned_cfg;
+            pc.ipc = tuned_ipc;
         } else {
             // rule: the widest power-of-two slice whose table keeps two CTAs
             // per SM (then one), with at most kMaxParts partitions
@@ -1019,11 +1023,14 @@ cudaError_t launch_groupby_partitioned(const int32_t* keys, const void* vals, lo
     }
     prof_end(PROF_PARTITION, s);
     if (e != cudaSuccess) return e;
-    int* win = nullptr;
+    // every group's window: exact from a window pass when groups are sparse,
+    // else a lower bound the task's items raise as they end (later items of
+    // a split partition then start near their groups' windows)
+    int* win = (int*)(b + ly.win);
+    const int win_hint = pp.windows ? 0 : 1;
+    if ((e = cudaMemsetAsync(win, 0xff, (size_t)pp.F * pp.Gp * 4, s)) != cudaSuccess) return e;  // -1: none yet
     if (pp.windows) {
-        win = (int*)(b + ly.win);
         PartChunk* wch = (PartChunk*)(b + ly.wchunks);
-        if ((e = cudaMemsetAsync(win, 0xff, (size_t)pp.F * pp.Gp * 4, s)) != cudaSuccess) return e;  // -1
         k_seg_chunks<<<1, 1024, 0, s>>>(pstart, pcount, pp.F, kWindowChunkRows, wch, nullptr, nullptr, ints + 4);
         const int grid = device_info().sms * 4;
         const size_t smem = (size_t)pp.Gp * 4;
@@ -1038,7 +1045,7 @@ cudaError_t launch_groupby_partitioned(const int32_t* keys, const void* vals, lo
     }
     PartGeom pg{pp.F, pc.shift, pp.Gp};
     k_part_plan<<<1, 1024, 0, s>>>(pstart, pcount, pg, (int)G, pp.cfg.R, pp.tpi, okeys, ovals,
-                                   dtype == REPRO_F64 ? 8 : 4, (unsigned char*)state, L, win, nullptr, 0,
+                                   dtype == REPRO_F64 ? 8 : 4, (unsigned char*)state, L, win, win_hint, nullptr, 0,
                                    (MTask*)(b + ly.tasks),
                                    (MItem*)(b + ly.items), ints, (MergeBlk*)(b + ly.blks), ints + 1);
     count_launches(1);
@@ -1212,7 +1219,7 @@ cudaError_t BatchPartition::launch(void* scratch, cudaStream_t s) const {
     if (e != cudaSuccess) return e;
     const PartGeom geo{P.F, P.pc.shift, P.Gp};
     k_part_plan<<<1, 1024, 0, s>>>(pstart, pcount, geo, 0, P.pc.cfg.R, P.tpi, okeys, ovals,
-                                   P.dtype == REPRO_F64 ? 8 : 4, nullptr, P.L, nullptr,
+                                   P.dtype == REPRO_F64 ? 8 : 4, nullptr, P.L, nullptr, 0,
                                    (const PartTask*)(b + P.ly.ptask), P.B, (MTask*)(b + P.ly.tasks),
                                    (MItem*)(b + P.ly.items), ints, (MergeBlk*)(b + P.ly.blks), ints + 1);
     count_launches(1);
