@@ -453,6 +453,11 @@ def run_multicol(args, local_rank):
     states = [R.State(G, L, dt, device=dev) for _ in colsl]
     outs = [torch.empty(G, dtype=dt, device=dev) for _ in colsl]
     stream = torch.cuda.current_stream(dev)
+    # group ids as the per-column path forms them (baselines and tuning, untimed)
+    gid = (k1.to(torch.int32) * 2 + k2.to(torch.int32)).contiguous()
+    tuned = None
+    if not args.no_tune:  # the per-column passes use the choice for 4 groups
+        tuned = R.tune(gid, colsl[0], G, L)
 
     def step():
         for st in states:
@@ -474,7 +479,6 @@ def run_multicol(args, local_rank):
     launches = lib.repro_launch_count() - l0
     prof = _prof_stop(lib)
     # conventional GroupBy on the same rows (group ids precomputed, untimed)
-    gid = (k1.to(torch.int32) * 2 + k2.to(torch.int32)).contiguous()
     fp_outs = [torch.empty(G, dtype=dt, device=dev) for _ in colsl]
     fp = R.groupby_sum_fp64 if dt == torch.float64 else R.groupby_sum_fp32
 
@@ -542,7 +546,7 @@ def run_multicol(args, local_rank):
                                      "ms_per_step": dec_ms, "repro_over_decimal_time": ms / dec_ms},
                 "e2e": {"value": n / (e2e_ms / 1e3), "unit": "rows/s", "h2d_bytes_per_step": n * (2 + 4 * esz),
                         "d2h_bytes_per_step": 4 * G * esz, "ms_per_step": e2e_ms},
-                "gpu_launches": int(launches), "clocks": clocks.summary()})
+                "gpu_launches": int(launches), "clocks": clocks.summary(), "tuned": tuned})
     return res
 
 

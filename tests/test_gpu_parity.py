@@ -405,3 +405,25 @@ def test_multicolumn_groups_of_columns_equal_one_pass_per_column(ncols, G, n, dt
         K, fl, lo, hi = st.host_view()
         rK, rfl, rlo, rhi = ref.host_view()
         assert np.array_equal(K, rK) and np.array_equal(fl, rfl) and np.array_equal(lo, rlo) and np.array_equal(hi, rhi)
+
+
+@pytest.mark.parametrize("ipc", [1, 8])
+def test_split_partitions_with_window_bounds_match_oracle(ipc, tmp_path):
+    """Partitions split into many work items (a loaded choice of 8 items per
+    CTA) share a window array of lower bounds between their items; the state
+    must still equal the oracle's bit for bit.  n >= 64 G, so no exact
+    window pass runs."""
+    G, L, n = 20_000, 3, (1 << 23) + 5
+    w = WL.sweep_cell(G, "zipf", L, n=n, seed=77, device=DEV)
+    f = tmp_path / "choice.txt"
+    f.write_text(f"part 0 {L} {(G - 1).bit_length()} 9 1 2 1024 8 2 1 {ipc}\n")
+    R.tune_clear()
+    R.tune_load(str(f))
+    try:
+        st, out = run_gpu(w.keys, w.values, w.G, w.L)
+    finally:
+        R.tune_clear()
+    assert st.check() == 0
+    ost, _ = oracle_state(_np(w.keys), _np(w.values), w.G, w.L, threads=8)
+    assert_state_equal(st, ost)
+    assert_bits_equal(_np(out), O.finalize(ost))
