@@ -179,8 +179,11 @@ __device__ __forceinline__ float words_value<float>(uint32_t hi, uint32_t) {
 // Phase A for four consecutive rows of a staged tile (r0 a multiple of 4):
 // vector loads, then -- when all four rows are ordinary (good key, normal
 // value inside its group's window) -- straight-line digits for the four rows
-// and predicated 32-bit atomics; otherwise the rows go one by one through
-// consume_row.
+// and predicated 32-bit atomics.  Failing that, when the only other rows are
+// zeros (+0 or -0: a discount column, say) the same straight-line code runs
+// with those rows' window set past the table, which switches off all their
+// atomics; the zero test stays off the common path, where it would cost
+// several percent.  Otherwise the rows go one by one through consume_row.
 template <typename T, int L>
 __device__ __forceinline__ void consume_quad(const SAddr& sa, const int32_t* tk, const T* tv, int r0, int G,
                                              const Table& t, int copy, int* sK, int* sKp, unsigned* sF,
@@ -198,16 +201,26 @@ __device__ __forceinline__ void consume_quad(const SAddr& sa, const int32_t* tk,
         K[q] = (int)lds_u32(sa.K + 4u * (uint32_t)(ok_key ? gq[q] : 0));
         fast = fast && ok_key && ok_val && kb[q] <= K[q];
     }
-    if (!fast) {  // some row is special, has a bad key, or must wait for a raise
+    if (!fast) {
+        bool masked = true;
 #pragma unroll
-        for (int q = 0; q < 4; ++q)
-            consume_row<T, L>(gq[q], words_value<T>(vhi[q], vlo[q]), r0 + q, G, t, copy, sK, sKp, sF, dlist,
-                              rlist, cnt, bad_key);
-        return;
+        for (int q = 0; q < 4; ++q) {
+            const bool zero = Lean<T>::is_zero(vhi[q], vlo[q]);
+            const bool ok_val = Lean<T>::decode_words(vhi[q], kb[q]);
+            masked = masked && (unsigned)gq[q] < (unsigned)G && (zero || (ok_val && kb[q] <= K[q]));
+            if (zero) K[q] = kb[q] + L;  // every level of the row falls past the table: no atomic
+        }
+        if (!masked) {  // some row is special, has a bad key, or must wait for a raise
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+                consume_row<T, L>(gq[q], words_value<T>(vhi[q], vlo[q]), r0 + q, G, t, copy, sK, sKp, sF, dlist,
+                                  rlist, cnt, bad_key);
+            return;
+        }
     }
-    // common case, straight-line: four rows' digits, then predicated atomics.
-    // Top and middle digits are almost never zero (adding zero is harmless);
-    // the low digit is zero whenever the value starts above its boundary.
+    // straight-line: four rows' digits, then predicated atomics.  Top and
+    // middle digits are almost never zero (adding zero is harmless); the low
+    // digit is zero whenever the value starts above its boundary.
     unsigned lo[12];
     int hi[12];
     uint32_t at[12];

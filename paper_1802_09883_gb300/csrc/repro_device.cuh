@@ -219,6 +219,10 @@ struct Lean<double> {
         vlo = (uint32_t)bits;
         return decode_words(vhi, kb);
     }
+    // +0 or -0 (adds nothing)
+    static __device__ __forceinline__ bool is_zero(uint32_t vhi, uint32_t vlo) {
+        return ((vhi << 1) | vlo) == 0u;
+    }
     // from the high word only (the low word is not needed to classify)
     static __device__ __forceinline__ bool decode_words(uint32_t vhi, int& kb) {
         const int E = (int)((vhi >> 20) & 0x7ffu);
@@ -269,6 +273,8 @@ struct Lean<float> {
         unused = 0;
         return decode_words(bits, kb);
     }
+    // +0 or -0 (adds nothing)
+    static __device__ __forceinline__ bool is_zero(uint32_t bits, uint32_t) { return (bits << 1) == 0u; }
     static __device__ __forceinline__ bool decode_words(uint32_t bits, int& kb) {
         const int E = (int)((bits >> 23) & 0xffu);
         kb = ((E + 23) * 3641) >> 16;  // (E + 23) / 18 for E + 23 < 2^9

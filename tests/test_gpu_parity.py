@@ -427,3 +427,24 @@ def test_split_partitions_with_window_bounds_match_oracle(ipc, tmp_path):
     ost, _ = oracle_state(_np(w.keys), _np(w.values), w.G, w.L, threads=8)
     assert_state_equal(st, ost)
     assert_bits_equal(_np(out), O.finalize(ost))
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+@pytest.mark.parametrize("G", [16, 1000, 70_000])
+def test_zero_heavy_columns_match_oracle(dtype, G):
+    """A third of the rows +0 or -0 (a discount column, say): zeros ride the
+    four-row fast path without touching the table; results and state equal
+    the oracle's."""
+    g = torch.Generator(device=DEV)
+    g.manual_seed(91 + G)
+    n = (1 << 21) + 3
+    keys = WL.uniform_keys(n, G, g, DEV)
+    vals = WL.random_values(n, -30, 30, g, DEV, dtype)
+    z = torch.rand(n, generator=g, device=DEV) < 0.33
+    signs = torch.where(torch.rand(n, generator=g, device=DEV) < 0.5, -1.0, 1.0).to(dtype)
+    vals = torch.where(z, torch.zeros_like(vals) * signs, vals)  # +0 and -0
+    st, out = run_gpu(keys, vals, G, 3)
+    assert st.check() == 0
+    ost, _ = oracle_state(_np(keys), _np(vals), G, 3, threads=8)
+    assert_state_equal(st, ost)
+    assert_bits_equal(_np(out), O.finalize(ost))
