@@ -329,7 +329,9 @@ repro_status groupby_sum_fp32(const int32_t* keys, const float* values, int64_t 
  * device memory, caller-owned).  repro_groupby_stats accumulates rows like
  * repro_groupby_sum (keys outside [0, num_groups) are skipped and flag
  * REPRO_ERR_KEY in the first part's header, read by repro_state_check);
- * scratch: one value column.  repro_stats_merge adds one state into another
+ * scratch: none beyond the single pass's partial tables when the group
+ * table fits on chip (the x*x pass squares each staged value in place),
+ * else one value column.  repro_stats_merge adds one state into another
  * (states of the same shape, not overlapping).
  *
  * repro_stats_finalize writes, per group g (any pointer may be NULL; value

@@ -47,7 +47,9 @@ struct FusedArgs {
 
 }  // namespace
 
-template <typename T, int L, int NCW>
+// SQ: sum x*x instead of x (each staged value squared in place, RN in T, by
+// the thread that consumes it; the sums behind VARIANCE / STDDEV).
+template <typename T, int L, int NCW, bool SQ>
 __global__ void __launch_bounds__(32 * (NCW + 1)) k_fused(FusedArgs a) {
     constexpr int NC = 32 * NCW;
     extern __shared__ __align__(128) unsigned char smem[];
@@ -153,6 +155,13 @@ __global__ void __launch_bounds__(32 * (NCW + 1)) k_fused(FusedArgs a) {
         if (ok) {
             sa.keys = smem_addr(tk);
             sa.vals = smem_addr(tv);
+            if (SQ) {  // this thread's quads, squared where they lie (read only after the barrier by others)
+                T* w = svals + (size_t)s * R;
+                for (int r = 4 * ctid; r < R; r += 4 * NC)
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) w[r + q] = w[r + q] * w[r + q];
+                asm volatile("" ::: "memory");  // the stores stay ahead of the quads' shared loads
+            }
             for (int r = 4 * ctid; r < R; r += 4 * NC)
                 consume_quad<T, L>(sa, tk, tv, r, G, tab, copy, sK, sKp, sF, dlist, rlist, cnt, bad_key);
         } else {
@@ -171,6 +180,7 @@ __global__ void __launch_bounds__(32 * (NCW + 1)) k_fused(FusedArgs a) {
             raise_and_add<T, L>(nr, nd, tk, tv, tab, sK, sKp, sF, dlist, rlist, ctid, NC);
             named_bar_sync(1, NC);
         }
+        if (SQ) fence_proxy_async_smem();  // the squares written here before the next TMA write
         __syncwarp();
         if ((ctid & 31) == 0) mbar_arrive(&empty[s]);
         rows_since_flush += R;
@@ -191,6 +201,11 @@ __global__ void __launch_bounds__(32 * (NCW + 1)) k_fused(FusedArgs a) {
         int* cnt = &ctl[2 * (tcount % 3)];
         const int32_t* tk = keyless ? skeys : a.keys + tail0;  // fewer than R tail rows
         const T* tv = vals + tail0;
+        if (SQ) {  // the tail's squares in the (now idle) first stage
+            for (int r = ctid; r < rows; r += NC) svals[r] = tv[r] * tv[r];
+            named_bar_sync(1, NC);
+            tv = svals;
+        }
         for (int r = ctid; r < rows; r += NC)
             consume_row<T, L>(tk[r], tv[r], r, G, tab, copy, sK, sKp, sF, dlist, rlist, cnt, bad_key);
         named_bar_sync(1, NC);
@@ -359,9 +374,9 @@ long long env_flush_rows() {
     return v;
 }
 
-template <typename T, int L, int NCW>
+template <typename T, int L, int NCW, bool SQ>
 cudaError_t launch_fused_t(const FusedArgs& a0, int ctas, size_t smem, cudaStream_t s) {
-    auto kern = k_fused<T, L, NCW>;
+    auto kern = k_fused<T, L, NCW, SQ>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     prof_begin(PROF_FUSED, s);
@@ -371,35 +386,46 @@ cudaError_t launch_fused_t(const FusedArgs& a0, int ctas, size_t smem, cudaStrea
     return cudaGetLastError();
 }
 
-template <typename T, int L>
+template <typename T, int L, bool SQ>
 cudaError_t dispatch_ncw(int ncw, const FusedArgs& a, int ctas, size_t smem, cudaStream_t s) {
-    if (ncw == 8) return launch_fused_t<T, L, 8>(a, ctas, smem, s);
-    return launch_fused_t<T, L, 16>(a, ctas, smem, s);
+    if (ncw == 8) return launch_fused_t<T, L, 8, SQ>(a, ctas, smem, s);
+    return launch_fused_t<T, L, 16, SQ>(a, ctas, smem, s);
 }
 
-template <typename T, int L>
+template <typename T, int L, bool SQ>
 const void* kernel_ncw(int ncw) {
-    return ncw == 8 ? (const void*)k_fused<T, L, 8> : (const void*)k_fused<T, L, 16>;
+    return ncw == 8 ? (const void*)k_fused<T, L, 8, SQ> : (const void*)k_fused<T, L, 16, SQ>;
 }
 
-template <typename T>
-const void* kernel_of(int L, int ncw) {
+template <typename T, bool SQ>
+const void* kernel_of_sq(int L, int ncw) {
     switch (L) {
-        case 1: return kernel_ncw<T, 1>(ncw);
-        case 2: return kernel_ncw<T, 2>(ncw);
-        case 3: return kernel_ncw<T, 3>(ncw);
-        default: return kernel_ncw<T, 4>(ncw);
+        case 1: return kernel_ncw<T, 1, SQ>(ncw);
+        case 2: return kernel_ncw<T, 2, SQ>(ncw);
+        case 3: return kernel_ncw<T, 3, SQ>(ncw);
+        default: return kernel_ncw<T, 4, SQ>(ncw);
     }
 }
 
 template <typename T>
-cudaError_t dispatch_L(int L, int ncw, const FusedArgs& a, int ctas, size_t smem, cudaStream_t s) {
+const void* kernel_of(int L, int ncw, bool square = false) {
+    return square ? kernel_of_sq<T, true>(L, ncw) : kernel_of_sq<T, false>(L, ncw);
+}
+
+template <typename T, bool SQ>
+cudaError_t dispatch_L_sq(int L, int ncw, const FusedArgs& a, int ctas, size_t smem, cudaStream_t s) {
     switch (L) {
-        case 1: return dispatch_ncw<T, 1>(ncw, a, ctas, smem, s);
-        case 2: return dispatch_ncw<T, 2>(ncw, a, ctas, smem, s);
-        case 3: return dispatch_ncw<T, 3>(ncw, a, ctas, smem, s);
-        default: return dispatch_ncw<T, 4>(ncw, a, ctas, smem, s);
+        case 1: return dispatch_ncw<T, 1, SQ>(ncw, a, ctas, smem, s);
+        case 2: return dispatch_ncw<T, 2, SQ>(ncw, a, ctas, smem, s);
+        case 3: return dispatch_ncw<T, 3, SQ>(ncw, a, ctas, smem, s);
+        default: return dispatch_ncw<T, 4, SQ>(ncw, a, ctas, smem, s);
     }
+}
+
+template <typename T>
+cudaError_t dispatch_L(int L, int ncw, const FusedArgs& a, int ctas, size_t smem, cudaStream_t s,
+                       bool square = false) {
+    return square ? dispatch_L_sq<T, true>(L, ncw, a, ctas, smem, s) : dispatch_L_sq<T, false>(L, ncw, a, ctas, smem, s);
 }
 
 }  // namespace
@@ -442,7 +468,7 @@ size_t fused_scratch_bytes(const FusedPlanConfig& cfg, int L, long long G, long 
 
 cudaError_t launch_groupby_fused(const int32_t* keys, const void* vals, long long n, int dtype, int L, long long G,
                                  const FusedPlanConfig& cfg, void* state, void* scratch, cudaStream_t s,
-                                 int max_ctas) {
+                                 int max_ctas, bool square) {
     const DeviceInfo& di = device_info();
     if (!fused_config_fits(dtype, L, (int)G, 0, cfg)) return cudaErrorInvalidValue;
     FusedArgs a;
@@ -458,7 +484,8 @@ cudaError_t launch_groupby_fused(const int32_t* keys, const void* vals, long lon
                                            : fused_layout<float>(cfg.S, cfg.R, (int)G, L, cfg.copies).total;
     // a persistent grid must be resident at once: never more CTAs per SM than
     // registers and shared memory allow
-    const void* kern = dtype == REPRO_F64 ? kernel_of<double>(L, cfg.ncw) : kernel_of<float>(L, cfg.ncw);
+    const void* kern =
+        dtype == REPRO_F64 ? kernel_of<double>(L, cfg.ncw, square) : kernel_of<float>(L, cfg.ncw, square);
     const int occ = resident_ctas(kern, 32 * (cfg.ncw + 1), smem);
     if (occ < 1) return cudaErrorInvalidConfiguration;
     int ctas = fused_ctas(a.ntiles, cfg, di);
@@ -469,8 +496,8 @@ cudaError_t launch_groupby_fused(const int32_t* keys, const void* vals, long lon
     a.flush_rows = fr > 0 ? fr : (1ll << 23);
     a.partials = (unsigned char*)scratch;
     a.errors = &reinterpret_cast<repro_state_header*>(state)->errors;
-    cudaError_t e = dtype == REPRO_F64 ? dispatch_L<double>(L, cfg.ncw, a, ctas, smem, s)
-                                       : dispatch_L<float>(L, cfg.ncw, a, ctas, smem, s);
+    cudaError_t e = dtype == REPRO_F64 ? dispatch_L<double>(L, cfg.ncw, a, ctas, smem, s, square)
+                                       : dispatch_L<float>(L, cfg.ncw, a, ctas, smem, s, square);
     if (e != cudaSuccess) return e;
     const int blocks = (int)((G + 31) / 32);
     prof_begin(PROF_MERGE, s);

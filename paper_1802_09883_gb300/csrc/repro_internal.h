@@ -61,10 +61,11 @@ bool fused_config_fits(int dtype, int L, int G, size_t extra_smem, const FusedPl
 size_t fused_plan_smem(int dtype, int L, int G, const FusedPlanConfig& cfg);
 bool fused_supported(int dtype, int L, long long G, const void* keys, const void* vals);
 size_t fused_scratch_bytes(const FusedPlanConfig& cfg, int L, long long G, long long n);
-// max_ctas > 0 caps the number of CTAs (and so the partial tables in scratch).
+// max_ctas > 0 caps the number of CTAs (and so the partial tables in scratch);
+// square: sum RN(x*x) instead of x.
 cudaError_t launch_groupby_fused(const int32_t* keys, const void* vals, long long n, int dtype, int L, long long G,
                                  const FusedPlanConfig& cfg, void* state, void* scratch, cudaStream_t s,
-                                 int max_ctas = 0);
+                                 int max_ctas = 0, bool square = false);
 
 // Large group counts: partition by key range, then the multi-task kernel
 // over the partitions (repro_partition.cu).  A choice fixes the partition

@@ -203,6 +203,25 @@ repro_status repro_groupby_stats(const int32_t* keys, const void* values, int64_
         count_launches(1);
         return from_cuda(cudaGetLastError());
     }
+    FusedPlanConfig cfg;
+    if (fused_supported(dtype, L, num_groups, keys, values) && fused_plan_config(dtype, L, (int)num_groups, 0, cfg)) {
+        // two single passes over the same columns, the second squaring each
+        // staged value in place (no x*x column in memory), and the counts
+        cudaMemPool_t pool0 = library_pool(err);
+        if (!pool0) return from_cuda(err);
+        void* part = nullptr;
+        err = cudaMallocFromPoolAsync(&part, std::max<size_t>(16, fused_scratch_bytes(cfg, L, num_groups, n)), pool0,
+                                      s);
+        if (err != cudaSuccess) return from_cuda(err);
+        err = launch_groupby_fused(keys, values, n, dtype, L, num_groups, cfg, b, part, s);
+        if (err == cudaSuccess)
+            err = launch_groupby_fused(keys, values, n, dtype, L, num_groups, cfg, b + ly.sq, part, s, 0, true);
+        cudaFreeAsync(part, s);
+        if (err != cudaSuccess) return from_cuda(err);
+        k_count<<<device_info().sms * 8, 256, 0, s>>>(keys, n, (int)num_groups, counts);
+        count_launches(1);
+        return from_cuda(cudaGetLastError());
+    }
     cudaMemPool_t pool = library_pool(err);
     if (!pool) return from_cuda(err);
     void* sq = nullptr;
