@@ -257,14 +257,17 @@ repro_status repro_batch_destroy(repro_batch_plan plan);
 /* How a prepared plan runs its tasks (a diagnostic; nothing is launched). */
 typedef struct {
     int32_t tasks;             /* tasks of the plan (including empty ones) */
-    int32_t single_pass_tasks; /* in the one persistent launch */
+    int32_t single_pass_tasks; /* in the persistent launches */
     int32_t partition_tasks;   /* in the batched partition pass */
     int32_t lane_tasks;        /* each on its own side-stream chain */
-    int32_t items;             /* work items of the persistent launch */
+    int32_t items;             /* work items of the persistent launches */
     int32_t merge_blocks;
     int32_t items_per_cta;     /* item sizing target (repro_batch_tune may change it) */
-    int32_t partition_overlap; /* 1: the partition pass runs beside the persistent launch, 0: before it */
+    int32_t partition_overlap; /* 1: the partition pass runs beside the persistent launches, 0: before them */
     int64_t device_bytes;      /* device memory the plan holds */
+    int32_t class_tasks[3];    /* single-pass tasks per table class (G <= 64, <= 1024, larger), one
+                                  persistent launch per class with tasks, each sized for its own largest table */
+    int32_t reserved;
 } repro_batch_info;
 
 repro_status repro_batch_describe(repro_batch_plan plan, repro_batch_info* out);

@@ -334,7 +334,7 @@ class _BatchInfo(ctypes.Structure):
                 ("partition_tasks", ctypes.c_int32), ("lane_tasks", ctypes.c_int32), ("items", ctypes.c_int32),
                 ("merge_blocks", ctypes.c_int32), ("items_per_cta", ctypes.c_int32),
                 ("partition_overlap", ctypes.c_int32),
-                ("device_bytes", ctypes.c_int64)]
+                ("device_bytes", ctypes.c_int64), ("class_tasks", ctypes.c_int32 * 3), ("reserved", ctypes.c_int32)]
 
 
 class BatchPlan:
@@ -376,7 +376,9 @@ class BatchPlan:
         side lanes), its items and the device memory it holds."""
         info = _BatchInfo()
         _check(lib().repro_batch_describe(self._plan, ctypes.byref(info)), "repro_batch_describe")
-        return {name: getattr(info, name) for name, _ in _BatchInfo._fields_}
+        out = {name: getattr(info, name) for name, _ in _BatchInfo._fields_ if name != "reserved"}
+        out["class_tasks"] = list(info.class_tasks)
+        return out
 
     def tune(self) -> float:
         """Time item sizes for this plan and keep the fastest (the states are

@@ -14,12 +14,26 @@ namespace rp {
 // Bytes of one partial-table record: int32 K, uint32 flags, L 128-bit bins.
 constexpr size_t batch_rec_bytes(int L) { return 8 + 16 * (size_t)L; }
 
+// The single-pass tasks are launched in classes by group count, one
+// persistent launch per class, each with the configuration of its own
+// largest table: small tables keep several CTAs per SM (and lane-private
+// copies for the smallest) instead of all tasks running at the occupancy
+// of the batch's largest table.
+constexpr int kBatchClasses = 3;
+constexpr long long kBatchClassBound[kBatchClasses] = {64, 1024, 1ll << 31};  // largest G of each class
+
+struct BatchClass {
+    FusedPlanConfig cfg{};  // cfg.S == 0: the class holds no task
+    int gcap = 1;           // largest group table among its tasks
+    int ctas = 0;           // CTAs of its persistent launch
+    int item0 = 0, nitems = 0;  // its items in HostBatch::items (largest first)
+    int ntasks = 0;
+};
+
 struct HostBatch {
-    FusedPlanConfig cfg{};
-    int gcap = 1;                  // largest group table among the single-pass tasks
-    int ctas = 0;                  // CTAs of the persistent launch
+    BatchClass cls[kBatchClasses];
     std::vector<MTask> tasks;      // one per input task (index = task number)
-    std::vector<MItem> items;      // largest first
+    std::vector<MItem> items;      // class by class
     std::vector<MergeBlk> blks;    // partial-merge blocks of the tasks cut into several items
     long long part_recs = 0;       // partial-table records the items write
     std::vector<repro_task> slow;  // tasks outside the single-pass path (two-pass path)
@@ -31,9 +45,10 @@ struct HostBatch {
 // item); items grow further while the partial tables would exceed
 // max_part_bytes.  Validates the tasks (REPRO_EINVAL) and the table size
 // (REPRO_ERANGE).
-// With fixed_cfg the single-pass configuration is that one (it must fit)
-// instead of a fresh choice, so a re-plan keeps an existing plan's kernel.
+// With fixed_cfg (one per class) each class's configuration is that one (it
+// must fit) instead of a fresh choice, so a re-plan keeps an existing plan's
+// kernels.
 repro_status plan_batch_host(const repro_task* tasks, int ntasks, int dtype, int L, size_t max_part_bytes,
-                             HostBatch& H, int items_per_cta = 4, const FusedPlanConfig* fixed_cfg = nullptr);
+                             HostBatch& H, int items_per_cta = 4, const BatchClass* fixed_cfg = nullptr);
 
 }  // namespace rp

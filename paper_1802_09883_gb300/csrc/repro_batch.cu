@@ -519,7 +519,7 @@ cudaError_t launch_merge_items(int L, int dtype, const void* tasks, const void* 
 }
 
 repro_status plan_batch_host(const repro_task* tasks, int ntasks, int dtype, int L, size_t max_part_bytes,
-                             HostBatch& H, int items_per_cta, const FusedPlanConfig* fixed_cfg) {
+                             HostBatch& H, int items_per_cta, const BatchClass* fixed_cfg) {
     if (ntasks < 0 || (ntasks > 0 && !tasks) || (dtype != REPRO_F64 && dtype != REPRO_F32) || L < 1 || L > 4)
         return REPRO_EINVAL;
     for (int t = 0; t < ntasks; ++t) {
@@ -530,15 +530,16 @@ repro_status plan_batch_host(const repro_task* tasks, int ntasks, int dtype, int
             return REPRO_EINVAL;
     }
     H = HostBatch{};
-    // single-pass tasks: aligned rows and a table that fits
-    std::vector<int> fast;
-    long long gcap = 1;
+    // single-pass tasks (aligned rows and a table that fits), by class
+    std::vector<int> fast[kBatchClasses];
     for (int t = 0; t < ntasks; ++t) {
         const repro_task& k = tasks[t];
         if (k.n == 0) continue;
         if (fused_supported(dtype, L, k.num_groups, k.keys, k.values)) {
-            fast.push_back(t);
-            gcap = std::max(gcap, (long long)k.num_groups);
+            int c = 0;
+            while (k.num_groups > kBatchClassBound[c]) ++c;
+            fast[c].push_back(t);
+            H.cls[c].gcap = std::max(H.cls[c].gcap, (int)k.num_groups);
         } else {
             H.slow.push_back(k);
             H.slow_gmax = std::max(H.slow_gmax, (long long)k.num_groups);
@@ -549,54 +550,74 @@ repro_status plan_batch_host(const repro_task* tasks, int ntasks, int dtype, int
         H.tasks[t] = MTask{tasks[t].keys, tasks[t].values, tasks[t].n, (int)tasks[t].num_groups,
                            (int)tasks[t].num_groups, (unsigned char*)tasks[t].state,
                            (unsigned char*)tasks[t].state + sizeof(repro_state_header), nullptr, 0, 0};
-    if (fast.empty()) return REPRO_OK;
-    if (fixed_cfg) {
-        if (!fused_config_fits(dtype, L, (int)gcap, kMetaSmemBytes, *fixed_cfg)) return REPRO_ERANGE;
-        H.cfg = *fixed_cfg;
-    } else if (!fused_plan_config(dtype, L, (int)gcap, kMetaSmemBytes, H.cfg)) {
-        return REPRO_ERANGE;
-    }
-    H.gcap = (int)gcap;
-    const int R = H.cfg.R;
-    long long total_tiles = 0;
-    for (int t : fast) total_tiles += (tasks[t].n + R - 1) / R;
-    H.ctas = device_info().sms * H.cfg.ctas_per_sm;
-    const long long tpi_max = (1ll << 23) / R;
-    const long long per = (long long)std::max(1, items_per_cta) * H.ctas;
-    long long tpi = (total_tiles + per - 1) / per;
-    tpi = std::max(8ll, std::min(tpi, tpi_max));
-    auto part_records = [&](long long tp) {
-        long long part = 0;
-        for (int t : fast) {
-            const long long nit = ((tasks[t].n + R - 1) / R + tp - 1) / tp;
-            if (nit > 1) part += nit * tasks[t].num_groups;
+    long long tpi0[kBatchClasses] = {};
+    long long tpi_max[kBatchClasses] = {};
+    for (int c = 0; c < kBatchClasses; ++c) {
+        BatchClass& B = H.cls[c];
+        if (fast[c].empty()) continue;
+        if (fixed_cfg && fixed_cfg[c].cfg.S) {
+            if (!fused_config_fits(dtype, L, B.gcap, kMetaSmemBytes, fixed_cfg[c].cfg)) return REPRO_ERANGE;
+            B.cfg = fixed_cfg[c].cfg;
+        } else if (!fused_plan_config(dtype, L, B.gcap, kMetaSmemBytes, B.cfg)) {
+            return REPRO_ERANGE;
         }
+        const int R = B.cfg.R;
+        long long total_tiles = 0;
+        for (int t : fast[c]) total_tiles += (tasks[t].n + R - 1) / R;
+        B.ctas = device_info().sms * B.cfg.ctas_per_sm;
+        tpi_max[c] = (1ll << 23) / R;
+        const long long per = (long long)std::max(1, items_per_cta) * B.ctas;
+        tpi0[c] = std::max(8ll, std::min((total_tiles + per - 1) / per, tpi_max[c]));
+    }
+    // items grow (all classes alike) while the partial tables would exceed max_part_bytes
+    auto tpi_of = [&](int c, long long f) { return std::min(tpi_max[c], tpi0[c] * f); };
+    auto part_records = [&](long long f) {
+        long long part = 0;
+        for (int c = 0; c < kBatchClasses; ++c)
+            for (int t : fast[c]) {
+                const long long R = H.cls[c].cfg.R, tp = tpi_of(c, f);
+                const long long nit = ((tasks[t].n + R - 1) / R + tp - 1) / tp;
+                if (nit > 1) part += nit * tasks[t].num_groups;
+            }
         return part;
     };
-    while (tpi < tpi_max && (size_t)part_records(tpi) * batch_rec_bytes(L) > max_part_bytes)
-        tpi = std::min(tpi_max, 2 * tpi);
+    long long f = 1;
+    auto can_grow = [&]() {
+        for (int c = 0; c < kBatchClasses; ++c)
+            if (!fast[c].empty() && tpi_of(c, f) < tpi_max[c]) return true;
+        return false;
+    };
+    while (can_grow() && (size_t)part_records(f) * batch_rec_bytes(L) > max_part_bytes) f *= 2;
     long long part = 0;
-    for (int t : fast) {
-        const long long ntile = (tasks[t].n + R - 1) / R;
-        const long long nit = (ntile + tpi - 1) / tpi;
-        const int G = (int)tasks[t].num_groups;
-        for (long long k = 0; k < nit; ++k) {
-            MItem it;
-            it.task = t;
-            it.excl = nit == 1;
-            it.row0 = k * tpi * R;
-            it.row1 = std::min<long long>(tasks[t].n, (k + 1) * tpi * R);
-            it.part = nit == 1 ? -1 : part + k * G;
-            H.items.push_back(it);
+    for (int c = 0; c < kBatchClasses; ++c) {
+        BatchClass& B = H.cls[c];
+        B.item0 = (int)H.items.size();
+        if (fast[c].empty()) continue;
+        const long long R = B.cfg.R, tpi = tpi_of(c, f);
+        for (int t : fast[c]) {
+            const long long ntile = (tasks[t].n + R - 1) / R;
+            const long long nit = (ntile + tpi - 1) / tpi;
+            const int G = (int)tasks[t].num_groups;
+            for (long long k = 0; k < nit; ++k) {
+                MItem it;
+                it.task = t;
+                it.excl = nit == 1;
+                it.row0 = k * tpi * R;
+                it.row1 = std::min<long long>(tasks[t].n, (k + 1) * tpi * R);
+                it.part = nit == 1 ? -1 : part + k * G;
+                H.items.push_back(it);
+            }
+            if (nit > 1) {
+                for (int g0 = 0; g0 < G; g0 += 32) H.blks.push_back(MergeBlk{t, g0, (int)nit, 0, part});
+                part += nit * G;
+            }
         }
-        if (nit > 1) {
-            for (int g0 = 0; g0 < G; g0 += 32) H.blks.push_back(MergeBlk{t, g0, (int)nit, 0, part});
-            part += nit * G;
-        }
+        B.nitems = (int)H.items.size() - B.item0;
+        B.ntasks = (int)fast[c].size();
+        // largest items first: the dynamic schedule then balances the tail
+        std::stable_sort(H.items.begin() + B.item0, H.items.end(),
+                         [](const MItem& x, const MItem& y) { return x.row1 - x.row0 > y.row1 - y.row0; });
     }
-    // largest items first: the dynamic schedule then balances the tail
-    std::stable_sort(H.items.begin(), H.items.end(),
-                     [](const MItem& x, const MItem& y) { return x.row1 - x.row0 > y.row1 - y.row0; });
     H.part_recs = part;
     return REPRO_OK;
 }
@@ -632,9 +653,7 @@ __global__ void k_batch_finalize(const MTask* __restrict__ tasks, void* const* _
 
 struct BatchPlan {
     int dtype = 0, L = 0;
-    FusedPlanConfig cfg{};
-    int gcap_ = 1;
-    int ctas = 0;
+    BatchClass cls[kBatchClasses];      // one persistent launch per class with tasks
     int nitems = 0, nblks = 0;
     int ntasks = 0;
     long long gmax = 1;                 // largest group count of any task
@@ -683,6 +702,7 @@ constexpr int kSlowLanes = 8;
 // (Re)allocate the plan's item, merge-block and partial arrays for H and
 // copy H's items and blocks to the device (synchronous).
 repro_status upload_items(BatchPlan& P, const HostBatch& H) {
+    for (int c = 0; c < kBatchClasses; ++c) P.cls[c] = H.cls[c];  // item ranges (and configurations)
     P.nitems = (int)H.items.size();
     P.nblks = (int)H.blks.size();
     if (P.nitems == 0) return REPRO_OK;
@@ -731,9 +751,7 @@ repro_status repro_batch_prepare(const repro_task* tasks, int ntasks, repro_dtyp
     BatchPlan& P = plan->p;
     P.dtype = dtype;
     P.L = L;
-    P.cfg = H.cfg;
-    P.gcap_ = H.gcap;
-    P.ctas = H.ctas;
+    for (int c = 0; c < kBatchClasses; ++c) P.cls[c] = H.cls[c];
     P.slow = H.slow;
     for (int t = 0; t < ntasks; ++t) P.single_tasks += tasks[t].n > 0 ? 1 : 0;
     P.single_tasks -= (int)H.slow.size();
@@ -849,10 +867,12 @@ repro_status repro_batch_run(repro_batch_plan plan, void* stream) {
         }
     }
     if (P.nitems > 0) {
-        const int ctas = std::min(P.ctas, std::max(1, P.nitems));
-        e = launch_multi(P.dtype, P.L, P.cfg, P.gcap_, P.d_tasks, P.d_items, P.nitems, nullptr, P.d_counter,
-                         P.d_partials, ctas, s);
-        if (e != cudaSuccess) return REPRO_ECUDA;
+        for (const BatchClass& B : P.cls) {  // one persistent launch per class, in stream order
+            if (B.nitems == 0) continue;
+            e = launch_multi(P.dtype, P.L, B.cfg, B.gcap, P.d_tasks, P.d_items + B.item0, B.nitems, nullptr,
+                             P.d_counter, P.d_partials, std::min(B.ctas, B.nitems), s);
+            if (e != cudaSuccess) return REPRO_ECUDA;
+        }
         if (P.nblks > 0) {
             e = launch_merge_items(P.L, P.dtype, P.d_tasks, P.d_blks, P.nblks, nullptr, P.d_partials, s);
             if (e != cudaSuccess) return REPRO_ECUDA;
@@ -940,7 +960,7 @@ repro_status repro_batch_tune(repro_batch_plan plan, void* stream, double* best_
         const int ipc = 1 << (trial % 5);
         P.bpart_overlap = trial < 5;
         HostBatch H;
-        st = plan_batch_host(P.tasks.data(), P.ntasks, P.dtype, P.L, kBatchPartBytes, H, ipc, &P.cfg);
+        st = plan_batch_host(P.tasks.data(), P.ntasks, P.dtype, P.L, kBatchPartBytes, H, ipc, P.cls);
         if (st == REPRO_OK) st = upload_items(P, H);
         if (st != REPRO_OK) break;
         std::vector<float> t;
@@ -968,7 +988,7 @@ repro_status repro_batch_tune(repro_batch_plan plan, void* stream, double* best_
     P.bpart_overlap = pick_overlap;
     if (st != REPRO_OK) return st;
     HostBatch H;
-    st = plan_batch_host(P.tasks.data(), P.ntasks, P.dtype, P.L, kBatchPartBytes, H, pick, &P.cfg);
+    st = plan_batch_host(P.tasks.data(), P.ntasks, P.dtype, P.L, kBatchPartBytes, H, pick, P.cls);
     if (st == REPRO_OK) st = upload_items(P, H);
     if (st == REPRO_OK) P.items_per_cta = pick;
     if (st == REPRO_OK) st = repro_batch_reset(plan, stream);
@@ -989,6 +1009,7 @@ repro_status repro_batch_describe(repro_batch_plan plan, repro_batch_info* out) 
     out->merge_blocks = P.nblks;
     out->items_per_cta = P.items_per_cta;
     out->partition_overlap = P.has_bpart && P.bpart_overlap ? 1 : 0;
+    for (int c = 0; c < kBatchClasses && c < 3; ++c) out->class_tasks[c] = P.cls[c].ntasks;
     out->device_bytes = (int64_t)(P.dev_bytes + P.items_cap + P.blks_cap + P.parts_cap +
                                   sizeof(MTask) * (size_t)P.ntasks + P.slow_each * P.lanes.size());
     return REPRO_OK;

@@ -236,10 +236,12 @@ struct Server {
         if (e != cudaSuccess) return e;
         int* counter = (int*)(a->dev + host_need);
         unsigned char* partials = a->dev + host_need + 256;
-        const int nitems = (int)H.items.size();
-        e = launch_multi(dtype, L, H.cfg, H.gcap, a->dev, a->dev + tb, nitems, nullptr, counter, partials,
-                         std::min(H.ctas, nitems), stream[0]);
-        if (e != cudaSuccess) return e;
+        for (const BatchClass& B : H.cls) {  // one persistent launch per table class, in stream order
+            if (B.nitems == 0) continue;
+            e = launch_multi(dtype, L, B.cfg, B.gcap, a->dev, a->dev + tb + sizeof(MItem) * (size_t)B.item0, B.nitems,
+                             nullptr, counter, partials, std::min(B.ctas, B.nitems), stream[0]);
+            if (e != cudaSuccess) return e;
+        }
         if (!H.blks.empty())
             e = launch_merge_items(L, dtype, a->dev, a->dev + tb + ib, (int)H.blks.size(), nullptr, partials,
                                    stream[0]);
