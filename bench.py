@@ -49,6 +49,8 @@ def parse():
                     help="host threads of the CPU oracle (reference arm, cpu_baseline); 0: all cores")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-tune", action="store_true", help="skip the untimed autotuning before the warm-up")
+    ap.add_argument("--tune-file", default="",
+                    help="sweep cells: load the tuned choices from this file if it exists, else tune and save them")
     ap.add_argument("--verify", action="store_true", help="check sampled groups against the oracle")
     ap.add_argument("--workload", default="sweep", choices=["sweep", "multicol", "batched", "serve", "scalar", "stats"],
                     help="sweep: one grouped SUM (default); multicol: 4 SUM columns over two uint8 keys; "
@@ -160,8 +162,13 @@ def run_ours(args, rank, world, local_rank):
     stream = torch.cuda.current_stream(dev)
 
     tuned = None
-    if not args.no_tune:  # untimed: measured configuration choice for this workload
+    if args.tune_file and os.path.exists(args.tune_file):  # an earlier run's measured choices
+        R.tune_load(args.tune_file)
+        tuned = {"loaded_from": args.tune_file}
+    elif not args.no_tune:  # untimed: measured configuration choice for this workload
         tuned = R.tune(w.keys, w.values, G, L)
+        if args.tune_file:
+            R.tune_save(args.tune_file)
 
     def step():
         st.reset()
