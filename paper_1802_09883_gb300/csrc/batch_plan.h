@@ -48,7 +48,10 @@ struct HostBatch {
 // With fixed_cfg (one per class) each class's configuration is that one (it
 // must fit) instead of a fresh choice, so a re-plan keeps an existing plan's
 // kernels.
+// With one_class, every single-pass task goes to the last class (one
+// persistent launch: fewer launches for a small batch).
 repro_status plan_batch_host(const repro_task* tasks, int ntasks, int dtype, int L, size_t max_part_bytes,
-                             HostBatch& H, int items_per_cta = 4, const BatchClass* fixed_cfg = nullptr);
+                             HostBatch& H, int items_per_cta = 4, const BatchClass* fixed_cfg = nullptr,
+                             bool one_class = false);
 
 }  // namespace rp

@@ -519,7 +519,7 @@ cudaError_t launch_merge_items(int L, int dtype, const void* tasks, const void* 
 }
 
 repro_status plan_batch_host(const repro_task* tasks, int ntasks, int dtype, int L, size_t max_part_bytes,
-                             HostBatch& H, int items_per_cta, const BatchClass* fixed_cfg) {
+                             HostBatch& H, int items_per_cta, const BatchClass* fixed_cfg, bool one_class) {
     if (ntasks < 0 || (ntasks > 0 && !tasks) || (dtype != REPRO_F64 && dtype != REPRO_F32) || L < 1 || L > 4)
         return REPRO_EINVAL;
     for (int t = 0; t < ntasks; ++t) {
@@ -536,7 +536,7 @@ repro_status plan_batch_host(const repro_task* tasks, int ntasks, int dtype, int
         const repro_task& k = tasks[t];
         if (k.n == 0) continue;
         if (fused_supported(dtype, L, k.num_groups, k.keys, k.values)) {
-            int c = 0;
+            int c = one_class ? kBatchClasses - 1 : 0;
             while (k.num_groups > kBatchClassBound[c]) ++c;
             fast[c].push_back(t);
             H.cls[c].gcap = std::max(H.cls[c].gcap, (int)k.num_groups);

@@ -64,6 +64,7 @@ size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 // Partial tables of one iteration's batch stay below this where the work
 // allows (the planner makes items longer otherwise).
 constexpr size_t kServePartBytes = 256ull << 20;
+constexpr long long kServeClassRows = 1ll << 26;  // iterations with fewer rows: one persistent launch
 
 // Stream 0 runs the batched single-pass launches; stream 1 the batched
 // partition pass of the queries whose tables need partitioning (aligned
@@ -196,8 +197,13 @@ struct Server {
     }
 
     cudaError_t launch_batch(int dtype, int L, const std::vector<repro_task>& tasks, Iter& it) {
+        // a light iteration runs as one persistent launch (latency), a heavy
+        // one by table class (throughput)
+        long long rows = 0;
+        for (const repro_task& k : tasks) rows += k.n;
         HostBatch H;
-        if (plan_batch_host(tasks.data(), (int)tasks.size(), dtype, L, kServePartBytes, H) != REPRO_OK)
+        if (plan_batch_host(tasks.data(), (int)tasks.size(), dtype, L, kServePartBytes, H, 4, nullptr,
+                            rows < kServeClassRows) != REPRO_OK)
             return cudaErrorInvalidValue;
         if (!H.slow.empty()) return cudaErrorInvalidValue;  // admission routes these to the other lane
         if (H.items.empty()) return cudaSuccess;
