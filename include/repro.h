@@ -216,7 +216,7 @@ repro_status repro_groupby_sum_noalloc(const int32_t* keys, const void* values, 
 
 /*
  * Batched grouped SUM: many independent aggregations (each with its own
- * keys, values, group count and state) in one persistent launch.  Same
+ * keys, values, group count and state) in a few persistent launches.  Same
  * result bits per task as repro_groupby_sum on that task alone.
  *
  * repro_batch_prepare builds a plan on the host (it allocates device memory
@@ -228,10 +228,11 @@ repro_status repro_groupby_sum_noalloc(const int32_t* keys, const void* values, 
  * repro_groupby_sum_batched = prepare + run + stream synchronise + destroy.
  *
  * Tasks whose rows are 16-byte aligned and whose group table fits the
- * single-pass path share the persistent launch: the plan cuts them into
- * work items of whole tiles (the item size is tuned to the batch: about four
- * items per CTA, at most 2^23 rows), largest first; an item that covers a
- * whole task merges straight into its state.  Tasks with more groups
+ * single-pass path share persistent launches, one per table class (up to 64
+ * groups, up to 1024, larger), each configured for its own largest table:
+ * the plan cuts them into work items of whole tiles (the item size is tuned
+ * to the batch: about four items per CTA, at most 2^23 rows), largest first;
+ * an item that covers a whole task merges straight into its state.  Tasks with more groups
  * than one shared-memory table holds (and 16-byte aligned rows, up to 2^19
  * groups) share one batched partition pass -- one partitioning of all of
  * them and one multi-task launch over their partitions -- on a side stream
@@ -380,7 +381,8 @@ repro_status repro_stats_finalize(const void* state, repro_dtype dtype, int L, i
  * device memory (state plus scratch, estimated at submit) fits the budget and
  * a slot is free.  It then runs iterations: each iteration takes the next
  * chunk_rows rows of every admitted query; chunks whose group table fits the
- * single-pass kernel go into one multi-task persistent launch; the chunks of
+ * single-pass kernel go into one multi-task persistent launch (one per table
+ * class when the iteration holds 2^26 rows or more); the chunks of
  * queries that need partitioning go into one batched partition pass on a
  * second stream (aligned columns, up to 2^19 groups) or, otherwise, through
  * the partitioned path on one of three more streams.  Partial states stay on
@@ -495,7 +497,7 @@ void repro_tune_clear(void);
 
 /* Time the plan with work items of several sizes (about 1, 2, 4, 8 and 16
    items per CTA) and, when it has a batched partition pass, with that pass
-   beside the persistent launch and before it; keep the fastest; *best_ms (may be NULL) receives its
+   beside the persistent launches and before them; keep the fastest; *best_ms (may be NULL) receives its
    median time per run.  Runs the plan several times on `stream` and
    synchronises; afterwards every task's state is re-initialised (as
    repro_batch_reset). */
