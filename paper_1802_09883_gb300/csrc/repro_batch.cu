@@ -232,6 +232,8 @@ __global__ void __launch_bounds__(32 * (NCW + 1)) k_fused_multi(MultiArgs a, int
         // ------------------------------------------------------------ producer
         if (tid == NC) {
             long long i = 0;  // tiles issued by this CTA (ring position)
+            int s = 0;        // i mod S and the parity of the ring round i / S, kept without divisions
+            uint32_t par = 0;
             bool ok = true;
             const int nitems = a.nitems_ptr ? *a.nitems_ptr : a.nitems;
             for (;;) {
@@ -241,9 +243,8 @@ __global__ void __launch_bounds__(32 * (NCW + 1)) k_fused_multi(MultiArgs a, int
                 const MTask tk = a.tasks[done ? 0 : it.task];
                 const long long nrows = it.row1 - it.row0;
                 const long long ntile = done ? 1 : (nrows + R - 1) / R;
-                for (long long t = 0; t < ntile; ++t, ++i) {
-                    const int s = (int)(i % S);
-                    if (i >= S && !mbar_wait_bounded(&empty[s], (uint32_t)(((i / S) - 1) & 1), kWaitNs)) {
+                for (long long t = 0; t < ntile; ++t) {
+                    if (i >= S && !mbar_wait_bounded(&empty[s], par ^ 1u, kWaitNs)) {
                         ok = false;
                         break;
                     }
@@ -278,6 +279,11 @@ __global__ void __launch_bounds__(32 * (NCW + 1)) k_fused_multi(MultiArgs a, int
                         bulk_g2s(skeys + (size_t)s * R, tk.keys + sm.row0, kb, &full[s]);
                         bulk_g2s(svals + (size_t)s * R, reinterpret_cast<const T*>(tk.vals) + sm.row0, vb, &full[s]);
                     }
+                    ++i;
+                    if (++s == S) {
+                        s = 0;
+                        par ^= 1u;
+                    }
                 }
                 if (done || !ok) break;
             }
@@ -296,10 +302,11 @@ __global__ void __launch_bounds__(32 * (NCW + 1)) k_fused_multi(MultiArgs a, int
     sa.lo = smem_addr(tab.lo);
     sa.hi = smem_addr(tab.hi);
     bool bad_key = false;
-    int tcount = 0;
-    for (long long i = 0;; ++i) {
-        const int s = (int)(i % S);
-        const bool ok = mbar_wait_bounded(&full[s], (uint32_t)((i / S) & 1), kWaitNs);
+    int c3 = 0;  // the tile's counter buffer (tiles processed mod 3)
+    int s = 0;   // the tile's stage and the parity of its ring round, kept without divisions
+    uint32_t par = 0;
+    for (;; ) {
+        const bool ok = mbar_wait_bounded(&full[s], par, kWaitNs);
         if (!ok) *abort_flag = 1;  // before the barrier, read after it
         named_bar_sync(1, NC);
         if (*abort_flag) break;
@@ -317,7 +324,7 @@ __global__ void __launch_bounds__(32 * (NCW + 1)) k_fused_multi(MultiArgs a, int
                 for (int g = ctid; g < G; g += NC) sK[g] = sKp[g] = __ldg(&sm.win[g]);
             named_bar_sync(1, NC);
         }
-        int* cnt = &ctl[2 * (tcount % 3)];
+        int* cnt = &ctl[2 * c3];
         const int32_t* tk_s = skeys + (size_t)s * R;
         const T* tv_s = svals + (size_t)s * R;
         const int32_t* gk = sm.keys;
@@ -330,7 +337,7 @@ __global__ void __launch_bounds__(32 * (NCW + 1)) k_fused_multi(MultiArgs a, int
             consume_row<T, L>(gk[r], gv[r], r, G, tab, copy, sK, sKp, sF, dlist, rlist, cnt, bad_key);
         named_bar_sync(1, NC);
         if (ctid == 0) {  // the counters of two tiles ago are no longer read
-            int* old = &ctl[2 * ((tcount + 2) % 3)];
+            int* old = &ctl[2 * (c3 == 0 ? 2 : c3 - 1)];
             old[0] = 0;
             old[1] = 0;
         }
@@ -342,7 +349,11 @@ __global__ void __launch_bounds__(32 * (NCW + 1)) k_fused_multi(MultiArgs a, int
         }
         __syncwarp();
         if ((ctid & 31) == 0) mbar_arrive(&empty[s]);
-        ++tcount;
+        c3 = c3 == 2 ? 0 : c3 + 1;
+        if (++s == S) {
+            s = 0;
+            par ^= 1u;
+        }
         if (sm.last) {
             const MItem it = a.items[sm.item];
             const MTask tk = a.tasks[it.task];

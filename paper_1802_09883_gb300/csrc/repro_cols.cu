@@ -129,9 +129,10 @@ __global__ void __launch_bounds__(32 * (NCW + 1)) k_fused_cols(ColsArgs a) {
         if (tid == NC) {
             const uint32_t kb = (uint32_t)R * 4, vb = (uint32_t)R * sizeof(T);
             int issued = 0;
+            int s = 0;  // i mod S and the parity of the ring round i / S, kept without divisions
+            uint32_t par = 0;
             for (int i = 0; i < ntile; ++i) {
-                const int s = i % S;
-                if (i >= S && !mbar_wait_bounded(&empty[s], ((i / S) - 1) & 1, kWaitNs)) {
+                if (i >= S && !mbar_wait_bounded(&empty[s], par ^ 1u, kWaitNs)) {
                     for (int c = 0; c < NV; ++c) atomicOr(a.errors[c], REPRO_ERR_TIMEOUT);
                     break;
                 }
@@ -141,6 +142,10 @@ __global__ void __launch_bounds__(32 * (NCW + 1)) k_fused_cols(ColsArgs a) {
                 for (int c = 0; c < NLOAD; ++c)
                     bulk_g2s(ring(c) + (size_t)s * R, static_cast<const T*>(a.vals[c]) + row0, vb, &full[s]);
                 ++issued;
+                if (++s == S) {
+                    s = 0;
+                    par ^= 1u;
+                }
             }
             for (int i = max(0, issued - S); i < issued; ++i)
                 if (!mbar_wait_bounded(&full[i % S], (i / S) & 1, kWaitNs)) break;
@@ -198,13 +203,14 @@ __global__ void __launch_bounds__(32 * (NCW + 1)) k_fused_cols(ColsArgs a) {
         ++tcount;
     };
 
+    int s = 0;  // the tile's stage and the parity of its ring round, kept without divisions
+    uint32_t par = 0;
     for (int i = 0; i < ntile; ++i) {
-        const int s = i % S;
         if (rows_since_flush + R > a.flush_rows) {
             flush_all();
             rows_since_flush = 0;
         }
-        const bool ok = mbar_wait_bounded(&full[s], (i / S) & 1, kWaitNs);
+        const bool ok = mbar_wait_bounded(&full[s], par, kWaitNs);
         if (!ok) {
             *abort_flag = 1;
             for (int c = 0; c < NV; ++c) atomicOr(a.errors[c], REPRO_ERR_TIMEOUT);
@@ -224,6 +230,10 @@ __global__ void __launch_bounds__(32 * (NCW + 1)) k_fused_cols(ColsArgs a) {
         __syncwarp();
         if ((ctid & 31) == 0) mbar_arrive(&empty[s]);
         rows_since_flush += R;
+        if (++s == S) {
+            s = 0;
+            par ^= 1u;
+        }
     }
 
     // ragged tail (n mod R rows), read from global memory by the last CTA

@@ -50,7 +50,7 @@ struct FusedArgs {
 // SQ: sum x*x instead of x (each staged value squared in place, RN in T, by
 // the thread that consumes it; the sums behind VARIANCE / STDDEV).
 template <typename T, int L, int NCW, bool SQ>
-__global__ void __launch_bounds__(32 * (NCW + 1)) k_fused(FusedArgs a) {
+__global__ void __launch_bounds__(32 * (NCW + 1), NCW == 8 ? 3 : 1) k_fused(FusedArgs a) {
     constexpr int NC = 32 * NCW;
     extern __shared__ __align__(128) unsigned char smem[];
     const FusedSmem m = fused_layout<T>(a.S, a.R, a.G, L, a.C);
@@ -107,9 +107,10 @@ __global__ void __launch_bounds__(32 * (NCW + 1)) k_fused(FusedArgs a) {
         if (tid == NC) {
             const uint32_t kb = keyless ? 0u : (uint32_t)R * 4, vb = (uint32_t)R * sizeof(T);
             int issued = 0;
+            int s = 0;         // stage of tile i (i mod S, kept without a division)
+            uint32_t par = 0;  // parity of the ring round i / S
             for (int i = 0; i < ntile; ++i) {
-                const int s = i % S;
-                if (i >= S && !mbar_wait_bounded(&empty[s], ((i / S) - 1) & 1, kWaitNs)) {
+                if (i >= S && !mbar_wait_bounded(&empty[s], par ^ 1u, kWaitNs)) {
                     // consumers will time out on the stages never filled
                     atomicOr(a.errors, REPRO_ERR_TIMEOUT);
                     break;
@@ -119,6 +120,10 @@ __global__ void __launch_bounds__(32 * (NCW + 1)) k_fused(FusedArgs a) {
                 if (!keyless) bulk_g2s(skeys + (size_t)s * R, a.keys + row0, kb, &full[s]);
                 bulk_g2s(svals + (size_t)s * R, vals + row0, vb, &full[s]);
                 ++issued;
+                if (++s == S) {
+                    s = 0;
+                    par ^= 1u;
+                }
             }
             // never leave with a copy in flight
             for (int i = max(0, issued - S); i < issued; ++i)
@@ -137,9 +142,11 @@ __global__ void __launch_bounds__(32 * (NCW + 1)) k_fused(FusedArgs a) {
     bool bad_key = false;
     bool first_flush = true;
     long long rows_since_flush = 0;
-    int tcount = 0;  // tiles processed (counter buffer index)
+    int tcount = 0;  // tiles processed
+    int c3 = 0;      // tcount mod 3: the counter buffer of this tile
+    int s = 0;       // stage of tile i and the parity of its ring round, kept without divisions
+    uint32_t par = 0;
     for (int i = 0; i < ntile; ++i) {
-        const int s = i % S;
         if (rows_since_flush + R > a.flush_rows) {
             named_bar_sync(1, NC);
             flush_partial<L>(a.partials + (size_t)blockIdx.x * G * (8 + 16 * L), G, tab, sK, sF, first_flush,
@@ -148,8 +155,8 @@ __global__ void __launch_bounds__(32 * (NCW + 1)) k_fused(FusedArgs a) {
             rows_since_flush = 0;
             named_bar_sync(1, NC);
         }
-        const bool ok = mbar_wait_bounded(&full[s], (i / S) & 1, kWaitNs);
-        int* cnt = &ctl[2 * (tcount % 3)];
+        const bool ok = mbar_wait_bounded(&full[s], par, kWaitNs);
+        int* cnt = &ctl[2 * c3];
         const int32_t* tk = skeys + (size_t)s * R;
         const T* tv = svals + (size_t)s * R;
         if (ok) {
@@ -170,7 +177,7 @@ __global__ void __launch_bounds__(32 * (NCW + 1)) k_fused(FusedArgs a) {
         }
         named_bar_sync(1, NC);
         if (ctid == 0) {  // the counters of two tiles ago are no longer read
-            int* old = &ctl[2 * ((tcount + 2) % 3)];
+            int* old = &ctl[2 * (c3 == 0 ? 2 : c3 - 1)];
             old[0] = 0;
             old[1] = 0;
         }
@@ -185,6 +192,11 @@ __global__ void __launch_bounds__(32 * (NCW + 1)) k_fused(FusedArgs a) {
         if ((ctid & 31) == 0) mbar_arrive(&empty[s]);
         rows_since_flush += R;
         ++tcount;
+        c3 = c3 == 2 ? 0 : c3 + 1;
+        if (++s == S) {
+            s = 0;
+            par ^= 1u;
+        }
     }
 
     // ragged tail (n mod R rows), read straight from global memory by the last CTA
@@ -198,7 +210,7 @@ __global__ void __launch_bounds__(32 * (NCW + 1)) k_fused(FusedArgs a) {
             first_flush = false;
             named_bar_sync(1, NC);
         }
-        int* cnt = &ctl[2 * (tcount % 3)];
+        int* cnt = &ctl[2 * c3];
         const int32_t* tk = keyless ? skeys : a.keys + tail0;  // fewer than R tail rows
         const T* tv = vals + tail0;
         if (SQ) {  // the tail's squares in the (now idle) first stage
