@@ -184,8 +184,10 @@ __device__ void clear_table(int G, const Table& t, int* sK, int* sKp, unsigned* 
 
 }  // namespace
 
+// At most 96 registers: two 8-warp CTAs per SM, and the compiler's own
+// choice for four levels otherwise grew past 110 with no gain.
 template <typename T, int L, int NCW>
-__global__ void __launch_bounds__(32 * (NCW + 1)) k_fused_multi(MultiArgs a, int dtype) {
+__global__ void __maxnreg__(96) k_fused_multi(MultiArgs a, int dtype) {
     constexpr int NC = 32 * NCW;
     extern __shared__ __align__(128) unsigned char smem[];
     const FusedSmem m = fused_layout<T>(a.S, a.R, a.Gcap, L, a.C);
