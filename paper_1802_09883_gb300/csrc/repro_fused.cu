@@ -315,7 +315,7 @@ namespace {
 // fits ctas_per_sm times into one SM's shared memory.
 template <typename T>
 bool config_fits(const FusedPlanConfig& c, int G, int L, const DeviceInfo& di, size_t extra) {
-    if (c.S < 2 || c.S > 8 || c.R < 1024 || c.R > 8192 || c.R % (128 * c.ncw) || (c.ncw != 8 && c.ncw != 16))
+    if (c.S < 1 || c.S > 8 || c.R < 1024 || c.R > 8192 || c.R % (128 * c.ncw) || (c.ncw != 8 && c.ncw != 16))
         return false;
     if (c.ctas_per_sm < 1 || c.ctas_per_sm > 4 || (c.copies != 1 && c.copies != 32)) return false;
     const size_t bytes = fused_layout<T>(c.S, c.R, G, L, c.copies).total + extra;

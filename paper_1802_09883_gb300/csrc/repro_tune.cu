@@ -150,12 +150,15 @@ repro_status repro_tune_groupby(const int32_t* keys, const void* values, int64_t
     if (fused_supported(dtype, L, G, keys, values)) {
         out->path = 0;
         std::vector<FusedPlanConfig> cands;
-        for (int S : {2, 3, 4})
+        // S = 1: a single stage per CTA (its tile loads while the SM's other
+        // CTAs compute), which leaves room for larger tiles at 3 CTAs per SM
+        for (int S : {1, 2, 3, 4})
             for (int R : {1024, 2048, 4096})
                 for (int ncw : {8, 16})
                     for (int cps : {1, 2, 3, 4})
                         for (int copies : {1, 32}) {
                             const FusedPlanConfig c{S, R, ncw, cps, copies};
+                            if (S == 1 && R == 1024) continue;
                             if (fused_config_fits(dtype, L, (int)G, 0, c)) cands.push_back(c);
                         }
         FusedPlanConfig def{};

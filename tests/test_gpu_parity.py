@@ -293,7 +293,8 @@ print("ok")
 
 @pytest.mark.parametrize("env", [{"REPRO_FLUSH_ROWS": "4096"}, {"REPRO_FUSED_CFG": "2,1024,16,1"},
                                  {"REPRO_FUSED_CFG": "4,1024,8,2"}, {"REPRO_FUSED_CFG": "3,2048,16,1"},
-                                 {"REPRO_FUSED_CFG": "3,1024,8,2,32"}])
+                                 {"REPRO_FUSED_CFG": "3,1024,8,2,32"}, {"REPRO_FUSED_CFG": "1,2048,8,3"},
+                                 {"REPRO_FUSED_CFG": "1,4096,16,1,32"}])
 def test_fused_variants_in_subprocess(env):
     """Mid-kernel flushes of the int64 table into the 128-bit partial, and
     other tile / stage / warp configurations, give the same bits."""
