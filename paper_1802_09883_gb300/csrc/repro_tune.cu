@@ -260,10 +260,11 @@ repro_status repro_tune_groupby(const int32_t* keys, const void* values, int64_t
         bool cfg_tuned = false;
         std::vector<PartChoice> cfgs;
         const PartChoice base = pick;
-        for (int S : {2, 3, 4})
+        for (int S : {1, 2, 3, 4})
             for (int R : {1024, 2048})
                 for (int ncw : {8, 16})
                     for (int cps : {1, 2, 3, 4}) {
+                        if (S == 1 && R == 1024) continue;
                         const FusedPlanConfig c{S, R, ncw, cps, 1};
                         if (c.S == base.cfg.S && c.R == base.cfg.R && c.ncw == base.cfg.ncw &&
                             c.ctas_per_sm == base.cfg.ctas_per_sm && c.copies == base.cfg.copies)

@@ -91,7 +91,7 @@ def test_partition_aggregation_configurations_give_identical_state(tmp_path):
     bucket = (G - 1).bit_length()
     f = tmp_path / "choice.txt"
     for cfg in ["2 1024 8 1 1", "3 2048 16 1 1", "4 1024 8 2 1", "2 2048 8 3 1", "2 1024 8 2 1 1",
-                "3 2048 8 2 1 8"]:
+                "3 2048 8 2 1 8", "1 2048 8 2 1", "1 2048 16 1 1 4"]:
         f.write_text(f"part 0 3 {bucket} 10 0 {cfg}\n")
         R.tune_clear()
         R.tune_load(str(f))
