@@ -51,7 +51,8 @@ def parse():
     ap.add_argument("--no-tune", action="store_true", help="skip the untimed autotuning before the warm-up")
     ap.add_argument("--tune-file", default="",
                     help="sweep cells: load the tuned choices from this file if it exists, else tune and save them")
-    ap.add_argument("--verify", action="store_true", help="check sampled groups against the oracle")
+    ap.add_argument("--no-verify", action="store_true",
+                    help="skip the (untimed) check of the step's state and results against the CPU oracle")
     ap.add_argument("--workload", default="sweep", choices=["sweep", "multicol", "batched", "serve", "scalar", "stats"],
                     help="sweep: one grouped SUM (default); multicol: 4 SUM columns over two uint8 keys; "
                          "batched: many aggregations in one launch; serve: the request server; "
@@ -202,6 +203,9 @@ def run_ours(args, rank, world, local_rank):
     clocks.stop()
     launches = lib.repro_launch_count() - launches0
     ms = e0.elapsed_time(e1) / args.steps
+    # the last timed step's state and results, kept for the checks below
+    dev_state = st.tensor.cpu().numpy().copy()
+    dev_out = out.cpu().numpy().copy()
     prof = {}
     for name in ("accum", "window", "fused", "partition", "merge", "finalize"):
         t = ctypes.c_double(0)
@@ -259,15 +263,15 @@ def run_ours(args, rank, world, local_rank):
             t = torch.tensor([e2e_ms], device=dev)
             dist.all_reduce(t, op=dist.ReduceOp.MAX)
             e2e_ms = float(t.item())
-        # the e2e result must be the device result, bit for bit
-        assert torch.equal(out_h.view(torch.int64), out.cpu().view(torch.int64))
+        # the e2e result must be the device-resident path's, bit for bit
+        assert np.array_equal(out_h.numpy().view(np.int64), dev_out.view(np.int64))
         e2e = {"value": n * world / (e2e_ms / 1e3), "unit": "rows/s", "h2d_bytes_per_step": n * (4 + 8),
                "d2h_bytes_per_step": G * 8, "ms_per_step": e2e_ms}
         del keys_h, vals_h
 
     verify = None
-    if args.verify:
-        verify = verify_sampled(w, out, st)
+    if not args.no_verify and rank == 0:  # untimed: the timed step's state and results against the oracle
+        verify = verify_step(w, dev_state, dev_out, args.oracle_threads)
 
     result = None
     if rank == 0:
@@ -322,22 +326,44 @@ def run_ours(args, rank, world, local_rank):
         }
         if verify is not None:
             result["verify"] = verify
+            result["bit_exact"] = verify["bit_exact"]
     if dist is not None:
         dist.destroy_process_group()
     return result
 
 
-def verify_sampled(w, out, st):
-    """Check a sample of groups against the CPU oracle (rows gathered per group)."""
+def verify_step(w, state_bytes, got, threads=0):
+    """The last timed step's state and results against the CPU oracle.
+
+    Up to 2^20 groups the whole state is compared -- every group's K, flags
+    and 128-bit bins and every result, bit for bit -- with the C oracle run
+    on all rows (threads over row chunks, exact merge).  Beyond, the oracle's
+    per-thread tables would not fit comfortably, so the rows of a random
+    sample of 512 groups are gathered and those groups' results compared."""
     import numpy as np
     import torch
 
+    import paper_1802_09883_gb300 as R
     from oracle import oracle as O
 
-    G = w.G
+    G, L = w.G, w.L
+    nth = threads if threads and threads > 0 else (os.cpu_count() or 1)
+    t0 = time.perf_counter()
+    if G <= (1 << 20):
+        kh, vh = w.keys.cpu().numpy(), w.values.cpu().numpy()
+        ref = O.init(np.float64, L, G)
+        bad = O.groupby_sum(ref, kh, vh, threads=nth)
+        K, fl, lo, hi = R.parse_state(state_bytes, L, G)
+        oK, ofl, olo, ohi = O.to_bins(ref)
+        state_ok = bool(np.array_equal(K, oK) and np.array_equal(fl, ofl) and np.array_equal(lo, olo)
+                        and np.array_equal(hi, ohi))
+        res_ok = bool(np.array_equal(got.view(np.int64), O.finalize(ref).view(np.int64)))
+        return {"mode": "full state", "groups": G, "rows": int(kh.size), "bad_keys": int(bad),
+                "state_equal": state_ok, "results_equal": res_ok, "bit_exact": state_ok and res_ok and bad == 0,
+                "oracle": f"C oracle, {nth} host threads", "seconds": round(time.perf_counter() - t0, 2)}
     gen = torch.Generator(device="cpu")
     gen.manual_seed(17)
-    ngroups = min(G, 8 if G <= 1024 else 512)
+    ngroups = min(G, 512)
     sample = torch.randperm(G, generator=gen)[:ngroups].to(w.keys.device)
     remap = torch.full((G,), -1, dtype=torch.int32, device=w.keys.device)
     remap[sample] = torch.arange(ngroups, dtype=torch.int32, device=w.keys.device)
@@ -345,10 +371,11 @@ def verify_sampled(w, out, st):
     mask = sel >= 0
     k = sel[mask].cpu().numpy()
     v = w.values[mask].cpu().numpy()
-    ref = O.groupby_sum_values(k, v, ngroups, w.L, threads=os.cpu_count() or 1)
-    got = out[sample].cpu().numpy()
-    ok = np.array_equal(got.view(np.int64), ref.view(np.int64))
-    return {"groups": ngroups, "rows": int(k.size), "bit_exact": bool(ok)}
+    ref = O.groupby_sum_values(k, v, ngroups, L, threads=nth)
+    mine = got[sample.cpu().numpy()]
+    ok = bool(np.array_equal(mine.view(np.int64), ref.view(np.int64)))
+    return {"mode": "sampled groups", "groups": ngroups, "rows": int(k.size), "results_equal": ok, "bit_exact": ok,
+            "oracle": f"C oracle, {nth} host threads", "seconds": round(time.perf_counter() - t0, 2)}
 
 
 # the sources each profiled kernel is compiled from
@@ -694,7 +721,7 @@ def run_serve(args, local_rank):
     res.update({"serving": {"capacity_requests_per_s": rate, "closed_loop": {k: closed[k] for k in (
                     "p50_ms", "p99_ms", "mean_ms", "rows_per_s", "span_s")}, "poisson": open_runs,
                     "server": {k: stats[k] for k in ("iterations", "batch_launches", "large_calls",
-                                                     "memory_peak", "memory_budget")}},
+                                                     "memory_peak", "memory_budget", "memory_server_peak")}},
                 "verify": {"queries_checked": len(sample), "bit_equal_alone_and_in_mix": bool(same)},
                 "e2e": {"value": closed["rows_per_s"], "unit": "rows/s", "h2d_bytes_per_step": 0,
                         "d2h_bytes_per_step": sum(q[2] for q in queries) * 8,

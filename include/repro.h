@@ -204,11 +204,14 @@ repro_status groupby_sum_decimal64(const int32_t* keys, const int64_t* values, i
  * when needed so that they fit.  Limits: keys and values 16-byte aligned,
  * and a group table that fits the single-pass path (num_groups up to a few
  * thousand, depending on L and dtype) with num_groups * (8 + 16 L) <= 16 MiB;
- * otherwise REPRO_ERANGE and nothing is enqueued.  The first call on a device
- * looks the array's address up with cudaGetSymbolAddress, so make it before
- * any stream capture.  Every call uses the same array: calls that overlap
- * on the GPU race (serialise them on one stream).  Nothing needs clearing
- * between calls.
+ * otherwise REPRO_ERANGE and nothing is enqueued.  Each call that is not
+ * under stream capture looks the array's address up (cudaGetSymbolAddress,
+ * with the device current), so a context created after cudaDeviceReset is
+ * served correctly; a call under capture reuses the address of the last
+ * uncaptured call on that device, so make one such call on each device
+ * before any capture (else REPRO_ECUDA).  Every call uses the same array:
+ * calls that overlap on the GPU race (serialise them on one stream).
+ * Nothing needs clearing between calls.
  */
 repro_status repro_groupby_sum_noalloc(const int32_t* keys, const void* values, int64_t n,
                                        repro_dtype dtype, int L, int64_t num_groups, void* state,
@@ -414,8 +417,16 @@ typedef struct {
     int64_t iterations;     /* scheduler iterations issued */
     int64_t batch_launches; /* multi-task launches */
     int64_t large_calls;    /* partitioned-path chunk calls */
+    /* Device memory, bytes: in use now and the peak -- the admitted queries'
+       charges (state + one chunk's partitioned-path scratch each) plus the
+       server's own buffers (iteration plans and partial tables, held until
+       destroy; partition-pass scratch while its iteration is in flight).
+       Admission keeps this within memory_budget, except that a query is
+       always admitted when no other one is, so the peak can exceed the
+       budget by at most memory_server_peak. */
     int64_t memory_in_use, memory_peak, memory_budget;
     int32_t active, waiting; /* admitted and not finished; arrived and not admitted */
+    int64_t memory_server_peak; /* peak of the server's own buffers alone */
 } repro_server_stats;
 
 /* Monotonic clock of the server's timestamps, in nanoseconds. */

@@ -322,5 +322,20 @@ __device__ void flush_partial(unsigned char* part, int G, const Table& t, const 
     }
 }
 
+// An empty record for every group (window kNoWindow, no flags, zero bins):
+// what a CTA that gave up on a wait leaves as its partial, so that the merge
+// adds nothing.  Consumer threads only.
+template <int L>
+__device__ void write_empty_partial(unsigned char* part, int G, int ctid, int NC) {
+    constexpr size_t rec = 8 + 16 * L;
+    for (int g = ctid; g < G; g += NC) {
+        unsigned char* r = part + (size_t)g * rec;
+        *reinterpret_cast<int*>(r) = kNoWindow;
+        *reinterpret_cast<unsigned*>(r + 4) = 0u;
+        long long* pb = reinterpret_cast<long long*>(r + 8);
+#pragma unroll
+        for (int j = 0; j < 2 * L; ++j) pb[j] = 0;
+    }
+}
 
 }  // namespace rp

@@ -18,6 +18,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cstdint>
 #include <cstdio>
 #include <cstdlib>
@@ -43,6 +44,8 @@ struct FusedArgs {
     long long flush_rows;     // flush the int64 table into the partial before this many rows
     unsigned char* partials;  // [gridDim.x][G] records of 8 + 16 L bytes
     unsigned* errors;         // state header error word
+    unsigned long long wait_ns;  // limit of every mbarrier wait
+    int stall_tile;           // failure injection: the producer issues no tile from this index on (-1: off)
 };
 
 }  // namespace
@@ -110,7 +113,8 @@ __global__ void __launch_bounds__(32 * (NCW + 1), NCW == 8 ? 3 : 1) k_fused(Fuse
             int s = 0;         // stage of tile i (i mod S, kept without a division)
             uint32_t par = 0;  // parity of the ring round i / S
             for (int i = 0; i < ntile; ++i) {
-                if (i >= S && !mbar_wait_bounded(&empty[s], par ^ 1u, kWaitNs)) {
+                if (i == a.stall_tile) break;  // injected failure: the consumers' waits run out
+                if (i >= S && !mbar_wait_bounded(&empty[s], par ^ 1u, a.wait_ns)) {
                     // consumers will time out on the stages never filled
                     atomicOr(a.errors, REPRO_ERR_TIMEOUT);
                     break;
@@ -127,7 +131,7 @@ __global__ void __launch_bounds__(32 * (NCW + 1), NCW == 8 ? 3 : 1) k_fused(Fuse
             }
             // never leave with a copy in flight
             for (int i = max(0, issued - S); i < issued; ++i)
-                if (!mbar_wait_bounded(&full[i % S], (i / S) & 1, kWaitNs)) break;
+                if (!mbar_wait_bounded(&full[i % S], (i / S) & 1, a.wait_ns)) break;
         }
         return;
     }
@@ -155,7 +159,7 @@ __global__ void __launch_bounds__(32 * (NCW + 1), NCW == 8 ? 3 : 1) k_fused(Fuse
             rows_since_flush = 0;
             named_bar_sync(1, NC);
         }
-        const bool ok = mbar_wait_bounded(&full[s], par, kWaitNs);
+        const bool ok = mbar_wait_bounded(&full[s], par, a.wait_ns);
         int* cnt = &ctl[2 * c3];
         const int32_t* tk = skeys + (size_t)s * R;
         const T* tv = svals + (size_t)s * R;
@@ -228,7 +232,13 @@ __global__ void __launch_bounds__(32 * (NCW + 1), NCW == 8 ? 3 : 1) k_fused(Fuse
     }
     if (__any_sync(0xffffffffu, bad_key) && (ctid & 31) == 0) atomicOr(a.errors, REPRO_ERR_KEY);
     named_bar_sync(1, NC);
-    if (*abort_flag) return;
+    if (*abort_flag) {
+        // the state is flagged; this CTA's partial adds nothing to it (rows
+        // flushed before the time-out included), so the merge leaves the
+        // state's bins as they were
+        write_empty_partial<L>(a.partials + (size_t)blockIdx.x * G * (8 + 16 * L), G, ctid, NC);
+        return;
+    }
     flush_partial<L>(a.partials + (size_t)blockIdx.x * G * (8 + 16 * L), G, tab, sK, sF, first_flush, ctid, NC);
 }
 
@@ -386,6 +396,33 @@ long long env_flush_rows() {
     return v;
 }
 
+// Test aids, read once per process: REPRO_FUSED_CTAS caps the grid (so that
+// one CTA takes many rows); REPRO_WAIT_NS shortens every bounded wait and
+// REPRO_STALL_TILE makes each CTA's producer stop issuing at that tile, so a
+// test can make the consumers' waits run out and check REPRO_ETIMEOUT.
+long long env_ll(const char* name, long long dflt) {
+    const char* e = getenv(name);
+    return e ? atoll(e) : dflt;
+}
+
+int env_max_ctas() {
+    static const int v = (int)env_ll("REPRO_FUSED_CTAS", 0);
+    return v;
+}
+
+unsigned long long env_wait_ns() {
+    static const long long v = env_ll("REPRO_WAIT_NS", 0);
+    return v > 0 ? (unsigned long long)v : kWaitNs;
+}
+
+// the stall applies to the first REPRO_STALL_LAUNCHES launches (default 1)
+int env_stall_tile() {
+    static const int v = (int)env_ll("REPRO_STALL_TILE", -1);
+    static std::atomic<long long> left{env_ll("REPRO_STALL_LAUNCHES", 1)};
+    if (v < 0) return -1;
+    return left.fetch_sub(1) > 0 ? v : -1;
+}
+
 template <typename T, int L, int NCW, bool SQ>
 cudaError_t launch_fused_t(const FusedArgs& a0, int ctas, size_t smem, cudaStream_t s) {
     auto kern = k_fused<T, L, NCW, SQ>;
@@ -503,11 +540,14 @@ cudaError_t launch_groupby_fused(const int32_t* keys, const void* vals, long lon
     int ctas = fused_ctas(a.ntiles, cfg, di);
     ctas = std::min(ctas, di.sms * std::min(occ, cfg.ctas_per_sm));
     if (max_ctas > 0 && ctas > max_ctas) ctas = max_ctas;
+    if (env_max_ctas() > 0 && ctas > env_max_ctas()) ctas = env_max_ctas();
     a.tiles_per_cta = (int)((a.ntiles + ctas - 1) / ctas);
     const long long fr = env_flush_rows();
     a.flush_rows = fr > 0 ? fr : (1ll << 23);
     a.partials = (unsigned char*)scratch;
     a.errors = &reinterpret_cast<repro_state_header*>(state)->errors;
+    a.wait_ns = env_wait_ns();
+    a.stall_tile = env_stall_tile();
     cudaError_t e = dtype == REPRO_F64 ? dispatch_L<double>(L, cfg.ncw, a, ctas, smem, s, square)
                                        : dispatch_L<float>(L, cfg.ncw, a, ctas, smem, s, square);
     if (e != cudaSuccess) return e;
@@ -562,9 +602,13 @@ namespace rp {
 constexpr size_t kStaticPartialBytes = 16u << 20;  // 16 MiB
 static __device__ __align__(256) unsigned char g_static_partials[kStaticPartialBytes];
 
-// Host-side device address of g_static_partials, looked up once per device
-// (with that device current) -- the symbol itself is only a host stand-in.
-static void* static_partials_address(cudaError_t& err) {
+// Host-side device address of g_static_partials -- the symbol itself is
+// only a host stand-in.  Looked up with the device current on every call
+// that is not being captured into a CUDA graph (a new context after
+// cudaDeviceReset gets a fresh address); a call under stream capture uses
+// the address an earlier uncaptured call on that device looked up, and
+// fails with REPRO_ECUDA if there was none.
+static void* static_partials_address(cudaStream_t stream, cudaError_t& err) {
     static void* addr[64] = {};
     static std::mutex mu;
     int dev = 0;
@@ -574,12 +618,18 @@ static void* static_partials_address(cudaError_t& err) {
         err = cudaErrorInvalidDevice;
         return nullptr;
     }
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    err = cudaStreamIsCapturing(stream, &cap);
+    if (err != cudaSuccess) return nullptr;
     std::lock_guard<std::mutex> lock(mu);
-    if (!addr[dev]) {
+    if (cap == cudaStreamCaptureStatusNone) {
         void* p = nullptr;
         err = cudaGetSymbolAddress(&p, g_static_partials);
         if (err != cudaSuccess) return nullptr;
         addr[dev] = p;
+    } else if (!addr[dev]) {
+        err = cudaErrorStreamCaptureUnsupported;
+        return nullptr;
     }
     err = cudaSuccess;
     return addr[dev];
@@ -605,7 +655,7 @@ extern "C" repro_status repro_groupby_sum_noalloc(const int32_t* keys, const voi
     const long long max_ctas = (long long)(kStaticPartialBytes / per_cta);
     if (max_ctas < 1) return REPRO_ERANGE;
     cudaError_t e;
-    void* scratch = static_partials_address(e);
+    void* scratch = static_partials_address((cudaStream_t)stream, e);
     if (!scratch) return REPRO_ECUDA;
     e = launch_groupby_fused(keys, values, n, dtype, L, num_groups, cfg, state, scratch, (cudaStream_t)stream,
                              (int)(max_ctas < 65535 ? max_ctas : 65535));

@@ -106,6 +106,7 @@ struct Arena {
 struct Iter {
     std::vector<Arena*> arenas;
     cudaEvent_t ev[kLanes] = {};
+    long long pass_bytes = 0;  // partition-pass scratch of this iteration, charged until it retires
 };
 
 struct Server;
@@ -131,6 +132,9 @@ struct Server {
     std::unordered_map<uint64_t, std::unique_ptr<Req>> reqs;
     std::vector<int> free_slots;
     long long in_use = 0, peak = 0;
+    // the server's own device buffers: iteration arenas (held until destroy)
+    // and the partition-pass scratch of iterations in flight
+    long long own = 0, own_peak = 0;
     int admitted = 0;  // admitted and not yet completed
     uint64_t next_id = 1;
     bool stop = false;
@@ -155,6 +159,15 @@ struct Server {
         return e;
     }
 
+    // Charge (bytes > 0) or release the server's own device memory; the
+    // footprint's peak counts it with the admitted queries' charges.
+    void charge_own(long long bytes) {
+        std::lock_guard<std::mutex> lk(mu);
+        own += bytes;
+        own_peak = std::max(own_peak, own);
+        peak = std::max(peak, in_use + own);
+    }
+
     Arena* take_arena() {
         if (!free_arenas.empty()) {
             Arena* a = free_arenas.back();
@@ -174,6 +187,7 @@ struct Server {
                 free_events.push_back(e);
             }
         for (Arena* a : it.arenas) free_arenas.push_back(a);
+        if (it.pass_bytes) charge_own(-it.pass_bytes);
         inflight.pop_front();
     }
 
@@ -228,9 +242,12 @@ struct Server {
         if (a->dev_cap < dev_need) {
             if (a->dev) cudaFreeAsync(a->dev, stream[0]);
             a->dev = nullptr;
+            const long long old_cap = (long long)a->dev_cap;
             a->dev_cap = std::max(dev_need, a->dev_cap * 2);
+            charge_own((long long)a->dev_cap - old_cap);
             e = cudaMallocFromPoolAsync((void**)&a->dev, a->dev_cap, pool, stream[0]);
             if (e != cudaSuccess) {
+                charge_own(-(long long)a->dev_cap);
                 a->dev_cap = 0;
                 return e;
             }
@@ -281,6 +298,8 @@ struct Server {
             }
         }
         void* scratch = nullptr;
+        it.pass_bytes += (long long)bp.scratch_bytes();
+        charge_own((long long)bp.scratch_bytes());
         e = cudaMallocFromPoolAsync(&scratch, bp.scratch_bytes(), pool, s);
         if (e == cudaSuccess) e = bp.upload_async(scratch, a->host, s);
         if (e == cudaSuccess) e = bp.launch(scratch, s);
@@ -399,15 +418,18 @@ struct Server {
                         waitq.push_back(pending.begin()->second);
                         pending.erase(pending.begin());
                     }
+                    // the server's own buffers count against the budget; a query
+                    // is always admitted when no other one is (progress)
                     while (!waitq.empty() && admitted < cfg.max_active && !free_slots.empty() &&
-                           in_use + (long long)waitq.front()->need <= cfg.memory_budget) {
+                           (admitted == 0 ||
+                            in_use + own + (long long)waitq.front()->need <= cfg.memory_budget)) {
                         Req* r = waitq.front();
                         waitq.pop_front();
                         r->slot = free_slots.back();
                         free_slots.pop_back();
                         r->admit_ns = now_ns();
                         in_use += (long long)r->need;
-                        peak = std::max(peak, in_use);
+                        peak = std::max(peak, in_use + own);
                         ++admitted;
                         admitted_now.push_back(r);
                     }
@@ -635,8 +657,9 @@ repro_status repro_server_stats_get(repro_server srv, repro_server_stats* out) {
     Server& S = srv->s;
     std::lock_guard<std::mutex> lk(S.mu);
     *out = S.st;
-    out->memory_in_use = S.in_use;
+    out->memory_in_use = S.in_use + S.own;
     out->memory_peak = S.peak;
+    out->memory_server_peak = S.own_peak;
     out->active = S.admitted;
     out->waiting = (int32_t)S.waitq.size();
     return REPRO_OK;

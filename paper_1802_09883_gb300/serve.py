@@ -33,7 +33,8 @@ class ServerStats(ctypes.Structure):
     _fields_ = [("submitted", ctypes.c_int64), ("completed", ctypes.c_int64), ("iterations", ctypes.c_int64),
                 ("batch_launches", ctypes.c_int64), ("large_calls", ctypes.c_int64),
                 ("memory_in_use", ctypes.c_int64), ("memory_peak", ctypes.c_int64),
-                ("memory_budget", ctypes.c_int64), ("active", ctypes.c_int32), ("waiting", ctypes.c_int32)]
+                ("memory_budget", ctypes.c_int64), ("active", ctypes.c_int32), ("waiting", ctypes.c_int32),
+                ("memory_server_peak", ctypes.c_int64)]
 
 
 def now_ns() -> int:

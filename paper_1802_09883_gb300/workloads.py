@@ -43,6 +43,20 @@ def random_values(n: int, e_lo: int, e_hi: int, gen: torch.Generator, device,
     raise ValueError("dtype must be float64 or float32")
 
 
+def binade_top_values(n: int, e: int, m_min: float, gen: torch.Generator, device, sign: int = 0) -> torch.Tensor:
+    """n float64 values s * M * 2^e with M uniform in [m_min, 2) (all fraction
+    bits random above that floor): magnitudes packed at the top of one binade.
+    sign = +1 or -1 fixes the sign, 0 draws it."""
+    lo = int((m_min - 1.0) * (1 << 52))
+    frac = torch.randint(lo, 1 << 52, (n,), generator=gen, device=device, dtype=torch.int64)
+    if sign == 0:
+        s = torch.randint(0, 2, (n,), generator=gen, device=device, dtype=torch.int64)
+    else:
+        s = torch.full((n,), 1 if sign < 0 else 0, device=device, dtype=torch.int64)
+    bits = (s << 63) | ((e + 1023) << 52) | frac
+    return bits.view(torch.float64)
+
+
 def uniform_keys(n: int, G: int, gen, device) -> torch.Tensor:
     """Keys uniform in [0, G) (Sec. VI-A)."""
     return torch.randint(0, G, (n,), generator=gen, device=device, dtype=torch.int32)

@@ -449,3 +449,28 @@ def test_zero_heavy_columns_match_oracle(dtype, G):
     ost, _ = oracle_state(_np(keys), _np(vals), G, 3, threads=8)
     assert_state_equal(st, ost)
     assert_bits_equal(_np(out), O.finalize(ost))
+
+
+# ------------------------------------------------- the benchmark's own cell
+
+def test_bench_headline_cell_full_state():
+    """The workload bench.py times by default -- 2^28 rows, 1024 groups
+    uniform, repro<double,3>, the same seed -- every group's state (K, flags,
+    128-bit bins) and result against the threaded C oracle, in the built-in
+    configuration and in the one the autotuner picks (which bench.py times)."""
+    import os
+    w = WL.sweep_cell(1 << 10, "uniform", 3, n=1 << 28, device=DEV)
+    ost, bad = oracle_state(_np(w.keys), _np(w.values), w.G, w.L, threads=os.cpu_count() or 1)
+    assert bad == 0
+    st, out = run_gpu(w.keys, w.values, w.G, w.L)
+    assert st.check() == 0
+    assert_state_equal(st, ost)
+    assert_bits_equal(_np(out), O.finalize(ost))
+    R.tune_clear()
+    try:
+        R.tune(w.keys, w.values, w.G, w.L)
+        st2, out2 = run_gpu(w.keys, w.values, w.G, w.L)
+    finally:
+        R.tune_clear()
+    assert_state_equal(st2, ost)
+    assert_bits_equal(_np(out2), O.finalize(ost))

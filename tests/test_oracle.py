@@ -178,3 +178,47 @@ def test_tie_heavy_input_is_order_independent():
     want = X.groupby_sum(np.zeros(vals.size, int), vals, 1, L, X.DOUBLE)[0]
     K, fl, lo, hi = O.to_bins(st)
     assert _oracle_T(lo, hi)[0] == want.T
+
+
+def test_oracle_levels_beyond_2p63():
+    """Bins past int64: the C oracle's carry counts, its 128-bit bin view and
+    its finalize against the exact model's digits times multiplicities.
+
+    Six values packed at the top of the window with top grid index 27 (top
+    digit close to 2^(W-1)), each repeated millions of times; group 0 sums
+    them positive, group 1 negative (both pass 2^64 at level 0), group 2
+    mixes signs and smaller values.  Algorithm 2 keeps S in [1.5, 1.75) ufp
+    and counts the carries in C, so T = (S - 1.5 ufp)/ulp + C 2^(m-2) must
+    reach these magnitudes exactly."""
+    fmt = X.DOUBLE
+    rs = np.random.default_rng(63)
+    tops = rs.uniform(1.9, 2.0, 6) * 2.0 ** 44  # |b| / u(27) in [1.9, 2) 2^38
+    small = rs.uniform(1.0, 2.0, 6) * np.exp2(rs.integers(-30, 20, 6))
+    mult = rs.integers(1 << 22, 1 << 23, 6)
+    L, G = 3, 3
+    parts_k, parts_v, want = [], [], []
+    for g, (vals, signs) in enumerate(((tops, np.ones(6)), (tops, -np.ones(6)),
+                                      (np.concatenate([tops, small]), np.tile([1.0, -1.0], 6)))):
+        m = mult if g < 2 else np.concatenate([mult, mult[::-1]]) >> 8
+        v = np.repeat(vals * signs, m)
+        parts_k.append(np.full(v.size, g, np.int32))
+        parts_v.append(v)
+        K = max(X.top_index(fmt, X.Fraction(float(x))) for x in vals)
+        T = [0] * L
+        for x, c in zip(vals * signs, m):
+            for j, d in enumerate(X.digits(fmt, X.Fraction(float(x)), K, L)):
+                T[j] += int(c) * d
+        want.append(X.GroupState(K, 0, T))
+    keys = np.concatenate(parts_k)
+    vals = np.concatenate(parts_v)
+    perm = rs.permutation(keys.size)
+    keys, vals = keys[perm], vals[perm]
+    st = O.init(np.float64, L, G)
+    assert O.groupby_sum(st, keys, vals, threads=8) == 0
+    K, fl, lo, hi = O.to_bins(st)
+    got_T = _oracle_T(lo, hi)
+    assert [w.K for w in want] == K.tolist()
+    assert [w.T for w in want] == got_T
+    assert got_T[0][0] > 1 << 63 and got_T[1][0] < -(1 << 63)  # past int64: a nonzero high word
+    res = np.array([X.to_float(X.finalize(w, L, fmt), fmt) for w in want])
+    assert _same_bits(O.finalize(st), res)
