@@ -315,16 +315,32 @@ repro_status repro_finalize(const void* state, repro_dtype dtype, int L, int64_t
 repro_status repro_state_check(const void* state, uint32_t* errors_out, void* stream);
 
 /* Conventional, NON-reproducible grouped SUM: out[g] = sum of values[i]
-   with keys[i] == g, added with floating-point atomics in whatever order
-   the GPU runs them (the "built-in" baseline the paper compares against,
-   Sec. VI-D).  out (double[num_groups]) is overwritten.  Rows with a key
-   outside [0, num_groups) are skipped. */
+   with keys[i] == g, added with built-in floating-point adds in whatever
+   order the GPU runs them (the "built-in" baseline the paper compares
+   against, Sec. VI-C and VI-D).  out (double[num_groups]) is overwritten.
+   Rows with a key outside [0, num_groups) are skipped.  Same input handling
+   as the reproducible kernels (16-byte vector loads when keys and values
+   are 16-byte aligned, persistent grid); the table strategy is picked by
+   group count: one shared-memory copy per lane for small tables, one shared
+   table with equal keys of a warp combined first up to the shared-memory
+   limit, global atomics (again combined per warp) beyond. */
 repro_status groupby_sum_fp64(const int32_t* keys, const double* values, int64_t n,
                               int64_t num_groups, double* out, void* stream);
 
 /* Float variant of the conventional baseline (float accumulators). */
 repro_status groupby_sum_fp32(const int32_t* keys, const float* values, int64_t n,
                               int64_t num_groups, float* out, void* stream);
+
+/* The conventional baseline with an explicit table strategy, so that a
+   benchmark can time them all and keep the fastest: mode 0 shared table
+   (one copy per lane when the copies fit), 1 shared table with equal keys
+   combined per warp (__match_any_sync), 2 one shared table per warp (plain
+   adds after the combining), 3 global atomics, 4 global atomics after the
+   combining.  values: double or float per dtype; out: num_groups of that
+   type, overwritten.  REPRO_ERANGE if the mode's tables do not fit in shared
+   memory for num_groups, REPRO_EINVAL for a bad mode or argument. */
+repro_status groupby_sum_fp_mode(const int32_t* keys, const void* values, int64_t n, repro_dtype dtype,
+                                 int64_t num_groups, int mode, void* out, void* stream);
 
 /*
  * SQL aggregates from reproducible sums.  The paper observes that with a

@@ -76,6 +76,7 @@ def lib(build_if_stale: bool = True):
         L.repro_state_check.argtypes = [vp, u32p, vp]
         L.groupby_sum_fp64.argtypes = [vp, vp, i64, i64, vp, vp]
         L.groupby_sum_fp32.argtypes = [vp, vp, i64, i64, vp, vp]
+        L.groupby_sum_fp_mode.argtypes = [vp, vp, i64, i32, i64, i32, vp, vp]
         L.repro_batch_prepare.argtypes = [vp, i32, i32, i32, ctypes.POINTER(vp)]
         L.repro_batch_run.argtypes = [vp, vp]
         L.repro_batch_destroy.argtypes = [vp]
@@ -119,7 +120,7 @@ def lib(build_if_stale: bool = True):
                      "repro_finalize", "repro_batch_prepare", "repro_batch_run", "repro_batch_destroy",
                      "repro_batch_reset", "repro_batch_set_outputs", "repro_batch_finalize", "repro_batch_describe",
                      "repro_groupby_sum_batched", "repro_groupby_sum_cols", "repro_release_cached_memory",
-                     "repro_state_check", "groupby_sum_fp64", "groupby_sum_fp32", "repro_server_create",
+                     "repro_state_check", "groupby_sum_fp64", "groupby_sum_fp32", "groupby_sum_fp_mode", "repro_server_create",
                      "repro_server_submit", "repro_server_poll", "repro_server_wait", "repro_server_release",
                      "repro_server_stats_get", "repro_server_destroy", "repro_tune_groupby", "repro_tune_save",
                      "repro_tune_load", "repro_batch_tune", "repro_stats_init", "repro_groupby_stats",
@@ -302,7 +303,7 @@ def groupby_sum(keys: torch.Tensor, values: torch.Tensor, num_groups: int, L: in
 
 def groupby_sum_fp64(keys: torch.Tensor, values: torch.Tensor, num_groups: int,
                      out: Optional[torch.Tensor] = None) -> torch.Tensor:
-    """Conventional (non-reproducible) float64 atomic GroupBy baseline."""
+    """Conventional (non-reproducible) float64 GroupBy baseline."""
     _require_cuda(keys, "keys")
     _require_cuda(values, "values")
     if out is None:
@@ -314,13 +315,33 @@ def groupby_sum_fp64(keys: torch.Tensor, values: torch.Tensor, num_groups: int,
 
 def groupby_sum_fp32(keys: torch.Tensor, values: torch.Tensor, num_groups: int,
                      out: Optional[torch.Tensor] = None) -> torch.Tensor:
-    """Conventional (non-reproducible) float32 atomic GroupBy baseline."""
+    """Conventional (non-reproducible) float32 GroupBy baseline."""
     _require_cuda(keys, "keys")
     _require_cuda(values, "values")
     if out is None:
         out = torch.empty(num_groups, dtype=torch.float32, device=values.device)
     _check(lib().groupby_sum_fp32(keys.data_ptr(), values.data_ptr(), keys.numel(), num_groups, out.data_ptr(),
                                   _stream(values.device)), "groupby_sum_fp32")
+    return out
+
+
+FP_MODES = {0: "shared table (one copy per lane when they fit)", 1: "shared table, equal keys combined per warp",
+            2: "one shared table per warp", 3: "global atomics", 4: "global atomics, equal keys combined per warp"}
+
+
+def groupby_sum_fp_mode(keys: torch.Tensor, values: torch.Tensor, num_groups: int, mode: int,
+                        out: Optional[torch.Tensor] = None) -> Optional[torch.Tensor]:
+    """The conventional baseline with an explicit table strategy (FP_MODES);
+    None when that strategy's tables do not fit for num_groups."""
+    _require_cuda(keys, "keys")
+    _require_cuda(values, "values")
+    if out is None:
+        out = torch.empty(num_groups, dtype=values.dtype, device=values.device)
+    st = lib().groupby_sum_fp_mode(keys.data_ptr(), values.data_ptr(), keys.numel(), _dtype_code(values.dtype),
+                                   num_groups, mode, out.data_ptr(), _stream(values.device))
+    if st == 3:  # REPRO_ERANGE
+        return None
+    _check(st, "groupby_sum_fp_mode")
     return out
 
 

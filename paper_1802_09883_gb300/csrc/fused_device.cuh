@@ -18,19 +18,24 @@ constexpr uint64_t kWaitNs = 2000000000ull;  // every mbarrier wait gives up aft
 
 struct FusedSmem {
     // byte offsets into dynamic shared memory
-    size_t bars, ctl, keys, vals, bins, K, Kp, F, dlist, rlist, total;
+    size_t bars, ctl, keys, vals, bins, K, Kp, F, dlist, slist, rlist, total;
 };
 
 __host__ __device__ inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
+// pad: the single-task kernel's table -- two spare levels after each group's
+// L levels and one spare group after the last, so that a row's three digit
+// adds always have table words at fixed offsets from its group's window
+// level (digits past the window land in the spare levels, rows with nothing
+// to add in the spare group; neither is ever read back).
 template <typename T>
-__host__ __device__ inline FusedSmem fused_layout(int S, int R, int G, int L, int C) {
+__host__ __device__ inline FusedSmem fused_layout(int S, int R, int G, int L, int C, bool pad = false) {
     FusedSmem m;
     size_t o = 0;
     m.bars = o;
     o += 16 * (size_t)S;  // full[S], empty[S]
     m.ctl = o;
-    o += 64;  // counters[3][2], abort, pad
+    o += 64;  // counters[3][2], abort, pad, slow-list counters[3]
     o = align_up(o, 128);
     m.keys = o;
     o += (size_t)S * R * 4;
@@ -38,8 +43,8 @@ __host__ __device__ inline FusedSmem fused_layout(int S, int R, int G, int L, in
     m.vals = o;
     o += (size_t)S * R * sizeof(T);
     o = align_up(o, 16);
-    m.bins = o;  // LO[G][L][C] (uint32) then HI[G][L][C] (int32)
-    o += (size_t)G * L * C * 8;
+    m.bins = o;  // LO[G][L][C] (uint32) then HI[G][L][C] (int32); padded: [G + 1][L + 2][C]
+    o += (size_t)(pad ? G + 1 : G) * (pad ? L + 2 : L) * C * 8;
     m.K = o;
     o += (size_t)G * 4;
     m.Kp = o;
@@ -47,6 +52,8 @@ __host__ __device__ inline FusedSmem fused_layout(int S, int R, int G, int L, in
     m.F = o;
     o += (size_t)G * 4;
     m.dlist = o;
+    o += (size_t)R * 2;
+    m.slist = o;
     o += (size_t)R * 2;
     o = align_up(o, 4);
     m.rlist = o;
@@ -243,6 +250,112 @@ __device__ __forceinline__ void consume_quad(const SAddr& sa, const int32_t* tk,
     for (int i = 0; i < 12; ++i) {
         const int h = hi[i] + (int)((unsigned)(old[i] + lo[i]) < old[i]);
         red_add_if(on[i] && h != 0, sa.hi + at[i], h);
+    }
+}
+
+// The two halves of adding digit (lo, hi) to a table word pair: a shared
+// atomic on the LO word returns its old value; hi plus the carry out of
+// old + lo then goes to the HI word with a reduction.  Unconditional (a
+// digit that must not be added arrives as zero, at a word of its own group),
+// so no predicate is needed.  Split in two so that a row's three atomics are
+// in flight together before their carries are needed; the asm blocks are
+// ordered among themselves (volatile), and the phases around them are
+// separated by barriers.
+__device__ __forceinline__ unsigned table_add_lo(uint32_t lo_addr, unsigned lo) {
+    unsigned old;
+    asm volatile("atom.shared.add.u32 %0, [%1], %2;" : "=r"(old) : "r"(lo_addr), "r"(lo));
+    return old;
+}
+
+__device__ __forceinline__ void table_add_hi(uint32_t hi_addr, unsigned old, unsigned lo, int hi) {
+    int h;
+    asm("{\n\t.reg .u32 t;\n\t"
+        "add.cc.u32 t, %1, %2;\n\t"
+        "addc.s32 %0, %3, 0;\n\t}"
+        : "=r"(h)
+        : "r"(old), "r"(lo), "r"(hi));
+    asm volatile("red.shared.add.s32 [%0], %1;" ::"r"(hi_addr), "r"(h));
+}
+
+// Biased exponent E and t = E + (fraction bits); K(b) = floor(t / W) by
+// multiply-shift.  E == 0 (zero, subnormal) and E all ones (Inf, NaN) are
+// left to the caller's checks: an all-ones E gives K(b) = KMAX + 1.
+template <typename T>
+struct Expo;
+template <>
+struct Expo<double> {
+    static __device__ __forceinline__ void get(uint32_t vhi, int& E, int& t, int& kb) {
+        E = (int)((vhi >> 20) & 0x7ffu);
+        t = E + 52;
+        // t / 40 as the high word of t * ceil(2^32 / 40): exact for t < 2^12
+        kb = (int)__umulhi((unsigned)t, 107374183u);
+    }
+};
+template <>
+struct Expo<float> {
+    static __device__ __forceinline__ void get(uint32_t bits, int& E, int& t, int& kb) {
+        E = (int)((bits >> 23) & 0xffu);
+        t = E + 23;
+        // t / 18 as the high word of t * ceil(2^32 / 18): exact for t < 2^12
+        kb = (int)__umulhi((unsigned)t, 238609295u);
+    }
+};
+
+// Phase A for four consecutive rows of a staged tile, row by row and
+// without branches on the common path (the table is the padded layout of
+// fused_layout; the copy count CC is fixed at compile time): a row whose key
+// is good, whose value is normal and inside its group's window adds its
+// three signed digits (Signed<T>) at fixed offsets from its top level; a
+// zero with a good key adds nothing (into the spare group); every other row
+// -- a bad key, a special or subnormal value, a group without a window yet,
+// a value above its group's window -- is put on the tile's slow list (its
+// counter at scnt_addr) for consume_row after the tile.  The digits of such
+// rows are computed too, from whatever their words hold, and added to the
+// spare group, which keeps the four rows' work straight-line.
+template <typename T, int L, int CC>
+__device__ __forceinline__ void consume_quad_fast(const SAddr& sa, int r0, int G, int copy, unsigned short* slist,
+                                                  uint32_t scnt_addr) {
+    constexpr uint32_t LP = L + 2;  // levels per group in the padded table
+    const uint4 k4 = lds_v4(sa.keys + 4u * (uint32_t)r0);
+    const int gq[4] = {(int)k4.x, (int)k4.y, (int)k4.z, (int)k4.w};
+    uint32_t vhi[4], vlo[4];
+    QuadWords<T>::load(sa.vals + (uint32_t)sizeof(T) * (uint32_t)r0, vhi, vlo);
+    const uint32_t hi_off = sa.hi - sa.lo;
+    unsigned slow = 0;  // bit q: row q goes to the slow list
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        int E, t, kb;
+        Expo<T>::get(vhi[q], E, t, kb);
+        const bool key_ok = (unsigned)gq[q] < (unsigned)G;
+        const unsigned gc = min((unsigned)gq[q], (unsigned)(G - 1));
+        const int K = (int)lds_u32(sa.K + 4u * gc);
+        const bool ok = key_ok && E != 0 && kb <= K;
+        unsigned lo[3];
+        int hi[3];
+        Signed<T>::digits(vhi[q], vlo[q], t, kb, lo, hi);
+        // the top digit's word: level K - kb of the row's group, or the spare
+        // group for a row with nothing to add (including a value so far below
+        // its window, K - kb >= L, that all its digits drop out); the other
+        // digits follow at fixed offsets (past the window: spare levels)
+        const bool adds = ok && K - kb < L;
+        const uint32_t tg = adds ? (uint32_t)gq[q] * LP + (uint32_t)(K - kb) : (uint32_t)G * LP;
+        const uint32_t a = sa.lo + 4u * (tg * CC + (uint32_t)copy);
+        constexpr int ND = L < 3 ? L : 3;
+        unsigned old[ND];
+#pragma unroll
+        for (int k = 0; k < ND; ++k) old[k] = table_add_lo(a + 4u * CC * k, lo[k]);
+#pragma unroll
+        for (int k = 0; k < ND; ++k) table_add_hi(a + hi_off + 4u * CC * k, old[k], lo[k], hi[k]);
+        slow |= (unsigned)(!ok && !(key_ok && Lean<T>::is_zero(vhi[q], vlo[q]))) << q;
+    }
+    if (slow) {  // rare: one branch per quad
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+            if (slow & (1u << q)) {
+                uint32_t idx;
+                asm volatile("atom.shared.add.u32 %0, [%1], 1;" : "=r"(idx) : "r"(scnt_addr) : "memory");
+                slist[idx] = (unsigned short)(r0 + q);
+            }
     }
 }
 

@@ -152,8 +152,8 @@ int groupby_dispatch(const int32_t* keys, const void* values, long long n, int d
     // each path's configuration is chosen once and passed on, so the scratch
     // size and the launch agree even if the tuned cache changes meanwhile
     FusedPlanConfig cfg;
-    if (n > 0 && fused_supported(dtype, L, num_groups, keys, values) &&
-        fused_plan_config(dtype, L, (int)num_groups, 0, cfg)) {
+    if (n > 0 && fused_supported(dtype, L, num_groups, keys, values, true) &&
+        fused_plan_config(dtype, L, (int)num_groups, 0, cfg, true)) {
         Scratch scratch(fused_scratch_bytes(cfg, L, num_groups, n), s);
         if (scratch.err != cudaSuccess) return from_cuda(scratch.err);
         return from_cuda(launch_groupby_fused(keys, values, n, dtype, L, num_groups, cfg, state, scratch.p, s));
@@ -243,7 +243,7 @@ repro_status repro_sum(const void* values, int64_t n, repro_dtype dtype, int L, 
     if (n == 0) return REPRO_OK;
     cudaStream_t s = (cudaStream_t)stream;
     FusedPlanConfig cfg;
-    if (fused_supported(dtype, L, 1, nullptr, values) && fused_plan_config(dtype, L, 1, 0, cfg)) {
+    if (fused_supported(dtype, L, 1, nullptr, values, true) && fused_plan_config(dtype, L, 1, 0, cfg, true)) {
         Scratch scratch(fused_scratch_bytes(cfg, L, 1, n), s);
         if (scratch.err != cudaSuccess) return from_cuda(scratch.err);
         return from_cuda(launch_groupby_fused(nullptr, values, n, dtype, L, 1, cfg, state, scratch.p, s));
@@ -355,6 +355,18 @@ repro_status groupby_sum_fp32(const int32_t* keys, const float* values, int64_t 
     if (!out || n < 0 || num_groups < 1 || num_groups > INT32_MAX) return REPRO_EINVAL;
     if (n > 0 && (!keys || !values)) return REPRO_EINVAL;
     return from_cuda(launch_groupby_fp32(keys, values, n, num_groups, out, (cudaStream_t)stream));
+}
+
+repro_status groupby_sum_fp_mode(const int32_t* keys, const void* values, int64_t n, repro_dtype dtype,
+                                 int64_t num_groups, int mode, void* out, void* stream) {
+    if (!out || n < 0 || num_groups < 1 || num_groups > INT32_MAX || !valid_dtype(dtype)) return REPRO_EINVAL;
+    if (n > 0 && (!keys || !values)) return REPRO_EINVAL;
+    if (mode < 0 || mode > 4) return REPRO_EINVAL;
+    if (!fp_mode_supported(dtype, mode, num_groups)) return REPRO_ERANGE;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (dtype == REPRO_F64)
+        return from_cuda(launch_groupby_fp64(keys, (const double*)values, n, num_groups, (double*)out, s, mode));
+    return from_cuda(launch_groupby_fp32(keys, (const float*)values, n, num_groups, (float*)out, s, mode));
 }
 
 const char* repro_strerror(repro_status status) {

@@ -301,6 +301,88 @@ struct Lean<float> {
     }
 };
 
+// ------------------------------------------ signed digits for the hot loop
+//
+// The same digits once more, with fewer operations: the sign is applied to
+// the significand before the shift (X is the two's complement of +-|b| /
+// u(kb - 2)), and the pieces and round-to-nearest-even carries are taken on
+// that signed X.  Rounding to nearest with ties to even is symmetric
+// (RNE(-x) = -RNE(x)), and on a two's complement X the floor-based pieces
+// with carry c = [rest > half, or rest == half and the part above is odd]
+// compute exactly RNE of the signed quotient, so the digits come out
+// negated for negative values without negating three digits afterwards.
+// Inputs: the value's words, t = E + 52 (double) / E + 23 (float) for its
+// biased exponent E >= 1, and kb = floor(t / W); the value must be normal.
+template <typename T>
+struct Signed;
+
+template <>
+struct Signed<double> {
+    static __device__ __forceinline__ void digits(uint32_t vhi, uint32_t vlo, int t, int kb, unsigned lo[3],
+                                                  int hi[3]) {
+        const uint32_t S = (uint32_t)((int)vhi >> 31);  // 0 or all ones
+        const uint32_t mh = (vhi & 0xfffffu) | 0x100000u;
+        uint32_t sl, sh;  // the significand with the value's sign, two's complement
+        asm("{\n\t.reg .u32 a, b;\n\t"
+            "xor.b32 a, %2, %4;\n\t"
+            "xor.b32 b, %3, %4;\n\t"
+            "sub.cc.u32 %0, a, %4;\n\t"
+            "subc.u32 %1, b, %4;\n\t}"
+            : "=r"(sl), "=r"(sh)
+            : "r"(vlo), "r"(mh), "r"(S));
+        // X = significand * 2^s, s = E + 79 - 40 kb in [27, 66]: shift by r
+        // within a word, then by q = 0, 1 or 2 whole words
+        const int s = t + 27 - 40 * kb;
+        const int r = s & 31, q = s >> 5;
+        const uint32_t v0 = sl << r;
+        const uint32_t v1 = __funnelshift_l(sl, sh, r);
+        const uint32_t v2 = __funnelshift_l(sh, S, r);
+        const uint32_t w0 = q == 0 ? v0 : 0u;
+        const uint32_t w1 = q == 0 ? v1 : (q == 1 ? v0 : 0u);
+        const uint32_t w2 = q == 0 ? v2 : (q == 1 ? v1 : v0);
+        const uint32_t w3 = q == 0 ? S : (q == 1 ? v2 : v1);
+        // 40-bit pieces: x0, x1 unsigned fields, x2 the signed part above
+        const uint32_t x0l = w0, x0h = w1 & 0xffu;
+        const uint32_t x1l = __funnelshift_r(w1, w2, 8), x1h = (w2 >> 8) & 0xffu;
+        const uint32_t x2l = __funnelshift_r(w2, w3, 16);
+        const int x2h = (int)w3 >> 16;
+        // carries at bits 40 and 80: [x + (2^39 - 1) + tie bit >= 2^40]
+        const uint32_t s1 = x1l & 1u;
+        const uint32_t s2b = (uint32_t)((x0h | x0l) != 0u) | (x2l & 1u);
+        const uint32_t c1 = (x0h + 0x7fu + (uint32_t)(((unsigned long long)x0l + 0xffffffffull + s1) >> 32)) >> 8;
+        const uint32_t c2 = (x1h + 0x7fu + (uint32_t)(((unsigned long long)x1l + 0xffffffffull + s2b) >> 32)) >> 8;
+        lo[0] = x2l + c2;
+        hi[0] = x2h + (int)(lo[0] < c2);
+        lo[1] = x1l + c1;
+        hi[1] = (int)x1h + (int)(lo[1] < c1) - 256 * (int)c2;
+        lo[2] = x0l;
+        hi[2] = (int)x0h - 256 * (int)c1;
+    }
+};
+
+template <>
+struct Signed<float> {
+    static __device__ __forceinline__ void digits(uint32_t bits, uint32_t, int t, int kb, unsigned lo[3], int hi[3]) {
+        const int M = (int)((bits & 0x7fffffu) | 0x800000u);
+        const int Ms = (int)bits < 0 ? -M : M;
+        const int s = t + 12 - 18 * kb;  // E + 35 - 18 kb in [12, 29]
+        const long long X = (long long)Ms << s;  // |X| < 2^53
+        const uint32_t xl = (uint32_t)X, xh = (uint32_t)((unsigned long long)X >> 32);
+        const int x0 = (int)(xl & 0x3ffffu);
+        const int x1 = (int)(__funnelshift_r(xl, xh, 18) & 0x3ffffu);
+        const int x2 = (int)xh >> 4;  // signed part above bit 36
+        const int c1 = (x0 + 0x1ffff + (x1 & 1)) >> 18;
+        const int c2 = (x1 + 0x1ffff + ((x0 != 0) | (x2 & 1))) >> 18;
+        const int d0 = x2 + c2, d1 = x1 + c1 - (c2 << 18), d2 = x0 - (c1 << 18);
+        lo[0] = (unsigned)d0;
+        hi[0] = d0 >> 31;
+        lo[1] = (unsigned)d1;
+        hi[1] = d1 >> 31;
+        lo[2] = (unsigned)d2;
+        hi[2] = d2 >> 31;
+    }
+};
+
 // ---------------------------------------------------------------- state view
 
 struct StateView {

@@ -52,31 +52,33 @@ struct FusedArgs {
 
 // SQ: sum x*x instead of x (each staged value squared in place, RN in T, by
 // the thread that consumes it; the sums behind VARIANCE / STDDEV).
-template <typename T, int L, int NCW, bool SQ>
-__global__ void __launch_bounds__(32 * (NCW + 1), NCW == 8 ? 3 : 1) k_fused(FusedArgs a) {
+// CC: copies of the table (a.C), fixed at compile time for the hot loop.
+template <typename T, int L, int NCW, bool SQ, int CC>
+__global__ void __launch_bounds__(32 * (NCW + 1), NCW == 8 ? 4 : 2) k_fused(FusedArgs a) {
     constexpr int NC = 32 * NCW;
     extern __shared__ __align__(128) unsigned char smem[];
-    const FusedSmem m = fused_layout<T>(a.S, a.R, a.G, L, a.C);
+    const FusedSmem m = fused_layout<T>(a.S, a.R, a.G, L, a.C, true);
     uint64_t* full = reinterpret_cast<uint64_t*>(smem + m.bars);
     uint64_t* empty = full + a.S;
-    int* ctl = reinterpret_cast<int*>(smem + m.ctl);  // cnt[3][2] at 0..5, abort at 6
+    int* ctl = reinterpret_cast<int*>(smem + m.ctl);  // cnt[3][2] at 0..5, abort at 6, slow counts[3] at 8..10
     int32_t* skeys = reinterpret_cast<int32_t*>(smem + m.keys);
     T* svals = reinterpret_cast<T*>(smem + m.vals);
     Table tab;
     tab.lo = reinterpret_cast<unsigned*>(smem + m.bins);
-    tab.hi = reinterpret_cast<int*>(tab.lo + (size_t)a.G * L * a.C);
-    tab.L = L;
+    tab.hi = reinterpret_cast<int*>(tab.lo + (size_t)(a.G + 1) * (L + 2) * a.C);
+    tab.L = L + 2;  // level stride of the padded table (levels L, L + 1 and group G are spare)
     tab.C = a.C;
     int* sK = reinterpret_cast<int*>(smem + m.K);
     int* sKp = reinterpret_cast<int*>(smem + m.Kp);
     unsigned* sF = reinterpret_cast<unsigned*>(smem + m.F);
     unsigned short* dlist = reinterpret_cast<unsigned short*>(smem + m.dlist);
+    unsigned short* slist = reinterpret_cast<unsigned short*>(smem + m.slist);
     int* rlist = reinterpret_cast<int*>(smem + m.rlist);
     volatile int* abort_flag = &ctl[6];  // consumers only
 
     const int tid = threadIdx.x;
     const int G = a.G, R = a.R, S = a.S;
-    for (int i = tid; i < G * L * a.C; i += blockDim.x) {
+    for (int i = tid; i < (G + 1) * (L + 2) * a.C; i += blockDim.x) {
         tab.lo[i] = 0;
         tab.hi[i] = 0;
     }
@@ -161,6 +163,7 @@ __global__ void __launch_bounds__(32 * (NCW + 1), NCW == 8 ? 3 : 1) k_fused(Fuse
         }
         const bool ok = mbar_wait_bounded(&full[s], par, a.wait_ns);
         int* cnt = &ctl[2 * c3];
+        int* scnt = &ctl[8 + c3];
         const int32_t* tk = skeys + (size_t)s * R;
         const T* tv = svals + (size_t)s * R;
         if (ok) {
@@ -174,18 +177,27 @@ __global__ void __launch_bounds__(32 * (NCW + 1), NCW == 8 ? 3 : 1) k_fused(Fuse
                 asm volatile("" ::: "memory");  // the stores stay ahead of the quads' shared loads
             }
             for (int r = 4 * ctid; r < R; r += 4 * NC)
-                consume_quad<T, L>(sa, tk, tv, r, G, tab, copy, sK, sKp, sF, dlist, rlist, cnt, bad_key);
+                consume_quad_fast<T, L, CC>(sa, r, G, copy, slist, smem_addr(scnt));
         } else {
             *abort_flag = 1;  // written before the barrier, read after it: uniform
             atomicOr(a.errors, REPRO_ERR_TIMEOUT);
         }
         named_bar_sync(1, NC);
-        if (ctid == 0) {  // the counters of two tiles ago are no longer read
-            int* old = &ctl[2 * (c3 == 0 ? 2 : c3 - 1)];
-            old[0] = 0;
-            old[1] = 0;
+        if (ctid == 0) {  // the counters of the tile before are no longer read
+            const int p = c3 == 0 ? 2 : c3 - 1;
+            ctl[2 * p] = 0;
+            ctl[2 * p + 1] = 0;
+            ctl[8 + p] = 0;
         }
         if (*abort_flag) break;
+        const int ns = *scnt;
+        if (ns > 0) {  // the tile's unusual rows, one by one (claims, flags, deferrals)
+            for (int i2 = ctid; i2 < ns; i2 += NC) {
+                const int r = slist[i2];
+                consume_row<T, L>(tk[r], tv[r], r, G, tab, copy, sK, sKp, sF, dlist, rlist, cnt, bad_key);
+            }
+            named_bar_sync(1, NC);
+        }
         const int nd = cnt[0], nr = cnt[1];
         if (nr > 0) {
             raise_and_add<T, L>(nr, nd, tk, tv, tab, sK, sKp, sF, dlist, rlist, ctid, NC);
@@ -324,11 +336,11 @@ namespace {
 // Whether a configuration is well formed and its layout (plus extra bytes)
 // fits ctas_per_sm times into one SM's shared memory.
 template <typename T>
-bool config_fits(const FusedPlanConfig& c, int G, int L, const DeviceInfo& di, size_t extra) {
+bool config_fits(const FusedPlanConfig& c, int G, int L, const DeviceInfo& di, size_t extra, bool pad) {
     if (c.S < 1 || c.S > 8 || c.R < 1024 || c.R > 8192 || c.R % (128 * c.ncw) || (c.ncw != 8 && c.ncw != 16))
         return false;
     if (c.ctas_per_sm < 1 || c.ctas_per_sm > 4 || (c.copies != 1 && c.copies != 32)) return false;
-    const size_t bytes = fused_layout<T>(c.S, c.R, G, L, c.copies).total + extra;
+    const size_t bytes = fused_layout<T>(c.S, c.R, G, L, c.copies, pad).total + extra;
     return bytes * c.ctas_per_sm + 1024 * c.ctas_per_sm <= di.smem_per_sm && bytes <= di.smem_optin;
 }
 
@@ -336,14 +348,14 @@ bool config_fits(const FusedPlanConfig& c, int G, int L, const DeviceInfo& di, s
 // behind the other), then one CTA with deeper staging; lane-private table
 // copies when the 32 copies fit next to the stages.
 template <typename T>
-bool rule_config(int G, int L, const DeviceInfo& di, FusedPlanConfig& cfg, size_t extra) {
+bool rule_config(int G, int L, const DeviceInfo& di, FusedPlanConfig& cfg, size_t extra, bool pad) {
     const FusedPlanConfig cands[] = {{3, 2048, 8, 2, 0}, {2, 2048, 8, 2, 0}, {3, 4096, 16, 1, 0}, {4, 1024, 8, 2, 0},
                                      {4, 2048, 16, 1, 0}, {3, 2048, 16, 1, 0}, {2, 2048, 16, 1, 0}, {2, 1024, 16, 1, 0}};
     for (int copies : {32, 1}) {
         if (copies == 32 && G > 256) continue;
         for (FusedPlanConfig c : cands) {
             c.copies = copies;
-            if (config_fits<T>(c, G, L, di, extra)) {
+            if (config_fits<T>(c, G, L, di, extra, pad)) {
                 cfg = c;
                 return true;
             }
@@ -368,23 +380,23 @@ const FusedPlanConfig* env_config() {
 // forced by the tuner (this thread) > REPRO_FUSED_CFG > tuned cache > rule;
 // each only if it fits.
 template <typename T>
-bool pick_config(int dtype, int G, int L, const DeviceInfo& di, FusedPlanConfig& cfg, size_t extra) {
+bool pick_config(int dtype, int G, int L, const DeviceInfo& di, FusedPlanConfig& cfg, size_t extra, bool pad) {
     if (const FusedPlanConfig* f = tune_forced_fused())
-        if (config_fits<T>(*f, G, L, di, extra)) {
+        if (config_fits<T>(*f, G, L, di, extra, pad)) {
             cfg = *f;
             return true;
         }
     if (const FusedPlanConfig* f = env_config())
-        if (config_fits<T>(*f, G, L, di, extra)) {
+        if (config_fits<T>(*f, G, L, di, extra, pad)) {
             cfg = *f;
             return true;
         }
     FusedPlanConfig t;
-    if (tune_lookup_fused(dtype, L, G, t) && config_fits<T>(t, G, L, di, extra)) {
+    if (tune_lookup_fused(dtype, L, G, t) && config_fits<T>(t, G, L, di, extra, pad)) {
         cfg = t;
         return true;
     }
-    return rule_config<T>(G, L, di, cfg, extra);
+    return rule_config<T>(G, L, di, cfg, extra, pad);
 }
 
 long long env_flush_rows() {
@@ -423,9 +435,9 @@ int env_stall_tile() {
     return left.fetch_sub(1) > 0 ? v : -1;
 }
 
-template <typename T, int L, int NCW, bool SQ>
+template <typename T, int L, int NCW, bool SQ, int CC>
 cudaError_t launch_fused_t(const FusedArgs& a0, int ctas, size_t smem, cudaStream_t s) {
-    auto kern = k_fused<T, L, NCW, SQ>;
+    auto kern = k_fused<T, L, NCW, SQ, CC>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     prof_begin(PROF_FUSED, s);
@@ -437,28 +449,31 @@ cudaError_t launch_fused_t(const FusedArgs& a0, int ctas, size_t smem, cudaStrea
 
 template <typename T, int L, bool SQ>
 cudaError_t dispatch_ncw(int ncw, const FusedArgs& a, int ctas, size_t smem, cudaStream_t s) {
-    if (ncw == 8) return launch_fused_t<T, L, 8, SQ>(a, ctas, smem, s);
-    return launch_fused_t<T, L, 16, SQ>(a, ctas, smem, s);
+    if (a.C == 32)
+        return ncw == 8 ? launch_fused_t<T, L, 8, SQ, 32>(a, ctas, smem, s)
+                        : launch_fused_t<T, L, 16, SQ, 32>(a, ctas, smem, s);
+    return ncw == 8 ? launch_fused_t<T, L, 8, SQ, 1>(a, ctas, smem, s) : launch_fused_t<T, L, 16, SQ, 1>(a, ctas, smem, s);
 }
 
 template <typename T, int L, bool SQ>
-const void* kernel_ncw(int ncw) {
-    return ncw == 8 ? (const void*)k_fused<T, L, 8, SQ> : (const void*)k_fused<T, L, 16, SQ>;
+const void* kernel_ncw(int ncw, int C) {
+    if (C == 32) return ncw == 8 ? (const void*)k_fused<T, L, 8, SQ, 32> : (const void*)k_fused<T, L, 16, SQ, 32>;
+    return ncw == 8 ? (const void*)k_fused<T, L, 8, SQ, 1> : (const void*)k_fused<T, L, 16, SQ, 1>;
 }
 
 template <typename T, bool SQ>
-const void* kernel_of_sq(int L, int ncw) {
+const void* kernel_of_sq(int L, int ncw, int C) {
     switch (L) {
-        case 1: return kernel_ncw<T, 1, SQ>(ncw);
-        case 2: return kernel_ncw<T, 2, SQ>(ncw);
-        case 3: return kernel_ncw<T, 3, SQ>(ncw);
-        default: return kernel_ncw<T, 4, SQ>(ncw);
+        case 1: return kernel_ncw<T, 1, SQ>(ncw, C);
+        case 2: return kernel_ncw<T, 2, SQ>(ncw, C);
+        case 3: return kernel_ncw<T, 3, SQ>(ncw, C);
+        default: return kernel_ncw<T, 4, SQ>(ncw, C);
     }
 }
 
 template <typename T>
-const void* kernel_of(int L, int ncw, bool square = false) {
-    return square ? kernel_of_sq<T, true>(L, ncw) : kernel_of_sq<T, false>(L, ncw);
+const void* kernel_of(int L, int ncw, int C, bool square = false) {
+    return square ? kernel_of_sq<T, true>(L, ncw, C) : kernel_of_sq<T, false>(L, ncw, C);
 }
 
 template <typename T, bool SQ>
@@ -479,26 +494,26 @@ cudaError_t dispatch_L(int L, int ncw, const FusedArgs& a, int ctas, size_t smem
 
 }  // namespace
 
-bool fused_plan_config(int dtype, int L, int G, size_t extra_smem, FusedPlanConfig& cfg) {
-    return dtype == REPRO_F64 ? pick_config<double>(dtype, G, L, device_info(), cfg, extra_smem)
-                              : pick_config<float>(dtype, G, L, device_info(), cfg, extra_smem);
+bool fused_plan_config(int dtype, int L, int G, size_t extra_smem, FusedPlanConfig& cfg, bool pad) {
+    return dtype == REPRO_F64 ? pick_config<double>(dtype, G, L, device_info(), cfg, extra_smem, pad)
+                              : pick_config<float>(dtype, G, L, device_info(), cfg, extra_smem, pad);
 }
 
-bool fused_config_fits(int dtype, int L, int G, size_t extra_smem, const FusedPlanConfig& cfg) {
-    return dtype == REPRO_F64 ? config_fits<double>(cfg, G, L, device_info(), extra_smem)
-                              : config_fits<float>(cfg, G, L, device_info(), extra_smem);
+bool fused_config_fits(int dtype, int L, int G, size_t extra_smem, const FusedPlanConfig& cfg, bool pad) {
+    return dtype == REPRO_F64 ? config_fits<double>(cfg, G, L, device_info(), extra_smem, pad)
+                              : config_fits<float>(cfg, G, L, device_info(), extra_smem, pad);
 }
 
-size_t fused_plan_smem(int dtype, int L, int G, const FusedPlanConfig& c) {
-    return dtype == REPRO_F64 ? fused_layout<double>(c.S, c.R, G, L, c.copies).total
-                              : fused_layout<float>(c.S, c.R, G, L, c.copies).total;
+size_t fused_plan_smem(int dtype, int L, int G, const FusedPlanConfig& c, bool pad) {
+    return dtype == REPRO_F64 ? fused_layout<double>(c.S, c.R, G, L, c.copies, pad).total
+                              : fused_layout<float>(c.S, c.R, G, L, c.copies, pad).total;
 }
 
-bool fused_supported(int dtype, int L, long long G, const void* keys, const void* vals) {
+bool fused_supported(int dtype, int L, long long G, const void* keys, const void* vals, bool pad) {
     if (G > 65535) return false;
     if ((uintptr_t)keys % 16 || (uintptr_t)vals % 16) return false;
     FusedPlanConfig cfg;
-    return fused_plan_config(dtype, L, (int)G, 0, cfg);
+    return fused_plan_config(dtype, L, (int)G, 0, cfg, pad);
 }
 
 static int fused_ctas(long long ntiles, const FusedPlanConfig& cfg, const DeviceInfo& di) {
@@ -519,7 +534,7 @@ cudaError_t launch_groupby_fused(const int32_t* keys, const void* vals, long lon
                                  const FusedPlanConfig& cfg, void* state, void* scratch, cudaStream_t s,
                                  int max_ctas, bool square) {
     const DeviceInfo& di = device_info();
-    if (!fused_config_fits(dtype, L, (int)G, 0, cfg)) return cudaErrorInvalidValue;
+    if (!fused_config_fits(dtype, L, (int)G, 0, cfg, true)) return cudaErrorInvalidValue;
     FusedArgs a;
     a.keys = keys;
     a.vals = vals;
@@ -529,12 +544,12 @@ cudaError_t launch_groupby_fused(const int32_t* keys, const void* vals, long lon
     a.S = cfg.S;
     a.C = cfg.copies;
     a.ntiles = n / cfg.R;
-    const size_t smem = dtype == REPRO_F64 ? fused_layout<double>(cfg.S, cfg.R, (int)G, L, cfg.copies).total
-                                           : fused_layout<float>(cfg.S, cfg.R, (int)G, L, cfg.copies).total;
+    const size_t smem = dtype == REPRO_F64 ? fused_layout<double>(cfg.S, cfg.R, (int)G, L, cfg.copies, true).total
+                                           : fused_layout<float>(cfg.S, cfg.R, (int)G, L, cfg.copies, true).total;
     // a persistent grid must be resident at once: never more CTAs per SM than
     // registers and shared memory allow
     const void* kern =
-        dtype == REPRO_F64 ? kernel_of<double>(L, cfg.ncw, square) : kernel_of<float>(L, cfg.ncw, square);
+        dtype == REPRO_F64 ? kernel_of<double>(L, cfg.ncw, cfg.copies, square) : kernel_of<float>(L, cfg.ncw, cfg.copies, square);
     const int occ = resident_ctas(kern, 32 * (cfg.ncw + 1), smem);
     if (occ < 1) return cudaErrorInvalidConfiguration;
     int ctas = fused_ctas(a.ntiles, cfg, di);
@@ -649,7 +664,8 @@ extern "C" repro_status repro_groupby_sum_noalloc(const int32_t* keys, const voi
     if (n == 0) return REPRO_OK;
     // only the fused path runs here: aligned inputs and a table that fits
     FusedPlanConfig cfg;
-    if (!fused_supported(dtype, L, num_groups, keys, values) || !fused_plan_config(dtype, L, (int)num_groups, 0, cfg))
+    if (!fused_supported(dtype, L, num_groups, keys, values, true) ||
+        !fused_plan_config(dtype, L, (int)num_groups, 0, cfg, true))
         return REPRO_ERANGE;
     const size_t per_cta = (size_t)num_groups * (8 + 16 * (size_t)L);
     const long long max_ctas = (long long)(kStaticPartialBytes / per_cta);

@@ -56,10 +56,12 @@ struct FusedPlanConfig {
 // else REPRO_FUSED_CFG, else the tuned cache, else the built-in rule -- the
 // first that fits; false if none fits.  Callers choose once per call and pass
 // the configuration on, so scratch sizing and launch always agree.
-bool fused_plan_config(int dtype, int L, int G, size_t extra_smem, FusedPlanConfig& cfg);
-bool fused_config_fits(int dtype, int L, int G, size_t extra_smem, const FusedPlanConfig& cfg);
-size_t fused_plan_smem(int dtype, int L, int G, const FusedPlanConfig& cfg);
-bool fused_supported(int dtype, int L, long long G, const void* keys, const void* vals);
+// pad: the single-task kernel's padded table (see fused_layout); false: the
+// multi-task kernel's.
+bool fused_plan_config(int dtype, int L, int G, size_t extra_smem, FusedPlanConfig& cfg, bool pad = false);
+bool fused_config_fits(int dtype, int L, int G, size_t extra_smem, const FusedPlanConfig& cfg, bool pad = false);
+size_t fused_plan_smem(int dtype, int L, int G, const FusedPlanConfig& cfg, bool pad = false);
+bool fused_supported(int dtype, int L, long long G, const void* keys, const void* vals, bool pad = false);
 size_t fused_scratch_bytes(const FusedPlanConfig& cfg, int L, long long G, long long n);
 // max_ctas > 0 caps the number of CTAs (and so the partial tables in scratch);
 // square: sum RN(x*x) instead of x.
@@ -150,9 +152,13 @@ cudaError_t launch_merge_partials(const void* parts, int C, long long G, void* s
                                   cudaStream_t s);
 cudaError_t launch_finalize(const void* state, int dtype, int L, long long G, void* out, cudaStream_t s);
 
+// The conventional floating-point GroupBy; mode < 0: the built-in choice
+// (or REPRO_FP_MODE), else one of the table strategies 0..4 of
+// repro_kernels.cu (fp_mode_supported tells which fit).
 cudaError_t launch_groupby_fp64(const int32_t* keys, const double* vals, long long n, long long G, double* out,
-                                cudaStream_t s);
+                                cudaStream_t s, int mode = -1);
 cudaError_t launch_groupby_fp32(const int32_t* keys, const float* vals, long long n, long long G, float* out,
-                                cudaStream_t s);
+                                cudaStream_t s, int mode = -1);
+bool fp_mode_supported(int dtype, int mode, long long G);
 
 }  // namespace rp

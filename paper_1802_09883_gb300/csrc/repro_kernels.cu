@@ -13,7 +13,9 @@
 // conventional floating-point atomic GroupBy used as the baseline.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstdint>
+#include <cstdlib>
 
 #include "repro_device.cuh"
 #include "repro_internal.h"
@@ -191,27 +193,144 @@ __global__ void k_finalize(const unsigned char* base, int dtype, int L, long lon
         out[g] = state_finalize_group<T>(st, g);
 }
 
-// Conventional floating-point GroupBy (non-reproducible baseline).
+// ------------------------------------- conventional GroupBy (the baseline)
+//
+// SUM(value) GROUP BY key with built-in floating-point adds in whatever order
+// the hardware takes them: the non-reproducible reference point the paper
+// measures its types against (Sec. VI-C, aggregation without summation
+// buffers).  Built for speed, with the same input handling as the
+// reproducible kernels -- 16-byte vector loads, two quads of rows in flight
+// per thread, a persistent grid -- and one of five table strategies:
+//   FP_SMEM    one shared-memory table per CTA (C = 32: one copy per lane,
+//              so a warp's adds never meet on an address), atomicAdd;
+//   FP_MATCH   one shared table, rows of equal key within a warp combined by
+//              __match_any_sync + shuffles first (skewed keys), one atomic
+//              per distinct key;
+//   FP_WARP    one table per warp: after the same combining the leaders'
+//              keys are distinct, so they add with plain loads and stores;
+//   FP_GLOBAL  atomicAdd straight into the result (L2 atomics);
+//   FP_GMATCH  the same after combining equal keys within the warp.
+// The launcher picks by group count, or a caller (the benchmark) times them
+// all and keeps the fastest.
+enum FpMode { FP_SMEM = 0, FP_MATCH = 1, FP_WARP = 2, FP_GLOBAL = 3, FP_GMATCH = 4, FP_MODES = 5 };
+
 template <typename T>
-__global__ void k_groupby_float(const int32_t* __restrict__ keys, const T* __restrict__ vals, long long n,
-                                int G, int smem_groups, T* __restrict__ out) {
-    extern __shared__ unsigned char s_raw[];
-    T* sacc = reinterpret_cast<T*>(s_raw);
-    const bool use_smem = G <= smem_groups;
-    if (use_smem) {
-        for (int g = threadIdx.x; g < G; g += blockDim.x) sacc[g] = (T)0;
+struct FpQuad;
+template <>
+struct FpQuad<double> {
+    static __device__ __forceinline__ void load(const double* v, long long q, double x[4]) {
+        const double2 a = __ldg(reinterpret_cast<const double2*>(v) + 2 * q);
+        const double2 b = __ldg(reinterpret_cast<const double2*>(v) + 2 * q + 1);
+        x[0] = a.x; x[1] = a.y; x[2] = b.x; x[3] = b.y;
+    }
+};
+template <>
+struct FpQuad<float> {
+    static __device__ __forceinline__ void load(const float* v, long long q, float x[4]) {
+        const float4 a = __ldg(reinterpret_cast<const float4*>(v) + q);
+        x[0] = a.x; x[1] = a.y; x[2] = a.z; x[3] = a.w;
+    }
+};
+
+// Combine the values of lanes holding the same key (all 32 lanes call it;
+// invalid rows pass a key no other lane has).  Returns true in the lane that
+// adds the combined sum (the lowest of its peers).
+template <typename T>
+__device__ __forceinline__ bool fp_combine(int key, T& v) {
+    const int lane = threadIdx.x & 31;
+    const unsigned peers = __match_any_sync(0xffffffffu, key);
+    const int leader = __ffs(peers) - 1;
+    unsigned others = lane == leader ? peers & ~(1u << lane) : 0u;
+    const int iters = __reduce_max_sync(0xffffffffu, __popc(others));
+    T sum = v;
+    for (int i = 0; i < iters; ++i) {
+        const int src = others ? __ffs(others) - 1 : lane;
+        const T x = __shfl_sync(0xffffffffu, v, src);
+        if (others) {
+            sum += x;
+            others &= others - 1;
+        }
+    }
+    v = sum;
+    return lane == leader;
+}
+
+template <typename T, int MODE>
+__device__ __forceinline__ void fp_add_row(int g, T v, int G, T* tab, int C, T* out) {
+    const int lane = threadIdx.x & 31;
+    const bool ok = (unsigned)g < (unsigned)G;
+    if (MODE == FP_SMEM) {
+        if (ok) atomicAdd(&tab[(size_t)g * C + (lane & (C - 1))], v);
+    } else if (MODE == FP_GLOBAL) {
+        if (ok) atomicAdd(&out[g], v);
+    } else {
+        const int key = ok ? g : -1 - lane;
+        const bool lead = fp_combine(key, v);
+        if (lead && ok) {
+            if (MODE == FP_MATCH) atomicAdd(&tab[g], v);
+            else if (MODE == FP_GMATCH) atomicAdd(&out[g], v);
+            else tab[g] += v;  // FP_WARP: this warp's own table, distinct keys
+        }
+    }
+}
+
+// VEC: keys and values 16-byte aligned (quads by vector loads); the rows
+// past the last whole quad, and every row when !VEC, by scalar loads.
+template <typename T, int MODE, bool VEC>
+__global__ void __launch_bounds__(512) k_groupby_fp(const int32_t* __restrict__ keys, const T* __restrict__ vals,
+                                                    long long n, int G, int C, T* __restrict__ out) {
+    extern __shared__ __align__(16) unsigned char s_raw[];
+    T* stab = reinterpret_cast<T*>(s_raw);
+    const bool smem = MODE == FP_SMEM || MODE == FP_MATCH || MODE == FP_WARP;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int words = MODE == FP_WARP ? G * nw : G * C;
+    T* tab = MODE == FP_WARP ? stab + (size_t)warp * G : stab;
+    if (smem) {
+        for (int i = threadIdx.x; i < words; i += blockDim.x) stab[i] = (T)0;
         __syncthreads();
     }
-    const long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += stride) {
-        const int g = keys[i];
-        if ((unsigned)g >= (unsigned)G) continue;
-        atomicAdd(use_smem ? &sacc[g] : &out[g], vals[i]);
+    const long long gw = (long long)blockIdx.x * nw + warp, nwarps = (long long)gridDim.x * nw;
+    const long long nq = VEC ? n / 4 : 0;
+    // two chunks of 32 quads per warp in flight; the loop bound is warp-uniform
+    for (long long c = gw; c * 32 < nq; c += 2 * nwarps) {
+        const long long q0 = c * 32 + lane, q1 = (c + nwarps) * 32 + lane;
+        const bool v0 = q0 < nq, v1 = q1 < nq;
+        int4 k0 = make_int4(-1, -1, -1, -1), k1 = make_int4(-1, -1, -1, -1);
+        T x0[4] = {0, 0, 0, 0}, x1[4] = {0, 0, 0, 0};
+        if (v0) {
+            k0 = __ldg(reinterpret_cast<const int4*>(keys) + q0);
+            FpQuad<T>::load(vals, q0, x0);
+        }
+        if (v1) {
+            k1 = __ldg(reinterpret_cast<const int4*>(keys) + q1);
+            FpQuad<T>::load(vals, q1, x1);
+        }
+        fp_add_row<T, MODE>(k0.x, x0[0], G, tab, C, out);
+        fp_add_row<T, MODE>(k0.y, x0[1], G, tab, C, out);
+        fp_add_row<T, MODE>(k0.z, x0[2], G, tab, C, out);
+        fp_add_row<T, MODE>(k0.w, x0[3], G, tab, C, out);
+        fp_add_row<T, MODE>(k1.x, x1[0], G, tab, C, out);
+        fp_add_row<T, MODE>(k1.y, x1[1], G, tab, C, out);
+        fp_add_row<T, MODE>(k1.z, x1[2], G, tab, C, out);
+        fp_add_row<T, MODE>(k1.w, x1[3], G, tab, C, out);
     }
-    if (use_smem) {
+    // scalar rows (all of them when the columns are not 16-byte aligned)
+    for (long long r0 = 4 * nq + gw * 32; r0 < n; r0 += nwarps * 32) {
+        const long long r = r0 + lane;
+        const bool v = r < n;
+        fp_add_row<T, MODE>(v ? keys[r] : -1, v ? vals[r] : (T)0, G, tab, C, out);
+    }
+    if (smem) {
         __syncthreads();
-        for (int g = threadIdx.x; g < G; g += blockDim.x)
-            if (sacc[g] != (T)0) atomicAdd(&out[g], sacc[g]);
+        for (int g = threadIdx.x; g < G; g += blockDim.x) {
+            T acc = (T)0;
+            if (MODE == FP_WARP) {
+                for (int w = 0; w < nw; ++w) acc += stab[(size_t)w * G + g];
+            } else {
+                for (int c = 0; c < C; ++c) acc += stab[(size_t)g * C + c];
+            }
+            if (acc != (T)0) atomicAdd(&out[g], acc);
+        }
     }
 }
 
@@ -321,32 +440,103 @@ cudaError_t launch_finalize(const void* state, int dtype, int L, long long G, vo
     return cudaGetLastError();
 }
 
+// Shared-memory words each strategy needs for G groups (0: not applicable).
 template <typename T>
-static cudaError_t launch_groupby_float_t(const int32_t* keys, const T* vals, long long n, long long G, T* out,
-                                          cudaStream_t s) {
-    cudaError_t e = cudaMemsetAsync(out, 0, sizeof(T) * (size_t)G, s);
-    if (e != cudaSuccess || n == 0) return e;
-    const int smem_groups = 12288;
-    const size_t smem = G <= smem_groups ? sizeof(T) * (size_t)G : 0;
-    if ((e = allow_smem(k_groupby_float<T>, smem)) != cudaSuccess) return e;
-    const int th = 256;
-    const ProfKernel pk = sizeof(T) == 8 ? PROF_FP64 : PROF_FP32;
-    prof_begin(pk, s);
-    k_groupby_float<T><<<grid_for(n, th, device_info().sms * 8), th, smem, s>>>(keys, vals, n, (int)G,
-                                                                                 smem_groups, out);
-    prof_end(pk, s);
-    count_launches(1);
+static size_t fp_smem_bytes(int mode, long long G, int threads, int& C) {
+    const size_t cap = 200 * 1024;
+    C = 1;
+    switch (mode) {
+        case FP_SMEM:
+            if ((size_t)G * 32 * sizeof(T) <= 64 * 1024) C = 32;  // one copy per lane
+            return (size_t)G * C * sizeof(T) <= cap ? (size_t)G * C * sizeof(T) : 0;
+        case FP_MATCH: return (size_t)G * sizeof(T) <= cap ? (size_t)G * sizeof(T) : 0;
+        case FP_WARP: return (size_t)G * (threads / 32) * sizeof(T) <= cap ? (size_t)G * (threads / 32) * sizeof(T) : 0;
+        default: return 0;
+    }
+}
+
+// The built-in choice: lane-private copies for small tables, one shared
+// table with within-warp combining up to the shared-memory limit, global
+// atomics with combining beyond.
+template <typename T>
+static int fp_rule(long long G) {
+    int C;
+    if ((size_t)G * 32 * sizeof(T) <= 64 * 1024) return FP_SMEM;
+    if (fp_smem_bytes<T>(FP_MATCH, G, 512, C)) return FP_MATCH;
+    return FP_GMATCH;
+}
+
+template <typename T, int MODE, bool VEC>
+static cudaError_t launch_fp_mode(const int32_t* keys, const T* vals, long long n, int G, int C, size_t smem,
+                                  T* out, cudaStream_t s) {
+    auto kern = k_groupby_fp<T, MODE, VEC>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const int th = 512;
+    int per_sm = 0;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, th, smem)) != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    const long long work = (n + 4ll * th - 1) / (4ll * th);
+    const int blocks = (int)std::max(1ll, std::min<long long>(work, (long long)device_info().sms * per_sm));
+    kern<<<blocks, th, smem, s>>>(keys, vals, n, G, C, out);
     return cudaGetLastError();
 }
 
+template <typename T, int MODE>
+static cudaError_t launch_fp_vec(bool vec, const int32_t* keys, const T* vals, long long n, int G, int C, size_t smem,
+                                 T* out, cudaStream_t s) {
+    return vec ? launch_fp_mode<T, MODE, true>(keys, vals, n, G, C, smem, out, s)
+               : launch_fp_mode<T, MODE, false>(keys, vals, n, G, C, smem, out, s);
+}
+
+static int env_fp_mode() {
+    static const int v = [] {
+        const char* e = getenv("REPRO_FP_MODE");
+        return e ? atoi(e) : -1;
+    }();
+    return v;
+}
+
+template <typename T>
+static cudaError_t launch_groupby_float_t(const int32_t* keys, const T* vals, long long n, long long G, T* out,
+                                          cudaStream_t s, int mode) {
+    cudaError_t e = cudaMemsetAsync(out, 0, sizeof(T) * (size_t)G, s);
+    if (e != cudaSuccess || n == 0) return e;
+    if (mode < 0) mode = env_fp_mode();
+    if (mode < 0 || mode >= FP_MODES) mode = fp_rule<T>(G);
+    int C = 1;
+    const size_t smem = fp_smem_bytes<T>(mode, G, 512, C);
+    if ((mode == FP_SMEM || mode == FP_MATCH || mode == FP_WARP) && smem == 0) return cudaErrorInvalidValue;
+    const bool vec = (uintptr_t)keys % 16 == 0 && (uintptr_t)vals % 16 == 0;
+    const ProfKernel pk = sizeof(T) == 8 ? PROF_FP64 : PROF_FP32;
+    prof_begin(pk, s);
+    switch (mode) {
+        case FP_SMEM: e = launch_fp_vec<T, FP_SMEM>(vec, keys, vals, n, (int)G, C, smem, out, s); break;
+        case FP_MATCH: e = launch_fp_vec<T, FP_MATCH>(vec, keys, vals, n, (int)G, C, smem, out, s); break;
+        case FP_WARP: e = launch_fp_vec<T, FP_WARP>(vec, keys, vals, n, (int)G, C, smem, out, s); break;
+        case FP_GLOBAL: e = launch_fp_vec<T, FP_GLOBAL>(vec, keys, vals, n, (int)G, C, smem, out, s); break;
+        default: e = launch_fp_vec<T, FP_GMATCH>(vec, keys, vals, n, (int)G, C, smem, out, s); break;
+    }
+    prof_end(pk, s);
+    count_launches(1);
+    return e;
+}
+
+bool fp_mode_supported(int dtype, int mode, long long G) {
+    if (mode < 0 || mode >= FP_MODES || G < 1 || G > INT32_MAX) return false;
+    if (mode == FP_GLOBAL || mode == FP_GMATCH) return true;
+    int C;
+    return (dtype == REPRO_F64 ? fp_smem_bytes<double>(mode, G, 512, C) : fp_smem_bytes<float>(mode, G, 512, C)) != 0;
+}
+
 cudaError_t launch_groupby_fp64(const int32_t* keys, const double* vals, long long n, long long G, double* out,
-                                cudaStream_t s) {
-    return launch_groupby_float_t<double>(keys, vals, n, G, out, s);
+                                cudaStream_t s, int mode) {
+    return launch_groupby_float_t<double>(keys, vals, n, G, out, s, mode);
 }
 
 cudaError_t launch_groupby_fp32(const int32_t* keys, const float* vals, long long n, long long G, float* out,
-                                cudaStream_t s) {
-    return launch_groupby_float_t<float>(keys, vals, n, G, out, s);
+                                cudaStream_t s, int mode) {
+    return launch_groupby_float_t<float>(keys, vals, n, G, out, s, mode);
 }
 
 }  // namespace rp

@@ -204,7 +204,8 @@ repro_status repro_groupby_stats(const int32_t* keys, const void* values, int64_
         return from_cuda(cudaGetLastError());
     }
     FusedPlanConfig cfg;
-    if (fused_supported(dtype, L, num_groups, keys, values) && fused_plan_config(dtype, L, (int)num_groups, 0, cfg)) {
+    if (fused_supported(dtype, L, num_groups, keys, values, true) &&
+        fused_plan_config(dtype, L, (int)num_groups, 0, cfg, true)) {
         // two single passes over the same columns, the second squaring each
         // staged value in place (no x*x column in memory), and the counts
         cudaMemPool_t pool0 = library_pool(err);

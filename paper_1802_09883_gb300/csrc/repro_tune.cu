@@ -147,7 +147,7 @@ repro_status repro_tune_groupby(const int32_t* keys, const void* values, int64_t
         if (state) cudaFree(state);
         if (scratch) cudaFree(scratch);
     };
-    if (fused_supported(dtype, L, G, keys, values)) {
+    if (fused_supported(dtype, L, G, keys, values, true)) {
         out->path = 0;
         std::vector<FusedPlanConfig> cands;
         // S = 1: a single stage per CTA (its tile loads while the SM's other
@@ -159,12 +159,12 @@ repro_status repro_tune_groupby(const int32_t* keys, const void* values, int64_t
                         for (int copies : {1, 32}) {
                             const FusedPlanConfig c{S, R, ncw, cps, copies};
                             if (S == 1 && R == 1024) continue;
-                            if (fused_config_fits(dtype, L, (int)G, 0, c)) cands.push_back(c);
+                            if (fused_config_fits(dtype, L, (int)G, 0, c, true)) cands.push_back(c);
                         }
         FusedPlanConfig def{};
         {
             Force f(nullptr, 0, true);
-            if (!fused_plan_config(dtype, L, (int)G, 0, def)) return REPRO_ERANGE;
+            if (!fused_plan_config(dtype, L, (int)G, 0, def, true)) return REPRO_ERANGE;
         }
         size_t need = 16;
         for (const FusedPlanConfig& c : cands) need = std::max(need, fused_scratch_bytes(c, L, G, n));

@@ -223,6 +223,33 @@ def test_fp64_baseline_close_to_exact():
     assert np.all(np.abs(out - ref) <= (cnt - 1).clip(min=0) * 2.0 ** -53 * absum + 1e-300)
 
 
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+@pytest.mark.parametrize("G,dist", [(16, "zipf"), (1000, "uniform"), (5000, "zipf"), (300_000, "uniform")])
+@pytest.mark.parametrize("offset", [0, 1])
+def test_conventional_baseline_strategies_within_error_bound(dtype, G, dist, offset):
+    """Every table strategy of the conventional GroupBy (aligned columns by
+    vector loads, unaligned ones by scalar loads) sums within eq. (5)'s bound
+    (n - 1) eps sum|b| of the exact group sums; strategies whose tables do
+    not fit report so."""
+    w = WL.sweep_cell(G, dist, 3, n=(1 << 20) + 7, seed=G + offset, device=DEV, dtype=dtype)
+    k, v = w.keys[offset:], w.values[offset:]
+    kn, vn = _np(k), _np(v).astype(np.float64)
+    ref = O.groupby_sum_values(kn, vn, G, 4)  # L = 4 holds every bit here
+    absum = np.bincount(kn, weights=np.abs(vn), minlength=G)
+    cnt = np.bincount(kn, minlength=G)
+    eps = 2.0 ** -53 if dtype == torch.float64 else 2.0 ** -24
+    ran = 0
+    for mode in R.FP_MODES:
+        out = R.groupby_sum_fp_mode(k, v, G, mode)
+        if out is None:
+            assert mode in (0, 1, 2) and G > 1000
+            continue
+        ran += 1
+        got = _np(out).astype(np.float64)
+        assert np.all(np.abs(got - ref) <= cnt.clip(min=1) * eps * absum + 1e-30), (mode, G)
+    assert ran >= 2
+
+
 def test_fp32_baseline_runs():
     w = WL.plain(n=100_000, G=100, L=3, seed=4, device=DEV, dtype=torch.float32)
     out = _np(R.groupby_sum_fp32(w.keys, w.values, w.G)).astype(np.float64)

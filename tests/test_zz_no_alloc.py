@@ -42,15 +42,15 @@ def _run(entry, keys, vals, G, L, code):
     (1024, 3, torch.float64, (1_000_003, 333_333)),
     (16, 2, torch.float64, (1_000_003, 333_333)),
     (700, 4, torch.float32, (1_000_003, 333_333)),
-    # 16 MiB holds only 74 partial tables of 4000 groups (56 bytes each at
+    # 16 MiB holds only 99 partial tables of 3000 groups (56 bytes each at
     # L = 3) where the grid would have one CTA per SM: the cap on the CTA
     # count, and the longer tile ranges it gives each CTA, are in effect
-    (4000, 3, torch.float64, ((1 << 24) + 3, (1 << 23) + 1)),
+    (3000, 3, torch.float64, ((1 << 24) + 3, (1 << 23) + 1)),
 ])
 def test_noalloc_matches_repro_groupby_sum_on_two_calls(G, L, dtype, rows):
     lib = R.lib()
     code = R.REPRO_F64 if dtype == torch.float64 else R.REPRO_F32
-    if G == 4000:  # the array's cap is below the one-CTA-per-SM grid
+    if G == 3000:  # the array's cap is below the one-CTA-per-SM grid
         assert (16 << 20) // (G * (8 + 16 * L)) < torch.cuda.get_device_properties(0).multi_processor_count
     for call, (n, seed) in enumerate(zip(rows, (11, 12))):
         w = WL.plain(n=n, G=G, L=L, seed=seed + G, device="cuda", e_lo=-45, e_hi=45, dtype=dtype)
