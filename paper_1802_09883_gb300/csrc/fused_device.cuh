@@ -162,11 +162,21 @@ struct QuadWords<double> {
         lo[0] = p.x; hi[0] = p.y; lo[1] = p.z; hi[1] = p.w;
         lo[2] = q.x; hi[2] = q.y; lo[3] = q.z; hi[3] = q.w;
     }
+    static __device__ __forceinline__ void load_ptr(const double* v, uint32_t hi[4], uint32_t lo[4]) {
+        const uint4 p = reinterpret_cast<const uint4*>(v)[0], q = reinterpret_cast<const uint4*>(v)[1];
+        lo[0] = p.x; hi[0] = p.y; lo[1] = p.z; hi[1] = p.w;
+        lo[2] = q.x; hi[2] = q.y; lo[3] = q.z; hi[3] = q.w;
+    }
 };
 template <>
 struct QuadWords<float> {
     static __device__ __forceinline__ void load(uint32_t a, uint32_t hi[4], uint32_t lo[4]) {
         const uint4 p = lds_v4(a);
+        hi[0] = p.x; hi[1] = p.y; hi[2] = p.z; hi[3] = p.w;
+        lo[0] = lo[1] = lo[2] = lo[3] = 0u;
+    }
+    static __device__ __forceinline__ void load_ptr(const float* v, uint32_t hi[4], uint32_t lo[4]) {
+        const uint4 p = *reinterpret_cast<const uint4*>(v);
         hi[0] = p.x; hi[1] = p.y; hi[2] = p.z; hi[3] = p.w;
         lo[0] = lo[1] = lo[2] = lo[3] = 0u;
     }
@@ -313,22 +323,25 @@ struct Expo<float> {
 // rows are computed too, from whatever their words hold, and added to the
 // spare group, which keeps the four rows' work straight-line.
 template <typename T, int L, int CC>
-__device__ __forceinline__ void consume_quad_fast(const SAddr& sa, int r0, int G, int copy, unsigned short* slist,
-                                                  uint32_t scnt_addr) {
+__device__ __forceinline__ void consume_quad_fast(const SAddr& sa, const int32_t* tk, const T* tv, const int* sK,
+                                                  int r0, int G, int copy, unsigned short* slist, uint32_t scnt_addr) {
     constexpr uint32_t LP = L + 2;  // levels per group in the padded table
-    const uint4 k4 = lds_v4(sa.keys + 4u * (uint32_t)r0);
-    const int gq[4] = {(int)k4.x, (int)k4.y, (int)k4.z, (int)k4.w};
+    // plain loads (the staged tile and the windows do not change during
+    // this phase), so that the compiler may start the next row's loads
+    // while this row's atomics are in flight
+    const int4 k4 = *reinterpret_cast<const int4*>(tk + r0);
+    const int gq[4] = {k4.x, k4.y, k4.z, k4.w};
     uint32_t vhi[4], vlo[4];
-    QuadWords<T>::load(sa.vals + (uint32_t)sizeof(T) * (uint32_t)r0, vhi, vlo);
+    QuadWords<T>::load_ptr(tv + r0, vhi, vlo);
     const uint32_t hi_off = sa.hi - sa.lo;
-    unsigned slow = 0;  // bit q: row q goes to the slow list
+    unsigned okm = 0;  // bit q: row q added its digits
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
         int E, t, kb;
         Expo<T>::get(vhi[q], E, t, kb);
         const bool key_ok = (unsigned)gq[q] < (unsigned)G;
         const unsigned gc = min((unsigned)gq[q], (unsigned)(G - 1));
-        const int K = (int)lds_u32(sa.K + 4u * gc);
+        const int K = sK[gc];
         const bool ok = key_ok && E != 0 && kb <= K;
         unsigned lo[3];
         int hi[3];
@@ -346,12 +359,12 @@ __device__ __forceinline__ void consume_quad_fast(const SAddr& sa, int r0, int G
         for (int k = 0; k < ND; ++k) old[k] = table_add_lo(a + 4u * CC * k, lo[k]);
 #pragma unroll
         for (int k = 0; k < ND; ++k) table_add_hi(a + hi_off + 4u * CC * k, old[k], lo[k], hi[k]);
-        slow |= (unsigned)(!ok && !(key_ok && Lean<T>::is_zero(vhi[q], vlo[q]))) << q;
+        okm |= (unsigned)ok << q;
     }
-    if (slow) {  // rare: one branch per quad
+    if (okm != 0xfu) {  // rare: a row that did not add; a zero with a good key needs nothing more
 #pragma unroll
         for (int q = 0; q < 4; ++q)
-            if (slow & (1u << q)) {
+            if (!(okm & (1u << q)) && !((unsigned)gq[q] < (unsigned)G && Lean<T>::is_zero(vhi[q], vlo[q]))) {
                 uint32_t idx;
                 asm volatile("atom.shared.add.u32 %0, [%1], 1;" : "=r"(idx) : "r"(scnt_addr) : "memory");
                 slist[idx] = (unsigned short)(r0 + q);

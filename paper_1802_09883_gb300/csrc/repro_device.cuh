@@ -330,27 +330,33 @@ struct Signed<double> {
             "subc.u32 %1, b, %4;\n\t}"
             : "=r"(sl), "=r"(sh)
             : "r"(vlo), "r"(mh), "r"(S));
-        // X = significand * 2^s, s = E + 79 - 40 kb in [27, 66]: shift by r
-        // within a word, then by q = 0, 1 or 2 whole words
-        const int s = t + 27 - 40 * kb;
-        const int r = s & 31, q = s >> 5;
-        const uint32_t v0 = sl << r;
-        const uint32_t v1 = __funnelshift_l(sl, sh, r);
-        const uint32_t v2 = __funnelshift_l(sh, S, r);
-        const uint32_t w0 = q == 0 ? v0 : 0u;
-        const uint32_t w1 = q == 0 ? v1 : (q == 1 ? v0 : 0u);
-        const uint32_t w2 = q == 0 ? v2 : (q == 1 ? v1 : v0);
-        const uint32_t w3 = q == 0 ? S : (q == 1 ? v2 : v1);
+        // X = significand * 2^s, s = E + 79 - 40 kb in [27, 66]: shifted by 5
+        // first (the signed significand still fits 64 bits), then by
+        // s - 5 in [22, 61] = r within a word and q = 0 or 1 whole words
+        const uint32_t sl5 = sl << 5, sh5 = __funnelshift_l(sl, sh, 5);
+        const int s5 = t + 22 - 40 * kb;
+        const int r = s5 & 31;
+        const bool q = s5 >= 32;
+        const uint32_t v0 = sl5 << r;
+        const uint32_t v1 = __funnelshift_l(sl5, sh5, r);
+        const uint32_t v2 = __funnelshift_l(sh5, S, r);
+        const uint32_t w0 = q ? 0u : v0;
+        const uint32_t w1 = q ? v0 : v1;
+        const uint32_t w2 = q ? v1 : v2;
+        const uint32_t w3 = q ? v2 : S;
         // 40-bit pieces: x0, x1 unsigned fields, x2 the signed part above
         const uint32_t x0l = w0, x0h = w1 & 0xffu;
         const uint32_t x1l = __funnelshift_r(w1, w2, 8), x1h = (w2 >> 8) & 0xffu;
         const uint32_t x2l = __funnelshift_r(w2, w3, 16);
         const int x2h = (int)w3 >> 16;
-        // carries at bits 40 and 80: [x + (2^39 - 1) + tie bit >= 2^40]
+        // carries at bits 40 and 80: [x + (2^39 - 1) + tie bit >= 2^40], the
+        // tie bit the parity above (bit 40) or, at bit 80, the parity of x2
+        // or any bit of x0; the low word's carry into the high word is
+        // [low word + tie bit > 0], folded into one add with carry-out
         const uint32_t s1 = x1l & 1u;
-        const uint32_t s2b = (uint32_t)((x0h | x0l) != 0u) | (x2l & 1u);
-        const uint32_t c1 = (x0h + 0x7fu + (uint32_t)(((unsigned long long)x0l + 0xffffffffull + s1) >> 32)) >> 8;
-        const uint32_t c2 = (x1h + 0x7fu + (uint32_t)(((unsigned long long)x1l + 0xffffffffull + s2b) >> 32)) >> 8;
+        const uint32_t z2 = x1l | x0l | x0h | (x2l & 1u);
+        const uint32_t c1 = (x0h + 0x7fu + (uint32_t)(((unsigned long long)(x0l | s1) + 0xffffffffull) >> 32)) >> 8;
+        const uint32_t c2 = (x1h + 0x7fu + (uint32_t)(((unsigned long long)z2 + 0xffffffffull) >> 32)) >> 8;
         lo[0] = x2l + c2;
         hi[0] = x2h + (int)(lo[0] < c2);
         lo[1] = x1l + c1;

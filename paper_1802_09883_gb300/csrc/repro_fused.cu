@@ -54,7 +54,7 @@ struct FusedArgs {
 // the thread that consumes it; the sums behind VARIANCE / STDDEV).
 // CC: copies of the table (a.C), fixed at compile time for the hot loop.
 template <typename T, int L, int NCW, bool SQ, int CC>
-__global__ void __launch_bounds__(32 * (NCW + 1), NCW == 8 ? 4 : 2) k_fused(FusedArgs a) {
+__global__ void __launch_bounds__(32 * (NCW + 1), NCW == 8 ? 4 : (NCW == 16 ? 2 : 1)) k_fused(FusedArgs a) {
     constexpr int NC = 32 * NCW;
     extern __shared__ __align__(128) unsigned char smem[];
     const FusedSmem m = fused_layout<T>(a.S, a.R, a.G, L, a.C, true);
@@ -177,7 +177,7 @@ __global__ void __launch_bounds__(32 * (NCW + 1), NCW == 8 ? 4 : 2) k_fused(Fuse
                 asm volatile("" ::: "memory");  // the stores stay ahead of the quads' shared loads
             }
             for (int r = 4 * ctid; r < R; r += 4 * NC)
-                consume_quad_fast<T, L, CC>(sa, r, G, copy, slist, smem_addr(scnt));
+                consume_quad_fast<T, L, CC>(sa, tk, tv, sK, r, G, copy, slist, smem_addr(scnt));
         } else {
             *abort_flag = 1;  // written before the barrier, read after it: uniform
             atomicOr(a.errors, REPRO_ERR_TIMEOUT);
@@ -337,7 +337,9 @@ namespace {
 // fits ctas_per_sm times into one SM's shared memory.
 template <typename T>
 bool config_fits(const FusedPlanConfig& c, int G, int L, const DeviceInfo& di, size_t extra, bool pad) {
-    if (c.S < 1 || c.S > 8 || c.R < 1024 || c.R > 8192 || c.R % (128 * c.ncw) || (c.ncw != 8 && c.ncw != 16))
+    // 24 and 31 consumer warps only in the single-task kernel (pad)
+    if (c.S < 1 || c.S > 8 || c.R < 1024 || c.R > 8192 || c.R % (128 * c.ncw) ||
+        (c.ncw != 8 && c.ncw != 16 && !(pad && (c.ncw == 24 || c.ncw == 31))))
         return false;
     if (c.ctas_per_sm < 1 || c.ctas_per_sm > 4 || (c.copies != 1 && c.copies != 32)) return false;
     const size_t bytes = fused_layout<T>(c.S, c.R, G, L, c.copies, pad).total + extra;
@@ -447,18 +449,31 @@ cudaError_t launch_fused_t(const FusedArgs& a0, int ctas, size_t smem, cudaStrea
     return cudaGetLastError();
 }
 
+template <typename T, int L, bool SQ, int CC>
+cudaError_t dispatch_ncw_cc(int ncw, const FusedArgs& a, int ctas, size_t smem, cudaStream_t s) {
+    if (ncw == 8) return launch_fused_t<T, L, 8, SQ, CC>(a, ctas, smem, s);
+    if (ncw == 16) return launch_fused_t<T, L, 16, SQ, CC>(a, ctas, smem, s);
+    if (ncw == 24) return launch_fused_t<T, L, 24, SQ, CC>(a, ctas, smem, s);
+    return launch_fused_t<T, L, 31, SQ, CC>(a, ctas, smem, s);
+}
+
 template <typename T, int L, bool SQ>
 cudaError_t dispatch_ncw(int ncw, const FusedArgs& a, int ctas, size_t smem, cudaStream_t s) {
-    if (a.C == 32)
-        return ncw == 8 ? launch_fused_t<T, L, 8, SQ, 32>(a, ctas, smem, s)
-                        : launch_fused_t<T, L, 16, SQ, 32>(a, ctas, smem, s);
-    return ncw == 8 ? launch_fused_t<T, L, 8, SQ, 1>(a, ctas, smem, s) : launch_fused_t<T, L, 16, SQ, 1>(a, ctas, smem, s);
+    return a.C == 32 ? dispatch_ncw_cc<T, L, SQ, 32>(ncw, a, ctas, smem, s)
+                     : dispatch_ncw_cc<T, L, SQ, 1>(ncw, a, ctas, smem, s);
+}
+
+template <typename T, int L, bool SQ, int CC>
+const void* kernel_ncw_cc(int ncw) {
+    if (ncw == 8) return (const void*)k_fused<T, L, 8, SQ, CC>;
+    if (ncw == 16) return (const void*)k_fused<T, L, 16, SQ, CC>;
+    if (ncw == 24) return (const void*)k_fused<T, L, 24, SQ, CC>;
+    return (const void*)k_fused<T, L, 31, SQ, CC>;
 }
 
 template <typename T, int L, bool SQ>
 const void* kernel_ncw(int ncw, int C) {
-    if (C == 32) return ncw == 8 ? (const void*)k_fused<T, L, 8, SQ, 32> : (const void*)k_fused<T, L, 16, SQ, 32>;
-    return ncw == 8 ? (const void*)k_fused<T, L, 8, SQ, 1> : (const void*)k_fused<T, L, 16, SQ, 1>;
+    return C == 32 ? kernel_ncw_cc<T, L, SQ, 32>(ncw) : kernel_ncw_cc<T, L, SQ, 1>(ncw);
 }
 
 template <typename T, bool SQ>

@@ -153,8 +153,8 @@ repro_status repro_tune_groupby(const int32_t* keys, const void* values, int64_t
         // S = 1: a single stage per CTA (its tile loads while the SM's other
         // CTAs compute), which leaves room for larger tiles at 3 CTAs per SM
         for (int S : {1, 2, 3, 4})
-            for (int R : {1024, 2048, 4096})
-                for (int ncw : {8, 16})
+            for (int R : {1024, 2048, 3072, 3968, 4096, 6144, 7936})
+                for (int ncw : {8, 16, 24, 31})
                     for (int cps : {1, 2, 3, 4})
                         for (int copies : {1, 32}) {
                             const FusedPlanConfig c{S, R, ncw, cps, copies};
