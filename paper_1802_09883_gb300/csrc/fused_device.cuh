@@ -23,13 +23,13 @@ struct FusedSmem {
 
 __host__ __device__ inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
-// pad: the single-task kernel's table -- two spare levels after each group's
-// L levels and one spare group after the last, so that a row's three digit
-// adds always have table words at fixed offsets from its group's window
-// level (digits past the window land in the spare levels, rows with nothing
-// to add in the spare group; neither is ever read back).
+// The table is padded: two spare levels after each group's L levels and one
+// spare group after the last, so that a row's three digit adds always have
+// table words at fixed offsets from its group's window level (digits past
+// the window land in the spare levels, rows with nothing to add in the
+// spare group; neither is ever read back, so they are never cleared).
 template <typename T>
-__host__ __device__ inline FusedSmem fused_layout(int S, int R, int G, int L, int C, bool pad = false) {
+__host__ __device__ inline FusedSmem fused_layout(int S, int R, int G, int L, int C) {
     FusedSmem m;
     size_t o = 0;
     m.bars = o;
@@ -43,8 +43,8 @@ __host__ __device__ inline FusedSmem fused_layout(int S, int R, int G, int L, in
     m.vals = o;
     o += (size_t)S * R * sizeof(T);
     o = align_up(o, 16);
-    m.bins = o;  // LO[G][L][C] (uint32) then HI[G][L][C] (int32); padded: [G + 1][L + 2][C]
-    o += (size_t)(pad ? G + 1 : G) * (pad ? L + 2 : L) * C * 8;
+    m.bins = o;  // LO[G + 1][L + 2][C] (uint32) then HI[G + 1][L + 2][C] (int32)
+    o += (size_t)(G + 1) * (L + 2) * C * 8;
     m.K = o;
     o += (size_t)G * 4;
     m.Kp = o;
@@ -324,7 +324,8 @@ struct Expo<float> {
 // spare group, which keeps the four rows' work straight-line.
 template <typename T, int L, int CC>
 __device__ __forceinline__ void consume_quad_fast(const SAddr& sa, const int32_t* tk, const T* tv, const int* sK,
-                                                  int r0, int G, int copy, unsigned short* slist, uint32_t scnt_addr) {
+                                                  int r0, int G, int spare, int copy, unsigned short* slist,
+                                                  uint32_t scnt_addr) {
     constexpr uint32_t LP = L + 2;  // levels per group in the padded table
     // plain loads (the staged tile and the windows do not change during
     // this phase), so that the compiler may start the next row's loads
@@ -351,7 +352,7 @@ __device__ __forceinline__ void consume_quad_fast(const SAddr& sa, const int32_t
         // its window, K - kb >= L, that all its digits drop out); the other
         // digits follow at fixed offsets (past the window: spare levels)
         const bool adds = ok && K - kb < L;
-        const uint32_t tg = adds ? (uint32_t)gq[q] * LP + (uint32_t)(K - kb) : (uint32_t)G * LP;
+        const uint32_t tg = adds ? (uint32_t)gq[q] * LP + (uint32_t)(K - kb) : (uint32_t)spare * LP;
         const uint32_t a = sa.lo + 4u * (tg * CC + (uint32_t)copy);
         constexpr int ND = L < 3 ? L : 3;
         unsigned old[ND];

@@ -186,32 +186,34 @@ __device__ void clear_table(int G, const Table& t, int* sK, int* sKp, unsigned* 
 
 // At most 96 registers: two 8-warp CTAs per SM, and the compiler's own
 // choice for four levels otherwise grew past 110 with no gain.
-template <typename T, int L, int NCW>
+// CC: copies of the table (a.C), fixed at compile time for the hot loop.
+template <typename T, int L, int NCW, int CC>
 __global__ void __maxnreg__(96) k_fused_multi(MultiArgs a, int dtype) {
     constexpr int NC = 32 * NCW;
     extern __shared__ __align__(128) unsigned char smem[];
     const FusedSmem m = fused_layout<T>(a.S, a.R, a.Gcap, L, a.C);
     uint64_t* full = reinterpret_cast<uint64_t*>(smem + m.bars);
     uint64_t* empty = full + a.S;
-    int* ctl = reinterpret_cast<int*>(smem + m.ctl);  // cnt[3][2] at 0..5, abort at 6
+    int* ctl = reinterpret_cast<int*>(smem + m.ctl);  // cnt[3][2] at 0..5, abort at 6, slow counts[3] at 8..10
     StageMeta* meta = reinterpret_cast<StageMeta*>(smem + m.total);  // S entries
     int32_t* skeys = reinterpret_cast<int32_t*>(smem + m.keys);
     T* svals = reinterpret_cast<T*>(smem + m.vals);
     Table tab;
     tab.lo = reinterpret_cast<unsigned*>(smem + m.bins);
-    tab.hi = reinterpret_cast<int*>(tab.lo + (size_t)a.Gcap * L * a.C);
-    tab.L = L;
+    tab.hi = reinterpret_cast<int*>(tab.lo + (size_t)(a.Gcap + 1) * (L + 2) * a.C);
+    tab.L = L + 2;  // level stride of the padded table (levels L, L + 1 and group Gcap are spare)
     tab.C = a.C;
     int* sK = reinterpret_cast<int*>(smem + m.K);
     int* sKp = reinterpret_cast<int*>(smem + m.Kp);
     unsigned* sF = reinterpret_cast<unsigned*>(smem + m.F);
     unsigned short* dlist = reinterpret_cast<unsigned short*>(smem + m.dlist);
+    unsigned short* slist = reinterpret_cast<unsigned short*>(smem + m.slist);
     int* rlist = reinterpret_cast<int*>(smem + m.rlist);
     volatile int* abort_flag = &ctl[6];
 
     const int tid = threadIdx.x;
     const int R = a.R, S = a.S;
-    for (int i = tid; i < a.Gcap * L * a.C; i += blockDim.x) {
+    for (int i = tid; i < (a.Gcap + 1) * (L + 2) * a.C; i += blockDim.x) {
         tab.lo[i] = 0;
         tab.hi[i] = 0;
     }
@@ -327,6 +329,7 @@ __global__ void __maxnreg__(96) k_fused_multi(MultiArgs a, int dtype) {
             named_bar_sync(1, NC);
         }
         int* cnt = &ctl[2 * c3];
+        int* scnt = &ctl[8 + c3];
         const int32_t* tk_s = skeys + (size_t)s * R;
         const T* tv_s = svals + (size_t)s * R;
         const int32_t* gk = sm.keys;
@@ -334,14 +337,23 @@ __global__ void __maxnreg__(96) k_fused_multi(MultiArgs a, int dtype) {
         sa.keys = smem_addr(tk_s);
         sa.vals = smem_addr(tv_s);
         for (int r = 4 * ctid; r < sm.rows_tma; r += 4 * NC)
-            consume_quad<T, L>(sa, tk_s, tv_s, r, G, tab, copy, sK, sKp, sF, dlist, rlist, cnt, bad_key);
+            consume_quad_fast<T, L, CC>(sa, tk_s, tv_s, sK, r, G, a.Gcap, copy, slist, smem_addr(scnt));
         for (int r = sm.rows_tma + ctid; r < sm.rows; r += NC)
             consume_row<T, L>(gk[r], gv[r], r, G, tab, copy, sK, sKp, sF, dlist, rlist, cnt, bad_key);
         named_bar_sync(1, NC);
-        if (ctid == 0) {  // the counters of two tiles ago are no longer read
-            int* old = &ctl[2 * (c3 == 0 ? 2 : c3 - 1)];
-            old[0] = 0;
-            old[1] = 0;
+        if (ctid == 0) {  // the counters of the tile before are no longer read
+            const int p = c3 == 0 ? 2 : c3 - 1;
+            ctl[2 * p] = 0;
+            ctl[2 * p + 1] = 0;
+            ctl[8 + p] = 0;
+        }
+        const int ns = *scnt;
+        if (ns > 0) {  // the tile's unusual staged rows, one by one (claims, flags, deferrals)
+            for (int i2 = ctid; i2 < ns; i2 += NC) {
+                const int r = slist[i2];
+                consume_row<T, L>(tk_s[r], tv_s[r], r, G, tab, copy, sK, sKp, sF, dlist, rlist, cnt, bad_key);
+            }
+            named_bar_sync(1, NC);
         }
         const int nd = cnt[0], nr = cnt[1];
         if (nr > 0) {
@@ -460,9 +472,9 @@ cudaError_t launch_merge_items(int L, int dtype, const void* tasks, const void* 
 
 namespace {
 
-template <typename T, int L, int NCW>
+template <typename T, int L, int NCW, int CC>
 cudaError_t launch_multi_t(const MultiArgs& a, int dtype, int ctas, size_t smem, cudaStream_t s) {
-    auto kern = k_fused_multi<T, L, NCW>;
+    auto kern = k_fused_multi<T, L, NCW, CC>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     // a persistent grid must be resident at once (items come from a counter,
@@ -479,7 +491,11 @@ cudaError_t launch_multi_t(const MultiArgs& a, int dtype, int ctas, size_t smem,
 
 template <typename T, int L>
 cudaError_t launch_multi_ncw(int ncw, const MultiArgs& a, int dtype, int ctas, size_t smem, cudaStream_t s) {
-    return ncw == 8 ? launch_multi_t<T, L, 8>(a, dtype, ctas, smem, s) : launch_multi_t<T, L, 16>(a, dtype, ctas, smem, s);
+    if (a.C == 32)
+        return ncw == 8 ? launch_multi_t<T, L, 8, 32>(a, dtype, ctas, smem, s)
+                        : launch_multi_t<T, L, 16, 32>(a, dtype, ctas, smem, s);
+    return ncw == 8 ? launch_multi_t<T, L, 8, 1>(a, dtype, ctas, smem, s)
+                    : launch_multi_t<T, L, 16, 1>(a, dtype, ctas, smem, s);
 }
 
 template <typename T>

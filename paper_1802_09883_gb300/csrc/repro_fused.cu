@@ -57,7 +57,7 @@ template <typename T, int L, int NCW, bool SQ, int CC>
 __global__ void __launch_bounds__(32 * (NCW + 1), NCW == 8 ? 4 : (NCW == 16 ? 2 : 1)) k_fused(FusedArgs a) {
     constexpr int NC = 32 * NCW;
     extern __shared__ __align__(128) unsigned char smem[];
-    const FusedSmem m = fused_layout<T>(a.S, a.R, a.G, L, a.C, true);
+    const FusedSmem m = fused_layout<T>(a.S, a.R, a.G, L, a.C);
     uint64_t* full = reinterpret_cast<uint64_t*>(smem + m.bars);
     uint64_t* empty = full + a.S;
     int* ctl = reinterpret_cast<int*>(smem + m.ctl);  // cnt[3][2] at 0..5, abort at 6, slow counts[3] at 8..10
@@ -177,7 +177,7 @@ __global__ void __launch_bounds__(32 * (NCW + 1), NCW == 8 ? 4 : (NCW == 16 ? 2 
                 asm volatile("" ::: "memory");  // the stores stay ahead of the quads' shared loads
             }
             for (int r = 4 * ctid; r < R; r += 4 * NC)
-                consume_quad_fast<T, L, CC>(sa, tk, tv, sK, r, G, copy, slist, smem_addr(scnt));
+                consume_quad_fast<T, L, CC>(sa, tk, tv, sK, r, G, G, copy, slist, smem_addr(scnt));
         } else {
             *abort_flag = 1;  // written before the barrier, read after it: uniform
             atomicOr(a.errors, REPRO_ERR_TIMEOUT);
@@ -342,7 +342,7 @@ bool config_fits(const FusedPlanConfig& c, int G, int L, const DeviceInfo& di, s
         (c.ncw != 8 && c.ncw != 16 && !(pad && (c.ncw == 24 || c.ncw == 31))))
         return false;
     if (c.ctas_per_sm < 1 || c.ctas_per_sm > 4 || (c.copies != 1 && c.copies != 32)) return false;
-    const size_t bytes = fused_layout<T>(c.S, c.R, G, L, c.copies, pad).total + extra;
+    const size_t bytes = fused_layout<T>(c.S, c.R, G, L, c.copies).total + extra;
     return bytes * c.ctas_per_sm + 1024 * c.ctas_per_sm <= di.smem_per_sm && bytes <= di.smem_optin;
 }
 
@@ -519,9 +519,9 @@ bool fused_config_fits(int dtype, int L, int G, size_t extra_smem, const FusedPl
                               : config_fits<float>(cfg, G, L, device_info(), extra_smem, pad);
 }
 
-size_t fused_plan_smem(int dtype, int L, int G, const FusedPlanConfig& c, bool pad) {
-    return dtype == REPRO_F64 ? fused_layout<double>(c.S, c.R, G, L, c.copies, pad).total
-                              : fused_layout<float>(c.S, c.R, G, L, c.copies, pad).total;
+size_t fused_plan_smem(int dtype, int L, int G, const FusedPlanConfig& c) {
+    return dtype == REPRO_F64 ? fused_layout<double>(c.S, c.R, G, L, c.copies).total
+                              : fused_layout<float>(c.S, c.R, G, L, c.copies).total;
 }
 
 bool fused_supported(int dtype, int L, long long G, const void* keys, const void* vals, bool pad) {
@@ -559,8 +559,8 @@ cudaError_t launch_groupby_fused(const int32_t* keys, const void* vals, long lon
     a.S = cfg.S;
     a.C = cfg.copies;
     a.ntiles = n / cfg.R;
-    const size_t smem = dtype == REPRO_F64 ? fused_layout<double>(cfg.S, cfg.R, (int)G, L, cfg.copies, true).total
-                                           : fused_layout<float>(cfg.S, cfg.R, (int)G, L, cfg.copies, true).total;
+    const size_t smem = dtype == REPRO_F64 ? fused_layout<double>(cfg.S, cfg.R, (int)G, L, cfg.copies).total
+                                           : fused_layout<float>(cfg.S, cfg.R, (int)G, L, cfg.copies).total;
     // a persistent grid must be resident at once: never more CTAs per SM than
     // registers and shared memory allow
     const void* kern =

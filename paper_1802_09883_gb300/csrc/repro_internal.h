@@ -56,11 +56,11 @@ struct FusedPlanConfig {
 // else REPRO_FUSED_CFG, else the tuned cache, else the built-in rule -- the
 // first that fits; false if none fits.  Callers choose once per call and pass
 // the configuration on, so scratch sizing and launch always agree.
-// pad: the single-task kernel's padded table (see fused_layout); false: the
-// multi-task kernel's.
+// pad (single): configurations of the single-task kernel, which also has
+// 24- and 31-warp variants; false: the multi-task kernel's.
 bool fused_plan_config(int dtype, int L, int G, size_t extra_smem, FusedPlanConfig& cfg, bool pad = false);
 bool fused_config_fits(int dtype, int L, int G, size_t extra_smem, const FusedPlanConfig& cfg, bool pad = false);
-size_t fused_plan_smem(int dtype, int L, int G, const FusedPlanConfig& cfg, bool pad = false);
+size_t fused_plan_smem(int dtype, int L, int G, const FusedPlanConfig& cfg);
 bool fused_supported(int dtype, int L, long long G, const void* keys, const void* vals, bool pad = false);
 size_t fused_scratch_bytes(const FusedPlanConfig& cfg, int L, long long G, long long n);
 // max_ctas > 0 caps the number of CTAs (and so the partial tables in scratch);
