@@ -299,6 +299,18 @@ repro_status repro_groupby_sum_batched(const repro_task* tasks, int ntasks, repr
 repro_status repro_merge(void* dst, const void* src, repro_dtype dtype, int L,
                          int64_t num_groups, void* stream);
 
+/*
+ * dst += src over two arrays of num_records bare group records (the record
+ * layout above, no header), in place: the same per-record merge as
+ * repro_merge (operator+=(repro), Sec. V-B; eq. (2)/(3) for equal windows,
+ * the larger window and dropped low levels otherwise).  For blocks of
+ * records that ranks exchange (a reduce-scatter of states by group ranges):
+ * no state has to be built around a block to merge it.  Both arrays 8-byte
+ * aligned, device memory, not overlapping; src is only read.  The dtype is
+ * not needed (records are integers).  REPRO_EINVAL for bad arguments.
+ */
+repro_status repro_merge_records(void* dst, const void* src, int L, int64_t num_records, void* stream);
+
 /* out[g] = the group's reproducible sum (eq. (1)): V_j = T_j * u(K - j)
    rounded to nearest even in T (gradual underflow, overflow to +-Inf), then
    Q = (((V_{L-1} + V_{L-2}) + ...) + V_0) in T arithmetic.  A group with

@@ -72,6 +72,7 @@ def lib(build_if_stale: bool = True):
         L.repro_groupby_sum.argtypes = [vp, vp, i64, i32, i32, i64, vp, vp]
         L.repro_groupby_sum_noalloc.argtypes = [vp, vp, i64, i32, i32, i64, vp, vp]
         L.repro_merge.argtypes = [vp, vp, i32, i32, i64, vp]
+        L.repro_merge_records.argtypes = [vp, vp, i32, i64, vp]
         L.repro_finalize.argtypes = [vp, i32, i32, i64, vp, vp]
         L.repro_state_check.argtypes = [vp, u32p, vp]
         L.groupby_sum_fp64.argtypes = [vp, vp, i64, i64, vp, vp]
@@ -116,7 +117,7 @@ def lib(build_if_stale: bool = True):
         L.repro_groupby_stats.argtypes = [vp, vp, i64, i32, i32, i64, vp, vp]
         L.repro_stats_merge.argtypes = [vp, vp, i32, i32, i64, vp]
         L.repro_stats_finalize.argtypes = [vp, i32, i32, i64, vp, vp]
-        for name in ("repro_state_init", "repro_groupby_sum", "repro_groupby_sum_noalloc", "repro_merge",
+        for name in ("repro_state_init", "repro_groupby_sum", "repro_groupby_sum_noalloc", "repro_merge", "repro_merge_records",
                      "repro_finalize", "repro_batch_prepare", "repro_batch_run", "repro_batch_destroy",
                      "repro_batch_reset", "repro_batch_set_outputs", "repro_batch_finalize", "repro_batch_describe",
                      "repro_groupby_sum_batched", "repro_groupby_sum_cols", "repro_release_cached_memory",

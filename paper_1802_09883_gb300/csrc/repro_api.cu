@@ -321,6 +321,17 @@ repro_status repro_merge(void* dst, const void* src, repro_dtype dtype, int L, i
     return from_cuda(launch_merge(dst, src, dtype, L, num_groups, (cudaStream_t)stream));
 }
 
+repro_status repro_merge_records(void* dst, const void* src, int L, int64_t num_records, void* stream) {
+    if (!dst || !src || L < 1 || L > 4 || num_records < 0) return REPRO_EINVAL;
+    if (dst == src || (uintptr_t)dst % 8 || (uintptr_t)src % 8) return REPRO_EINVAL;
+    const size_t bytes = (size_t)num_records * (8 + 16 * (size_t)L);
+    const char* a = (const char*)dst;
+    const char* b = (const char*)src;
+    if (num_records > 0 && a < b + bytes && b < a + bytes) return REPRO_EINVAL;
+    if (num_records == 0) return REPRO_OK;
+    return from_cuda(launch_merge_records(dst, src, L, num_records, (cudaStream_t)stream));
+}
+
 repro_status repro_finalize(const void* state, repro_dtype dtype, int L, int64_t num_groups, void* out,
                             void* stream) {
     if (!state || !out || !valid_dtype(dtype) || !valid_shape(L, num_groups)) return REPRO_EINVAL;

@@ -147,6 +147,8 @@ cudaError_t launch_merge_items(int L, int dtype, const void* tasks, const void* 
                                const void* partials, cudaStream_t s);
 
 cudaError_t launch_merge(void* dst, const void* src, int dtype, int L, long long G, cudaStream_t s);
+// dst += src over G bare records (no headers).
+cudaError_t launch_merge_records(void* dst, const void* src, int L, long long G, cudaStream_t s);
 // state += C partial record arrays of G records each (parts[c * G + g]).
 cudaError_t launch_merge_partials(const void* parts, int C, long long G, void* state, int dtype, int L,
                                   cudaStream_t s);

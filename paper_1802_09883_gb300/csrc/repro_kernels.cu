@@ -183,6 +183,31 @@ __global__ void k_merge(unsigned char* dst, const unsigned char* src, int dtype,
     }
 }
 
+// dst += src over bare record arrays (no headers): the same per-group
+// merge as k_merge, for blocks of records exchanged between ranks.
+__global__ void k_merge_records(unsigned char* dst, const unsigned char* src, int L, long long G) {
+    const size_t rec = 8 + 16 * (size_t)L;
+    for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < G;
+         g += (long long)gridDim.x * blockDim.x) {
+        unsigned char* d = dst + (size_t)g * rec;
+        const unsigned char* s = src + (size_t)g * rec;
+        const int Kd = *reinterpret_cast<const int*>(d), Ks = *reinterpret_cast<const int*>(s);
+        const int K = max(Kd, Ks);
+        long long* db = reinterpret_cast<long long*>(d + 8);
+        const long long* sb = reinterpret_cast<const long long*>(s + 8);
+        __int128 acc[4];
+        for (int j = 0; j < L; ++j) {
+            __int128 v = 0;
+            if (j - (K - Kd) >= 0) v += bin_read(&db[2 * (j - (K - Kd))], &db[2 * (j - (K - Kd)) + 1]);
+            if (j - (K - Ks) >= 0) v += bin_read(&sb[2 * (j - (K - Ks))], &sb[2 * (j - (K - Ks)) + 1]);
+            acc[j] = v;
+        }
+        for (int j = 0; j < L; ++j) bin_write(&db[2 * j], &db[2 * j + 1], acc[j]);
+        *reinterpret_cast<int*>(d) = K;
+        *reinterpret_cast<unsigned*>(d + 4) |= *reinterpret_cast<const unsigned*>(s + 4);
+    }
+}
+
 // Eq. (1): V_j = RN_T(T_j u(K - j)), folded from the lowest level up.
 template <typename T>
 __global__ void k_finalize(const unsigned char* base, int dtype, int L, long long G, T* __restrict__ out) {
@@ -422,6 +447,16 @@ cudaError_t launch_merge(void* dst, const void* src, int dtype, int L, long long
     prof_begin(PROF_MERGE, s);
     k_merge<<<grid_for(G, th, device_info().sms * 8), th, 0, s>>>((unsigned char*)dst, (const unsigned char*)src,
                                                                    dtype, L, G);
+    prof_end(PROF_MERGE, s);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_merge_records(void* dst, const void* src, int L, long long G, cudaStream_t s) {
+    const int th = 256;
+    prof_begin(PROF_MERGE, s);
+    k_merge_records<<<grid_for(G, th, device_info().sms * 8), th, 0, s>>>((unsigned char*)dst,
+                                                                           (const unsigned char*)src, L, G);
     prof_end(PROF_MERGE, s);
     count_launches(1);
     return cudaGetLastError();

@@ -105,18 +105,17 @@ def or_over_ranks(x: int, group=None, device=None) -> int:
 # ------------------------------------------------------------ GPU states
 
 def device_merge(dtype, L: int) -> MergeFn:
-    """Merge of record arrays with the library's merge kernel (records are
-    copied into scratch states, whose headers the kernel checks)."""
-    from . import HEADER_BYTES, State
+    """Merge of record arrays in place with the library's record merge kernel
+    (repro_merge_records): no state is built around a block, nothing is
+    copied.  dtype is unused (records are exact integers)."""
+    from . import _check, _stream, lib
 
     def merge(dst: torch.Tensor, src: torch.Tensor) -> None:
+        if not (dst.is_contiguous() and src.is_contiguous()) or dst.shape != src.shape:
+            raise ValueError("record blocks must be contiguous and of the same shape")
         g = dst.shape[0]
-        a = State(g, L, dtype, device=dst.device)
-        b = State(g, L, dtype, device=dst.device)
-        a.tensor[HEADER_BYTES:].copy_(dst.reshape(-1))
-        b.tensor[HEADER_BYTES:].copy_(src.reshape(-1))
-        a.merge(b)
-        dst.reshape(-1).copy_(a.tensor[HEADER_BYTES:])
+        _check(lib().repro_merge_records(dst.data_ptr(), src.data_ptr(), L, g, _stream(dst.device)),
+               "repro_merge_records")
 
     return merge
 
