@@ -148,7 +148,7 @@ __device__ __forceinline__ void consume_row(int g, T b, int idx, int G, const Ta
 struct SAddr {
     uint32_t keys, vals;  // stage s starts at keys + 4 R s, vals + sizeof(T) R s
     uint32_t K;           // int K[G]
-    uint32_t lo, hi;      // table words [(g L + j) C + copy]
+    uint32_t lo, hi;      // table words [(g LP + j) C + copy], LP = L + 2 levels per group
 };
 
 // Value bit-words of four consecutive rows: (hi, lo) per row for double,
@@ -157,11 +157,6 @@ template <typename T>
 struct QuadWords;
 template <>
 struct QuadWords<double> {
-    static __device__ __forceinline__ void load(uint32_t a, uint32_t hi[4], uint32_t lo[4]) {
-        const uint4 p = lds_v4(a), q = lds_v4(a + 16);
-        lo[0] = p.x; hi[0] = p.y; lo[1] = p.z; hi[1] = p.w;
-        lo[2] = q.x; hi[2] = q.y; lo[3] = q.z; hi[3] = q.w;
-    }
     static __device__ __forceinline__ void load_ptr(const double* v, uint32_t hi[4], uint32_t lo[4]) {
         const uint4 p = reinterpret_cast<const uint4*>(v)[0], q = reinterpret_cast<const uint4*>(v)[1];
         lo[0] = p.x; hi[0] = p.y; lo[1] = p.z; hi[1] = p.w;
@@ -170,11 +165,6 @@ struct QuadWords<double> {
 };
 template <>
 struct QuadWords<float> {
-    static __device__ __forceinline__ void load(uint32_t a, uint32_t hi[4], uint32_t lo[4]) {
-        const uint4 p = lds_v4(a);
-        hi[0] = p.x; hi[1] = p.y; hi[2] = p.z; hi[3] = p.w;
-        lo[0] = lo[1] = lo[2] = lo[3] = 0u;
-    }
     static __device__ __forceinline__ void load_ptr(const float* v, uint32_t hi[4], uint32_t lo[4]) {
         const uint4 p = *reinterpret_cast<const uint4*>(v);
         hi[0] = p.x; hi[1] = p.y; hi[2] = p.z; hi[3] = p.w;
@@ -182,86 +172,6 @@ struct QuadWords<float> {
     }
 };
 
-template <typename T>
-__device__ __forceinline__ T words_value(uint32_t hi, uint32_t lo);
-template <>
-__device__ __forceinline__ double words_value<double>(uint32_t hi, uint32_t lo) {
-    return __longlong_as_double((long long)(((unsigned long long)hi << 32) | lo));
-}
-template <>
-__device__ __forceinline__ float words_value<float>(uint32_t hi, uint32_t) {
-    return __uint_as_float(hi);
-}
-
-// Phase A for four consecutive rows of a staged tile (r0 a multiple of 4):
-// vector loads, then -- when all four rows are ordinary (good key, normal
-// value inside its group's window) -- straight-line digits for the four rows
-// and predicated 32-bit atomics.  Failing that, when the only other rows are
-// zeros (+0 or -0: a discount column, say) the same straight-line code runs
-// with those rows' window set past the table, which switches off all their
-// atomics; the zero test stays off the common path, where it would cost
-// several percent.  Otherwise the rows go one by one through consume_row.
-template <typename T, int L>
-__device__ __forceinline__ void consume_quad(const SAddr& sa, const int32_t* tk, const T* tv, int r0, int G,
-                                             const Table& t, int copy, int* sK, int* sKp, unsigned* sF,
-                                             unsigned short* dlist, int* rlist, int* cnt, bool& bad_key) {
-    const uint4 k4 = lds_v4(sa.keys + 4u * (uint32_t)r0);
-    const int gq[4] = {(int)k4.x, (int)k4.y, (int)k4.z, (int)k4.w};
-    uint32_t vhi[4], vlo[4];
-    QuadWords<T>::load(sa.vals + (uint32_t)sizeof(T) * (uint32_t)r0, vhi, vlo);
-    int kb[4], K[4];
-    bool fast = true;
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        const bool ok_key = (unsigned)gq[q] < (unsigned)G;
-        const bool ok_val = Lean<T>::decode_words(vhi[q], kb[q]);
-        K[q] = (int)lds_u32(sa.K + 4u * (uint32_t)(ok_key ? gq[q] : 0));
-        fast = fast && ok_key && ok_val && kb[q] <= K[q];
-    }
-    if (!fast) {
-        bool masked = true;
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const bool zero = Lean<T>::is_zero(vhi[q], vlo[q]);
-            const bool ok_val = Lean<T>::decode_words(vhi[q], kb[q]);
-            masked = masked && (unsigned)gq[q] < (unsigned)G && (zero || (ok_val && kb[q] <= K[q]));
-            if (zero) K[q] = kb[q] + L;  // every level of the row falls past the table: no atomic
-        }
-        if (!masked) {  // some row is special, has a bad key, or must wait for a raise
-#pragma unroll
-            for (int q = 0; q < 4; ++q)
-                consume_row<T, L>(gq[q], words_value<T>(vhi[q], vlo[q]), r0 + q, G, t, copy, sK, sKp, sF, dlist,
-                                  rlist, cnt, bad_key);
-            return;
-        }
-    }
-    // straight-line: four rows' digits, then predicated atomics.  Top and
-    // middle digits are almost never zero (adding zero is harmless); the low
-    // digit is zero whenever the value starts above its boundary.
-    unsigned lo[12];
-    int hi[12];
-    uint32_t at[12];
-    bool on[12];
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        Lean<T>::digits(vhi[q], vlo[q], kb[q], &lo[3 * q], &hi[3 * q]);
-        const int j = K[q] - kb[q];  // window level of the value's top digit
-        const uint32_t row = 4u * ((uint32_t)gq[q] * (uint32_t)(L * t.C) + (uint32_t)copy);
-#pragma unroll
-        for (int k = 0; k < 3; ++k) {
-            on[3 * q + k] = (j + k < L) && (k < 2 || (lo[3 * q + k] | (unsigned)hi[3 * q + k]) != 0u);
-            at[3 * q + k] = row + 4u * (uint32_t)(min(j + k, L - 1) * t.C);
-        }
-    }
-    unsigned old[12];
-#pragma unroll
-    for (int i = 0; i < 12; ++i) old[i] = atom_add_if(on[i], sa.lo + at[i], lo[i]);
-#pragma unroll
-    for (int i = 0; i < 12; ++i) {
-        const int h = hi[i] + (int)((unsigned)(old[i] + lo[i]) < old[i]);
-        red_add_if(on[i] && h != 0, sa.hi + at[i], h);
-    }
-}
 
 // The two halves of adding digit (lo, hi) to a table word pair: a shared
 // atomic on the LO word returns its old value; hi plus the carry out of

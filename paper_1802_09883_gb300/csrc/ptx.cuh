@@ -111,31 +111,6 @@ __device__ __forceinline__ uint32_t lds_u32(uint32_t a) {
     return v;
 }
 
-// Shared-memory atomic add, executed only when `pred` holds (a predicated
-// instruction, not a branch); returns the previous value, which is
-// unspecified when the add is skipped.
-__device__ __forceinline__ unsigned atom_add_if(bool pred, uint32_t addr, unsigned v) {
-    unsigned old;
-    asm volatile(
-        "{\n\t.reg .pred q;\n\t"
-        "setp.ne.u32 q, %3, 0;\n\t"
-        "@q atom.shared.add.u32 %0, [%1], %2;\n\t}"
-        : "=r"(old)
-        : "r"(addr), "r"(v), "r"((unsigned)pred)
-        : "memory");
-    return old;
-}
-
-// Shared-memory reduction add (no return), executed only when `pred` holds.
-__device__ __forceinline__ void red_add_if(bool pred, uint32_t addr, int v) {
-    asm volatile(
-        "{\n\t.reg .pred q;\n\t"
-        "setp.ne.u32 q, %2, 0;\n\t"
-        "@q red.shared.add.s32 [%0], %1;\n\t}" ::"r"(addr),
-        "r"(v), "r"((unsigned)pred)
-        : "memory");
-}
-
 // Barrier over the first `threads` threads of the CTA (named barrier `id`).
 __device__ __forceinline__ void named_bar_sync(int id, int threads) {
     asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(threads) : "memory");

@@ -37,7 +37,7 @@ struct ColsArgs {
 };
 
 struct ColsSmem {
-    size_t bars, ctl, keys, vals, bins, K, Kp, F, dlist, rlist, total;
+    size_t bars, ctl, keys, vals, bins, K, Kp, F, dlist, slist, rlist, total;
     size_t ring, bins_col, grp_col;  // bytes of one value ring, one column's bins, one column's K (or Kp, F)
 };
 
@@ -56,7 +56,7 @@ __host__ __device__ inline ColsSmem cols_layout(int S, int R, int G, int L, int 
     m.ring = align_up((size_t)S * R * sizeof(T), 128);
     m.vals = o;
     o += m.ring * NV;
-    m.bins_col = (size_t)G * L * C * 8;
+    m.bins_col = (size_t)(G + 1) * (L + 2) * C * 8;  // padded as the single-pass tables
     m.bins = o;
     o += m.bins_col * NV;
     m.grp_col = (size_t)G * 4;
@@ -68,6 +68,8 @@ __host__ __device__ inline ColsSmem cols_layout(int S, int R, int G, int L, int 
     o += m.grp_col * NV;
     m.dlist = o;
     o += (size_t)R * 2;
+    m.slist = o;
+    o += (size_t)R * 2;
     o = align_up(o, 4);
     m.rlist = o;
     o += (size_t)(R < G ? R : G) * 4;
@@ -75,16 +77,18 @@ __host__ __device__ inline ColsSmem cols_layout(int S, int R, int G, int L, int 
     return m;
 }
 
-template <typename T, int L, int NCW, int NV, bool SQUARE>
+// CC: copies of each column's table (a.C), fixed at compile time.
+template <typename T, int L, int NCW, int NV, bool SQUARE, int CC>
 __global__ void __launch_bounds__(32 * (NCW + 1)) k_fused_cols(ColsArgs a) {
     constexpr int NC = 32 * NCW;
     extern __shared__ __align__(128) unsigned char smem[];
     const ColsSmem m = cols_layout<T>(a.S, a.R, a.G, L, a.C, NV);
     uint64_t* full = reinterpret_cast<uint64_t*>(smem + m.bars);
     uint64_t* empty = full + a.S;
-    int* ctl = reinterpret_cast<int*>(smem + m.ctl);  // cnt[3][2] at 0..5, abort at 6
+    int* ctl = reinterpret_cast<int*>(smem + m.ctl);  // cnt[3][2] at 0..5, abort at 6, slow counts[3] at 8..10
     int32_t* skeys = reinterpret_cast<int32_t*>(smem + m.keys);
     unsigned short* dlist = reinterpret_cast<unsigned short*>(smem + m.dlist);
+    unsigned short* slist = reinterpret_cast<unsigned short*>(smem + m.slist);
     int* rlist = reinterpret_cast<int*>(smem + m.rlist);
     volatile int* abort_flag = &ctl[6];
     const int tid = threadIdx.x;
@@ -93,8 +97,8 @@ __global__ void __launch_bounds__(32 * (NCW + 1)) k_fused_cols(ColsArgs a) {
     auto table = [&](int c) {
         Table t;
         t.lo = reinterpret_cast<unsigned*>(smem + m.bins + m.bins_col * c);
-        t.hi = reinterpret_cast<int*>(t.lo + (size_t)G * L * a.C);
-        t.L = L;
+        t.hi = reinterpret_cast<int*>(t.lo + (size_t)(G + 1) * (L + 2) * a.C);
+        t.L = L + 2;  // level stride of the padded table
         t.C = a.C;
         return t;
     };
@@ -172,6 +176,7 @@ __global__ void __launch_bounds__(32 * (NCW + 1)) k_fused_cols(ColsArgs a) {
     // one column over the rows of a staged tile (or the tail), then its raises
     auto column_pass = [&](int c, const int32_t* tk, const T* tv, int rows, bool staged) {
         int* cnt = &ctl[2 * (tcount % 3)];
+        int* scnt = &ctl[8 + tcount % 3];
         const Table tab = table(c);
         int* sK = colK(c);
         int* sKp = colKp(c);
@@ -184,16 +189,25 @@ __global__ void __launch_bounds__(32 * (NCW + 1)) k_fused_cols(ColsArgs a) {
             sa.keys = smem_addr(tk);
             sa.vals = smem_addr(tv);
             for (int r = 4 * ctid; r < rows; r += 4 * NC)
-                consume_quad<T, L>(sa, tk, tv, r, G, tab, copy, sK, sKp, sF, dlist, rlist, cnt, bad_key);
+                consume_quad_fast<T, L, CC>(sa, tk, tv, sK, r, G, G, copy, slist, smem_addr(scnt));
         } else {
             for (int r = ctid; r < rows; r += NC)
                 consume_row<T, L>(tk[r], tv[r], r, G, tab, copy, sK, sKp, sF, dlist, rlist, cnt, bad_key);
         }
         named_bar_sync(1, NC);
-        if (ctid == 0) {  // the counters of two passes ago are no longer read
-            int* old = &ctl[2 * ((tcount + 2) % 3)];
-            old[0] = 0;
-            old[1] = 0;
+        if (ctid == 0) {  // the counters of the pass before are no longer read
+            const int p = (tcount + 2) % 3;
+            ctl[2 * p] = 0;
+            ctl[2 * p + 1] = 0;
+            ctl[8 + p] = 0;
+        }
+        const int ns = *scnt;
+        if (ns > 0) {  // the pass's unusual rows, one by one (claims, flags, deferrals)
+            for (int i2 = ctid; i2 < ns; i2 += NC) {
+                const int r = slist[i2];
+                consume_row<T, L>(tk[r], tv[r], r, G, tab, copy, sK, sKp, sF, dlist, rlist, cnt, bad_key);
+            }
+            named_bar_sync(1, NC);
         }
         const int nd = cnt[0], nr = cnt[1];
         if (nr > 0) {
@@ -264,24 +278,25 @@ __global__ void __launch_bounds__(32 * (NCW + 1)) k_fused_cols(ColsArgs a) {
 }
 
 template <typename T, int L, int NV, bool SQ>
-const void* cols_kernel() {
-    return (const void*)k_fused_cols<T, L, 8, NV, SQ>;
+const void* cols_kernel(int C) {
+    return C == 32 ? (const void*)k_fused_cols<T, L, 8, NV, SQ, 32> : (const void*)k_fused_cols<T, L, 8, NV, SQ, 1>;
 }
 
 template <typename T, int NV, bool SQ>
-const void* cols_kernel_L(int L) {
+const void* cols_kernel_L(int L, int C) {
     switch (L) {
-        case 1: return cols_kernel<T, 1, NV, SQ>();
-        case 2: return cols_kernel<T, 2, NV, SQ>();
-        case 3: return cols_kernel<T, 3, NV, SQ>();
-        default: return cols_kernel<T, 4, NV, SQ>();
+        case 1: return cols_kernel<T, 1, NV, SQ>(C);
+        case 2: return cols_kernel<T, 2, NV, SQ>(C);
+        case 3: return cols_kernel<T, 3, NV, SQ>(C);
+        default: return cols_kernel<T, 4, NV, SQ>(C);
     }
 }
 
 // The kernels built: four plain columns, and x with x*x.
-const void* cols_kernel_of(int dtype, int L, bool square) {
-    if (dtype == REPRO_F64) return square ? cols_kernel_L<double, 2, true>(L) : cols_kernel_L<double, 4, false>(L);
-    return square ? cols_kernel_L<float, 2, true>(L) : cols_kernel_L<float, 4, false>(L);
+const void* cols_kernel_of(int dtype, int L, bool square, int C) {
+    if (dtype == REPRO_F64)
+        return square ? cols_kernel_L<double, 2, true>(L, C) : cols_kernel_L<double, 4, false>(L, C);
+    return square ? cols_kernel_L<float, 2, true>(L, C) : cols_kernel_L<float, 4, false>(L, C);
 }
 
 size_t cols_smem(int dtype, int L, int G, int NV, const FusedPlanConfig& c) {
@@ -321,7 +336,8 @@ int cols_ctas(long long ntiles, const FusedPlanConfig& cfg, int resident) {
 
 template <typename T, int L, int NV, bool SQ>
 void launch_t(const ColsArgs& a, int ctas, size_t smem, cudaStream_t s) {
-    k_fused_cols<T, L, 8, NV, SQ><<<ctas, 32 * 9, smem, s>>>(a);
+    if (a.C == 32) k_fused_cols<T, L, 8, NV, SQ, 32><<<ctas, 32 * 9, smem, s>>>(a);
+    else k_fused_cols<T, L, 8, NV, SQ, 1><<<ctas, 32 * 9, smem, s>>>(a);
 }
 
 template <typename T, int NV, bool SQ>
@@ -370,7 +386,7 @@ cudaError_t launch_groupby_cols(const int32_t* keys, const void* const* vals, in
     FusedPlanConfig cfg;
     if (!cols_config(dtype, L, G, nv, cfg)) return cudaErrorInvalidValue;
     const size_t smem = cols_smem(dtype, L, (int)G, nv, cfg);
-    const int resident = resident_ctas(cols_kernel_of(dtype, L, square), 32 * 9, smem);
+    const int resident = resident_ctas(cols_kernel_of(dtype, L, square, cfg.copies), 32 * 9, smem);
     if (resident < 1) return cudaErrorInvalidConfiguration;
     ColsArgs a{};
     a.keys = keys;

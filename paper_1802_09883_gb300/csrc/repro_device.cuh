@@ -196,109 +196,21 @@ __device__ __forceinline__ void digits3<float>(const Split& s, long long& top, l
     }
 }
 
-// ------------------------------------------------ lean path for normal values
-//
-// The same digits as digits3, computed on 32-bit words for values with a
-// normal exponent whose window is in range (all but zeros, subnormals, NaN,
-// Inf and out-of-range values).  Each digit comes out as the pair
-// (lo, hi) = (low 32 bits, signed high part) of its two's complement.
-//
-// double: X = |b| / u(kb - 2) is the 53-bit significand shifted left by
-// s2 = E + 79 - 40 kb (27..66); its four 32-bit words give the 40-bit pieces
-// x0 = X[0,40), x1 = X[40,80), x2 = X[80,120) as (low word, high byte).
-// float:  X = significand << s2, s2 = E + 35 - 18 kb (12..29), below 2^53.
-// K(b) = (E + 52) / 40 (double), (E + 23) / 18 (float), by multiply-shift.
+// Zero test on a value's bit words (hi, lo) for double, the single word for
+// float: +0 and -0 add nothing.
 template <typename T>
 struct Lean;
 
 template <>
 struct Lean<double> {
-    static __device__ __forceinline__ bool decode(double b, uint32_t& vhi, uint32_t& vlo, int& kb) {
-        const unsigned long long bits = (unsigned long long)__double_as_longlong(b);
-        vhi = (uint32_t)(bits >> 32);
-        vlo = (uint32_t)bits;
-        return decode_words(vhi, kb);
-    }
-    // +0 or -0 (adds nothing)
     static __device__ __forceinline__ bool is_zero(uint32_t vhi, uint32_t vlo) {
         return ((vhi << 1) | vlo) == 0u;
-    }
-    // from the high word only (the low word is not needed to classify)
-    static __device__ __forceinline__ bool decode_words(uint32_t vhi, int& kb) {
-        const int E = (int)((vhi >> 20) & 0x7ffu);
-        kb = ((E + 52) * 52429) >> 21;  // (E + 52) / 40 for E + 52 < 2^11
-        return (unsigned)(E - 1) < 2027u;  // normal and K(b) <= 51
-    }
-    static __device__ __forceinline__ void digits(uint32_t vhi, uint32_t vlo, int kb, unsigned lo[3], int hi[3]) {
-        const int E = (int)((vhi >> 20) & 0x7ffu);
-        const int s2 = E + 79 - 40 * kb;
-        const uint32_t mh = (vhi & 0xfffffu) | 0x100000u, ml = vlo;
-        const int q = s2 >> 5, r = s2 & 31;
-        const uint32_t v0 = ml << r, v1 = __funnelshift_l(ml, mh, r), v2 = __funnelshift_l(mh, 0u, r);
-        const uint32_t w0 = q == 0 ? v0 : 0u;
-        const uint32_t w1 = q == 0 ? v1 : (q == 1 ? v0 : 0u);
-        const uint32_t w2 = q == 0 ? v2 : (q == 1 ? v1 : v0);
-        const uint32_t w3 = q == 0 ? 0u : (q == 1 ? v2 : v1);
-        const uint32_t x0l = w0, x0h = w1 & 0xffu;
-        const uint32_t x1l = __funnelshift_r(w1, w2, 8), x1h = (w2 >> 8) & 0xffu;
-        const uint32_t x2l = __funnelshift_r(w2, w3, 16), x2h = (w3 >> 16) & 0xffu;
-        // round-to-nearest-even carries at the 40-bit boundaries: with
-        // H = 2^39, carry = [x + s > H] = floor((x + (H - 1) + s) / 2^40),
-        // s the tie-break bit (parity above for c1; for c2 the sticky bit of
-        // x0 or, on an exact tie, the parity of x2)
-        const uint32_t s1 = x1l & 1u;
-        const uint32_t s2b = (uint32_t)((x0h | x0l) != 0u) | (x2l & 1u);
-        const uint32_t c1 = (x0h + 0x7fu + (uint32_t)(((unsigned long long)x0l + 0xffffffffull + s1) >> 32)) >> 8;
-        const uint32_t c2 = (x1h + 0x7fu + (uint32_t)(((unsigned long long)x1l + 0xffffffffull + s2b) >> 32)) >> 8;
-        lo[0] = x2l + c2;
-        hi[0] = (int)x2h + (int)(lo[0] < c2);
-        lo[1] = x1l + c1;
-        hi[1] = (int)x1h + (int)(lo[1] < c1) - 256 * (int)c2;
-        lo[2] = x0l;
-        hi[2] = (int)x0h - 256 * (int)c1;
-        if (vhi >> 31) {
-#pragma unroll
-            for (int k = 0; k < 3; ++k) {
-                hi[k] = -hi[k] - (int)(lo[k] != 0u);
-                lo[k] = 0u - lo[k];
-            }
-        }
     }
 };
 
 template <>
 struct Lean<float> {
-    static __device__ __forceinline__ bool decode(float b, uint32_t& bits, uint32_t& unused, int& kb) {
-        bits = __float_as_uint(b);
-        unused = 0;
-        return decode_words(bits, kb);
-    }
-    // +0 or -0 (adds nothing)
     static __device__ __forceinline__ bool is_zero(uint32_t bits, uint32_t) { return (bits << 1) == 0u; }
-    static __device__ __forceinline__ bool decode_words(uint32_t bits, int& kb) {
-        const int E = (int)((bits >> 23) & 0xffu);
-        kb = ((E + 23) * 3641) >> 16;  // (E + 23) / 18 for E + 23 < 2^9
-        return (unsigned)(E - 1) < 246u;  // normal and K(b) <= 14
-    }
-    static __device__ __forceinline__ void digits(uint32_t bits, uint32_t, int kb, unsigned lo[3], int hi[3]) {
-        const int E = (int)((bits >> 23) & 0xffu);
-        const int s2 = E + 35 - 18 * kb;
-        const uint32_t M = (bits & 0x7fffffu) | 0x800000u;
-        const uint32_t Xl = M << s2, Xh = M >> (32 - s2);
-        const int x0 = (int)(Xl & 0x3ffffu);
-        const int x1 = (int)(__funnelshift_r(Xl, Xh, 18) & 0x3ffffu);
-        const int x2 = (int)(Xh >> 4);
-        const int c1 = (x0 + 0x1ffff + (x1 & 1)) >> 18;
-        const int c2 = (x1 + 0x1ffff + ((x0 != 0) | (x2 & 1))) >> 18;
-        int d[3] = {x2 + c2, x1 + c1 - (c2 << 18), x0 - (c1 << 18)};
-        const bool neg = (bits >> 31) != 0;
-#pragma unroll
-        for (int k = 0; k < 3; ++k) {
-            const int v = neg ? -d[k] : d[k];
-            lo[k] = (unsigned)v;
-            hi[k] = v >> 31;
-        }
-    }
 };
 
 // ------------------------------------------ signed digits for the hot loop
