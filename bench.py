@@ -44,6 +44,10 @@ def parse():
     ap.add_argument("--G", type=int, default=1 << 10)
     ap.add_argument("--dist", default="uniform", choices=["uniform", "zipf"])
     ap.add_argument("--L", type=int, default=3)
+    ap.add_argument("--key-span", type=int, default=0,
+                    help="draw the keys over [0, span) while the state declares --G groups (0: span = G)")
+    ap.add_argument("--adaptive", action="store_true",
+                    help="aggregate through repro_groupby_sum_adaptive (depth from the keys' range)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--oracle-threads", type=int, default=0,
                     help="host threads of the CPU oracle (reference arm, cpu_baseline); 0: all cores")
@@ -155,9 +159,12 @@ def run_ours(args, rank, world, local_rank):
     lib = R.lib()
 
     # weak scaling: every rank aggregates its own shard of the same shape
-    w = WL.sweep_cell(args.G, args.dist, args.L, n=args.n, device=dev,
+    span = args.key_span if args.key_span > 0 else args.G
+    w = WL.sweep_cell(span, args.dist, args.L, n=args.n, device=dev,
                       seed=None if rank == 0 else 1000 + rank)
+    w.G = args.G  # the declared group count (keys reach [0, span))
     G, L, n = w.G, w.L, w.n
+    depth = None
     st = R.State(G, L, torch.float64, device=dev)
     out = torch.empty(G, dtype=torch.float64, device=dev)
     stream = torch.cuda.current_stream(dev)
@@ -172,8 +179,12 @@ def run_ours(args, rank, world, local_rank):
             R.tune_save(args.tune_file)
 
     def step():
+        nonlocal depth
         st.reset()
-        st.add(w.keys, w.values)
+        if args.adaptive:
+            depth = st.add_adaptive(w.keys, w.values)
+        else:
+            st.add(w.keys, w.values)
         st.finalize(out)
 
     def barrier():
@@ -305,8 +316,11 @@ def run_ours(args, rank, world, local_rank):
             "dtype": "f64",
             "data": "synthetic",
             "config": {"workload": f"grouped SUM, {n} rows, {G} groups {args.dist}, repro<double,{L}>, "
-                                   f"exponents U[-40,40], 10% cancelling pairs",
-                       "n": n, "G": G, "dist": args.dist, "L": L, "parallelism": f"shards{world}",
+                                   f"exponents U[-40,40], 10% cancelling pairs"
+                                   + (f", keys over [0, {span})" if span != G else "")
+                                   + (", adaptive depth" if args.adaptive else ""),
+                       "n": n, "G": G, "key_span": span, "adaptive_depth": depth,
+                       "dist": args.dist, "L": L, "parallelism": f"shards{world}",
                        "l2": "inputs (12 B/row) far larger than L2; no flush"},
             "hbm_gbs_algorithmic": algo_bytes / (ms / 1e3) / 1e9,
             "roofline": roof,

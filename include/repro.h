@@ -131,6 +131,29 @@ repro_status repro_groupby_sum(const int32_t* keys, const void* values, int64_t 
                                void* stream);
 
 /*
+ * repro_groupby_sum with the partitioning depth chosen from the data.  The
+ * paper picks the number of partitioning levels by the number of groups:
+ * enough levels that the last one aggregates in cache, no more, and it
+ * proposes choosing them adaptively, from the groups actually met, instead
+ * of offline (Sec. V-C, "Tuning Buffer Size and Partitioning Depth").  Here
+ * num_groups only bounds the keys; when it exceeds one shared-memory table,
+ * a probe kernel first reads the keys once (4 bytes per row) for their
+ * range, the stream is synchronised and the depth is picked for the groups
+ * the keys reach, max(key) + 1: no partitioning while one table holds them
+ * (a single pass over records [0, max(key)]), else one or two partition
+ * passes and a fan-out sized for that many groups (heavy partitions are
+ * then split over several CTAs as in repro_groupby_sum).  Same arguments
+ * and the same result bits as repro_groupby_sum.  *depth_out (may be NULL)
+ * receives the partition passes taken: 0, 1 or 2, or -1 when the call went
+ * the plain way (keys or values not 16-byte aligned, bad keys, or a stream
+ * under capture: then no probe runs and the depth is the built-in rule's).
+ * Unlike repro_groupby_sum this call synchronises `stream` once when it
+ * probes.
+ */
+repro_status repro_groupby_sum_adaptive(const int32_t* keys, const void* values, int64_t n, repro_dtype dtype, int L,
+                                        int64_t num_groups, void* state, int* depth_out, void* stream);
+
+/*
  * repro_groupby_sum on columns in page-locked HOST memory (cudaHostAlloc /
  * pinned tensors; anything else is REPRO_EINVAL): the rows are staged in
  * chunks of 2^24 through two device buffers from the library's pool, copied

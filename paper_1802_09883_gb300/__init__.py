@@ -71,6 +71,7 @@ def lib(build_if_stale: bool = True):
         L.repro_state_init.argtypes = [vp, i32, i32, i64, vp]
         L.repro_groupby_sum.argtypes = [vp, vp, i64, i32, i32, i64, vp, vp]
         L.repro_groupby_sum_noalloc.argtypes = [vp, vp, i64, i32, i32, i64, vp, vp]
+        L.repro_groupby_sum_adaptive.argtypes = [vp, vp, i64, i32, i32, i64, vp, ctypes.POINTER(ctypes.c_int), vp]
         L.repro_merge.argtypes = [vp, vp, i32, i32, i64, vp]
         L.repro_merge_records.argtypes = [vp, vp, i32, i64, vp]
         L.repro_finalize.argtypes = [vp, i32, i32, i64, vp, vp]
@@ -117,7 +118,7 @@ def lib(build_if_stale: bool = True):
         L.repro_groupby_stats.argtypes = [vp, vp, i64, i32, i32, i64, vp, vp]
         L.repro_stats_merge.argtypes = [vp, vp, i32, i32, i64, vp]
         L.repro_stats_finalize.argtypes = [vp, i32, i32, i64, vp, vp]
-        for name in ("repro_state_init", "repro_groupby_sum", "repro_groupby_sum_noalloc", "repro_merge", "repro_merge_records",
+        for name in ("repro_state_init", "repro_groupby_sum", "repro_groupby_sum_noalloc", "repro_groupby_sum_adaptive", "repro_merge", "repro_merge_records",
                      "repro_finalize", "repro_batch_prepare", "repro_batch_run", "repro_batch_destroy",
                      "repro_batch_reset", "repro_batch_set_outputs", "repro_batch_finalize", "repro_batch_describe",
                      "repro_groupby_sum_batched", "repro_groupby_sum_cols", "repro_release_cached_memory",
@@ -208,6 +209,21 @@ class State:
                                        self.G, self.tensor.data_ptr(), _stream(self.device)),
                "repro_groupby_sum")
         return self
+
+    def add_adaptive(self, keys: torch.Tensor, values: torch.Tensor) -> int:
+        """As add(), with the partitioning depth picked from the keys' range
+        (a probe of the keys and one stream synchronisation first); returns
+        the partition passes taken (0, 1, 2; -1: the plain way)."""
+        _require_cuda(keys, "keys")
+        _require_cuda(values, "values")
+        if keys.dtype != torch.int32 or values.dtype != self.dtype or keys.numel() != values.numel():
+            raise ValueError("keys int32 and values of the state's dtype, same length")
+        keys, values = keys.contiguous(), values.contiguous()
+        depth = ctypes.c_int(-1)
+        _check(lib().repro_groupby_sum_adaptive(keys.data_ptr(), values.data_ptr(), keys.numel(), self.code, self.L,
+                                                self.G, self.tensor.data_ptr(), ctypes.byref(depth),
+                                                _stream(self.device)), "repro_groupby_sum_adaptive")
+        return depth.value
 
     def merge(self, other: "State"):
         if (other.G, other.L, other.dtype) != (self.G, self.L, self.dtype):

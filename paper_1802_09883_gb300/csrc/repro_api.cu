@@ -132,6 +132,9 @@ using namespace rp;
 
 namespace rp {
 
+// Coarse buckets of the adaptive entry point's key probe (at most).
+constexpr long long kProbeBuckets = 4096;
+
 // Rows per staged chunk of repro_groupby_sum_host (two chunks in flight).
 constexpr long long kHostChunkRows = 1ll << 24;
 
@@ -192,6 +195,63 @@ repro_status repro_groupby_sum(const int32_t* keys, const void* values, int64_t 
     if ((uintptr_t)state % 16 || (uintptr_t)keys % 4 || (uintptr_t)values % (dtype == REPRO_F64 ? 8 : 4))
         return REPRO_EINVAL;
     return (repro_status)groupby_dispatch(keys, values, n, dtype, L, num_groups, state, (cudaStream_t)stream);
+}
+
+repro_status repro_groupby_sum_adaptive(const int32_t* keys, const void* values, int64_t n, repro_dtype dtype, int L,
+                                        int64_t num_groups, void* state, int* depth_out, void* stream) {
+    if (depth_out) *depth_out = -1;
+    if (!state || !valid_dtype(dtype) || !valid_shape(L, num_groups) || n < 0) return REPRO_EINVAL;
+    if (n > 0 && (!keys || !values)) return REPRO_EINVAL;
+    if ((uintptr_t)state % 16 || (uintptr_t)keys % 4 || (uintptr_t)values % (dtype == REPRO_F64 ? 8 : 4))
+        return REPRO_EINVAL;
+    if (n == 0) return REPRO_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    FusedPlanConfig cfg;
+    if (fused_supported(dtype, L, num_groups, keys, values, true) &&
+        fused_plan_config(dtype, L, (int)num_groups, 0, cfg, true)) {  // one table holds every group anyway
+        if (depth_out) *depth_out = 0;
+        return (repro_status)groupby_dispatch(keys, values, n, dtype, L, num_groups, state, s);
+    }
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cap) != cudaSuccess || cap != cudaStreamCaptureStatusNone ||
+        (uintptr_t)keys % 16 || (uintptr_t)values % 16)
+        return (repro_status)groupby_dispatch(keys, values, n, dtype, L, num_groups, state, s);
+    // the probe: key range and coarse bucket counts, read back once
+    int cshift = 0;
+    while ((num_groups - 1) >> cshift >= kProbeBuckets) ++cshift;
+    const int nb = (int)(((num_groups - 1) >> cshift) + 1);
+    Scratch probe(sizeof(int) * (2 + (size_t)nb), s);
+    if (probe.err != cudaSuccess) return from_cuda(probe.err);
+    int* out = (int*)probe.p;
+    const int init[2] = {INT32_MAX, INT32_MIN};
+    cudaError_t e = cudaMemsetAsync(out + 2, 0, sizeof(int) * (size_t)nb, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(out, init, sizeof(init), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = launch_key_probe(keys, n, num_groups, cshift, nb, out, s);
+    int range[2] = {0, 0};
+    if (e == cudaSuccess) e = cudaMemcpyAsync(range, out, sizeof(range), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return from_cuda(e);
+    if (range[0] < 0 || (long long)range[1] >= num_groups)  // bad keys: the plain path flags them
+        return (repro_status)groupby_dispatch(keys, values, n, dtype, L, num_groups, state, s);
+    // depth from the groups the keys reach: none while one table holds them,
+    // else the partition passes and fan-out for that many groups
+    const long long Gk = (long long)range[1] + 1;
+    if (fused_supported(dtype, L, Gk, keys, values, true) && fused_plan_config(dtype, L, (int)Gk, 0, cfg, true)) {
+        Scratch scratch(fused_scratch_bytes(cfg, L, Gk, n), s);
+        if (scratch.err != cudaSuccess) return from_cuda(scratch.err);
+        if (depth_out) *depth_out = 0;
+        return from_cuda(launch_groupby_fused(keys, values, n, dtype, L, Gk, cfg, state, scratch.p, s, 0, false,
+                                              num_groups));
+    }
+    PartChoice pc;
+    if (partitioned_supported(dtype, L, Gk, n, keys, values) && partition_choose(dtype, L, Gk, pc)) {
+        Scratch scratch(partitioned_scratch_bytes(pc, dtype, L, Gk, n), s);
+        if (scratch.err != cudaSuccess) return from_cuda(scratch.err);
+        if (depth_out) *depth_out = pc.shift1 > pc.shift ? 2 : 1;
+        return from_cuda(launch_groupby_partitioned(keys, values, n, dtype, L, Gk, pc, state, scratch.p, s,
+                                                    num_groups));
+    }
+    return (repro_status)groupby_dispatch(keys, values, n, dtype, L, num_groups, state, s);
 }
 
 repro_status repro_groupby_sum_cols(const uint8_t* key1, const uint8_t* key2, int card2, const void* const* cols,

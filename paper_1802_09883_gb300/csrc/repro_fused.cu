@@ -256,9 +256,11 @@ __global__ void __launch_bounds__(32 * (NCW + 1), NCW == 8 ? 4 : (NCW == 16 ? 2 
 
 // state += sum of C partial tables (one record per group each), aligned to
 // the largest window.  Block = 32 groups x NW warps; warps split the partials.
+// G_hdr: the group count the state's header must show (the partials may
+// cover only its first G groups).
 template <int L>
 __global__ void __launch_bounds__(256) k_merge_partials(const unsigned char* __restrict__ parts, int C, int G,
-                                                        unsigned char* base, int dtype) {
+                                                        unsigned char* base, int dtype, long long G_hdr) {
     constexpr int NW = 8;
     constexpr size_t rec = 8 + 16 * L;
     StateView st{base, L, G};
@@ -270,7 +272,7 @@ __global__ void __launch_bounds__(256) k_merge_partials(const unsigned char* __r
     if (threadIdx.x == 0) {
         const repro_state_header* h = st.header();
         s_ok = h->magic == REPRO_STATE_MAGIC && h->dtype == (uint32_t)dtype && h->L == (uint32_t)L &&
-               h->num_groups == G;
+               h->num_groups == G_hdr;
         if (!s_ok) atomicOr(&st.header()->errors, REPRO_ERR_LAYOUT);
     }
     __syncthreads();
@@ -547,7 +549,8 @@ size_t fused_scratch_bytes(const FusedPlanConfig& cfg, int L, long long G, long 
 
 cudaError_t launch_groupby_fused(const int32_t* keys, const void* vals, long long n, int dtype, int L, long long G,
                                  const FusedPlanConfig& cfg, void* state, void* scratch, cudaStream_t s,
-                                 int max_ctas, bool square) {
+                                 int max_ctas, bool square, long long G_hdr) {
+    if (G_hdr <= 0) G_hdr = G;
     const DeviceInfo& di = device_info();
     if (!fused_config_fits(dtype, L, (int)G, 0, cfg, true)) return cudaErrorInvalidValue;
     FusedArgs a;
@@ -584,10 +587,10 @@ cudaError_t launch_groupby_fused(const int32_t* keys, const void* vals, long lon
     const int blocks = (int)((G + 31) / 32);
     prof_begin(PROF_MERGE, s);
     switch (L) {
-        case 1: k_merge_partials<1><<<blocks, 256, 0, s>>>(a.partials, ctas, (int)G, (unsigned char*)state, dtype); break;
-        case 2: k_merge_partials<2><<<blocks, 256, 0, s>>>(a.partials, ctas, (int)G, (unsigned char*)state, dtype); break;
-        case 3: k_merge_partials<3><<<blocks, 256, 0, s>>>(a.partials, ctas, (int)G, (unsigned char*)state, dtype); break;
-        default: k_merge_partials<4><<<blocks, 256, 0, s>>>(a.partials, ctas, (int)G, (unsigned char*)state, dtype); break;
+        case 1: k_merge_partials<1><<<blocks, 256, 0, s>>>(a.partials, ctas, (int)G, (unsigned char*)state, dtype, G_hdr); break;
+        case 2: k_merge_partials<2><<<blocks, 256, 0, s>>>(a.partials, ctas, (int)G, (unsigned char*)state, dtype, G_hdr); break;
+        case 3: k_merge_partials<3><<<blocks, 256, 0, s>>>(a.partials, ctas, (int)G, (unsigned char*)state, dtype, G_hdr); break;
+        default: k_merge_partials<4><<<blocks, 256, 0, s>>>(a.partials, ctas, (int)G, (unsigned char*)state, dtype, G_hdr); break;
     }
     prof_end(PROF_MERGE, s);
     count_launches(1);
@@ -601,10 +604,10 @@ cudaError_t launch_merge_partials(const void* parts, int C, long long G, void* s
     unsigned char* st = (unsigned char*)state;
     prof_begin(PROF_MERGE, s);
     switch (L) {
-        case 1: k_merge_partials<1><<<blocks, 256, 0, s>>>(p, C, (int)G, st, dtype); break;
-        case 2: k_merge_partials<2><<<blocks, 256, 0, s>>>(p, C, (int)G, st, dtype); break;
-        case 3: k_merge_partials<3><<<blocks, 256, 0, s>>>(p, C, (int)G, st, dtype); break;
-        default: k_merge_partials<4><<<blocks, 256, 0, s>>>(p, C, (int)G, st, dtype); break;
+        case 1: k_merge_partials<1><<<blocks, 256, 0, s>>>(p, C, (int)G, st, dtype, G); break;
+        case 2: k_merge_partials<2><<<blocks, 256, 0, s>>>(p, C, (int)G, st, dtype, G); break;
+        case 3: k_merge_partials<3><<<blocks, 256, 0, s>>>(p, C, (int)G, st, dtype, G); break;
+        default: k_merge_partials<4><<<blocks, 256, 0, s>>>(p, C, (int)G, st, dtype, G); break;
     }
     prof_end(PROF_MERGE, s);
     count_launches(1);

@@ -64,10 +64,11 @@ size_t fused_plan_smem(int dtype, int L, int G, const FusedPlanConfig& cfg);
 bool fused_supported(int dtype, int L, long long G, const void* keys, const void* vals, bool pad = false);
 size_t fused_scratch_bytes(const FusedPlanConfig& cfg, int L, long long G, long long n);
 // max_ctas > 0 caps the number of CTAs (and so the partial tables in scratch);
-// square: sum RN(x*x) instead of x.
+// square: sum RN(x*x) instead of x; G_hdr > 0: the state holds G_hdr >= G
+// groups and every key is below G (only its first G records are touched).
 cudaError_t launch_groupby_fused(const int32_t* keys, const void* vals, long long n, int dtype, int L, long long G,
                                  const FusedPlanConfig& cfg, void* state, void* scratch, cudaStream_t s,
-                                 int max_ctas = 0, bool square = false);
+                                 int max_ctas = 0, bool square = false, long long G_hdr = 0);
 
 // Large group counts: partition by key range, then the multi-task kernel
 // over the partitions (repro_partition.cu).  A choice fixes the partition
@@ -84,8 +85,17 @@ struct PartChoice {
 bool partition_choose(int dtype, int L, long long G, PartChoice& pc);
 bool partitioned_supported(int dtype, int L, long long G, long long n, const void* keys, const void* vals);
 size_t partitioned_scratch_bytes(const PartChoice& pc, int dtype, int L, long long G, long long n);
+// G_hdr > 0: the state holds G_hdr >= G groups and every key is below G.
 cudaError_t launch_groupby_partitioned(const int32_t* keys, const void* vals, long long n, int dtype, int L,
-                                       long long G, const PartChoice& pc, void* state, void* scratch, cudaStream_t s);
+                                       long long G, const PartChoice& pc, void* state, void* scratch, cudaStream_t s,
+                                       long long G_hdr = 0);
+
+// Key probe of the adaptive entry point: the smallest and largest key (over
+// all rows) and rows per coarse bucket key >> cshift (nb buckets), into
+// out = {min, max, counts[nb]} (the caller presets min / max and zeroes the
+// counts).  Keys outside [0, G) are not counted in the buckets.
+cudaError_t launch_key_probe(const int32_t* keys, long long n, long long G, int cshift, int nb, int* out,
+                             cudaStream_t s);
 
 // Several value columns over one key column in one pass (repro_cols.cu):
 // four columns (NV = 4), or one column and its square (NV = 2, square:

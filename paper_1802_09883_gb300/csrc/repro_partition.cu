@@ -650,7 +650,8 @@ __global__ void __launch_bounds__(1024) k_part_plan(const long long* __restrict_
                                                     size_t vsize, unsigned char* hdr, int L,
                                                     const int* win, int win_hint, const PartTask* __restrict__ tt,
                                                     int B, MTask* __restrict__ tasks, MItem* __restrict__ items,
-                                                    int* nitems, MergeBlk* __restrict__ blks, int* nblks) {
+                                                    int* nitems, MergeBlk* __restrict__ blks, int* nblks,
+                                                    long long G_hdr) {
     __shared__ long long s_it[1024], s_pt[1024], s_bk[1024];
     const size_t rec = 8 + 16 * (size_t)L;
     const int per = (pg.F + blockDim.x - 1) / blockDim.x;
@@ -702,7 +703,7 @@ __global__ void __launch_bounds__(1024) k_part_plan(const long long* __restrict_
         t.vals = static_cast<const unsigned char*>(ovals) + (size_t)pstart[p] * vsize;
         t.n = cnt;
         t.G = Gp;
-        t.G_hdr = Gt;
+        t.G_hdr = tt ? Gt : (int)G_hdr;  // one input: its state may hold more groups than its keys reach
         t.hdr = h;
         t.recs = h + sizeof(repro_state_header) + (size_t)j * pg.Gp * rec;
         t.win = win ? win + (size_t)p * pg.Gp : nullptr;
@@ -974,7 +975,8 @@ size_t partitioned_scratch_bytes(const PartChoice& pc, int dtype, int L, long lo
 
 cudaError_t launch_groupby_partitioned(const int32_t* keys, const void* vals, long long n, int dtype, int L,
                                        long long G, const PartChoice& pc, void* state, void* scratch,
-                                       cudaStream_t s) {
+                                       cudaStream_t s, long long G_hdr) {
+    if (G_hdr <= 0) G_hdr = G;
     PartPlan pp;
     if (!make_part_plan(pc, L, G, n, pp) || !fused_config_fits(dtype, L, pp.Gp, kMetaSmemBytes, pc.cfg))
         return cudaErrorInvalidValue;
@@ -1047,7 +1049,7 @@ cudaError_t launch_groupby_partitioned(const int32_t* keys, const void* vals, lo
     k_part_plan<<<1, 1024, 0, s>>>(pstart, pcount, pg, (int)G, pp.cfg.R, pp.tpi, okeys, ovals,
                                    dtype == REPRO_F64 ? 8 : 4, (unsigned char*)state, L, win, win_hint, nullptr, 0,
                                    (MTask*)(b + ly.tasks),
-                                   (MItem*)(b + ly.items), ints, (MergeBlk*)(b + ly.blks), ints + 1);
+                                   (MItem*)(b + ly.items), ints, (MergeBlk*)(b + ly.blks), ints + 1, G_hdr);
     count_launches(1);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     e = launch_multi(dtype, L, pp.cfg, pp.Gp, b + ly.tasks, b + ly.items, (int)pp.max_items, ints, ints + 2,
@@ -1221,7 +1223,7 @@ cudaError_t BatchPartition::launch(void* scratch, cudaStream_t s) const {
     k_part_plan<<<1, 1024, 0, s>>>(pstart, pcount, geo, 0, P.pc.cfg.R, P.tpi, okeys, ovals,
                                    P.dtype == REPRO_F64 ? 8 : 4, nullptr, P.L, nullptr, 0,
                                    (const PartTask*)(b + P.ly.ptask), P.B, (MTask*)(b + P.ly.tasks),
-                                   (MItem*)(b + P.ly.items), ints, (MergeBlk*)(b + P.ly.blks), ints + 1);
+                                   (MItem*)(b + P.ly.items), ints, (MergeBlk*)(b + P.ly.blks), ints + 1, 0);
     count_launches(1);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     e = launch_multi(P.dtype, P.L, P.pc.cfg, P.Gp, b + P.ly.tasks, b + P.ly.items, (int)P.max_items, ints, ints + 2,
@@ -1231,6 +1233,59 @@ cudaError_t BatchPartition::launch(void* scratch, cudaStream_t s) const {
         e = launch_merge_items(P.L, P.dtype, b + P.ly.tasks, b + P.ly.blks, (int)P.max_blks, ints + 1, b + P.ly.parts,
                                s);
     return e;
+}
+
+// ------------------------------------------------------------------
+// Key probe (the adaptive entry point's look at the data before it picks a
+// depth): one read of the keys with 16-byte loads, the smallest and largest
+// key, and rows per coarse bucket key >> cshift of the valid keys.
+
+__global__ void __launch_bounds__(512) k_key_probe(const int32_t* __restrict__ keys, long long n, long long G,
+                                                   int cshift, int nb, int* __restrict__ out) {
+    extern __shared__ int s_cnt[];
+    for (int b = threadIdx.x; b < nb; b += blockDim.x) s_cnt[b] = 0;
+    __syncthreads();
+    int kmin = 0x7fffffff, kmax = (int)0x80000000;
+    auto one = [&](int k) {
+        kmin = min(kmin, k);
+        kmax = max(kmax, k);
+        if ((unsigned)k < (unsigned long long)G) atomicAdd(&s_cnt[(unsigned)k >> cshift], 1);
+    };
+    const long long n4 = n & ~3ll;
+    const long long stride = 4ll * gridDim.x * blockDim.x;
+    for (long long i = 4ll * (blockIdx.x * (long long)blockDim.x + threadIdx.x); i < n4; i += stride) {
+        const int4 k = *reinterpret_cast<const int4*>(keys + i);
+        one(k.x);
+        one(k.y);
+        one(k.z);
+        one(k.w);
+    }
+    if (blockIdx.x == 0)
+        for (long long i = n4 + threadIdx.x; i < n; i += blockDim.x) one(keys[i]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        kmin = min(kmin, __shfl_xor_sync(0xffffffffu, kmin, o));
+        kmax = max(kmax, __shfl_xor_sync(0xffffffffu, kmax, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicMin(&out[0], kmin);
+        atomicMax(&out[1], kmax);
+    }
+    __syncthreads();
+    for (int b = threadIdx.x; b < nb; b += blockDim.x)
+        if (s_cnt[b]) atomicAdd(&out[2 + b], s_cnt[b]);
+}
+
+cudaError_t launch_key_probe(const int32_t* keys, long long n, long long G, int cshift, int nb, int* out,
+                             cudaStream_t s) {
+    const size_t smem = (size_t)nb * 4;
+    cudaError_t e = cudaFuncSetAttribute(k_key_probe, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const long long work = (n / 4 + 511) / 512;
+    const int grid = (int)std::max(1ll, std::min<long long>(work, (long long)device_info().sms * 4));
+    k_key_probe<<<grid, 512, smem, s>>>(keys, n, G, cshift, nb, out);
+    count_launches(1);
+    return cudaGetLastError();
 }
 
 }  // namespace rp
