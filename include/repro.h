@@ -141,8 +141,11 @@ repro_status repro_groupby_sum(const int32_t* keys, const void* values, int64_t 
  * range, the stream is synchronised and the depth is picked for the groups
  * the keys reach, max(key) + 1: no partitioning while one table holds them
  * (a single pass over records [0, max(key)]), else one or two partition
- * passes and a fan-out sized for that many groups (heavy partitions are
- * then split over several CTAs as in repro_groupby_sum).  Same arguments
+ * passes and a fan-out sized for that many groups.  The probe also counts
+ * rows per coarse key bucket; when the fullest bucket holds more than four
+ * times the mean (skewed keys), the partitions are cut into more, shorter
+ * work items (8 per CTA instead of 2), so that a hot partition is spread over
+ * many CTAs; a tuned choice (repro_tune_groupby) takes precedence.  Same arguments
  * and the same result bits as repro_groupby_sum.  *depth_out (may be NULL)
  * receives the partition passes taken: 0, 1 or 2, or -1 when the call went
  * the plain way (keys or values not 16-byte aligned, bad keys, or a stream

@@ -151,27 +151,31 @@ struct SAddr {
     uint32_t lo, hi;      // table words [(g LP + j) C + copy], LP = L + 2 levels per group
 };
 
-// Value bit-words of four consecutive rows: (hi, lo) per row for double,
-// the single word for float.
+// Value bit-words of two consecutive rows: (hi, lo) per row for double, the
+// single word for float.
 template <typename T>
-struct QuadWords;
+struct PairWords;
 template <>
-struct QuadWords<double> {
-    static __device__ __forceinline__ void load_ptr(const double* v, uint32_t hi[4], uint32_t lo[4]) {
-        const uint4 p = reinterpret_cast<const uint4*>(v)[0], q = reinterpret_cast<const uint4*>(v)[1];
-        lo[0] = p.x; hi[0] = p.y; lo[1] = p.z; hi[1] = p.w;
-        lo[2] = q.x; hi[2] = q.y; lo[3] = q.z; hi[3] = q.w;
-    }
-};
-template <>
-struct QuadWords<float> {
-    static __device__ __forceinline__ void load_ptr(const float* v, uint32_t hi[4], uint32_t lo[4]) {
+struct PairWords<double> {
+    static __device__ __forceinline__ void load(const double* v, uint32_t& h0, uint32_t& l0, uint32_t& h1,
+                                                uint32_t& l1) {
         const uint4 p = *reinterpret_cast<const uint4*>(v);
-        hi[0] = p.x; hi[1] = p.y; hi[2] = p.z; hi[3] = p.w;
-        lo[0] = lo[1] = lo[2] = lo[3] = 0u;
+        l0 = p.x;
+        h0 = p.y;
+        l1 = p.z;
+        h1 = p.w;
     }
 };
-
+template <>
+struct PairWords<float> {
+    static __device__ __forceinline__ void load(const float* v, uint32_t& h0, uint32_t& l0, uint32_t& h1,
+                                                uint32_t& l1) {
+        const uint2 p = *reinterpret_cast<const uint2*>(v);
+        h0 = p.x;
+        h1 = p.y;
+        l0 = l1 = 0u;
+    }
+};
 
 // The two halves of adding digit (lo, hi) to a table word pair: a shared
 // atomic on the LO word returns its old value; hi plus the carry out of
@@ -232,7 +236,12 @@ struct Expo<float> {
 // counter at scnt_addr) for consume_row after the tile.  The digits of such
 // rows are computed too, from whatever their words hold, and added to the
 // spare group, which keeps the four rows' work straight-line.
-template <typename T, int L, int CC>
+// The four rows are r0, r0 + 1, r0 + H and r0 + H + 1.  H = 2 takes four
+// consecutive rows; H = 64 with r0 = (128-row block) + 2 lane makes each of
+// a warp's shared loads of keys and values one contiguous run (no bank
+// conflicts: 16-byte loads at a 32-byte lane stride took two wavefronts per
+// 128 bytes).
+template <typename T, int L, int CC, int H>
 __device__ __forceinline__ void consume_quad_fast(const SAddr& sa, const int32_t* tk, const T* tv, const int* sK,
                                                   int r0, int G, int spare, int copy, unsigned short* slist,
                                                   uint32_t scnt_addr) {
@@ -240,10 +249,24 @@ __device__ __forceinline__ void consume_quad_fast(const SAddr& sa, const int32_t
     // plain loads (the staged tile and the windows do not change during
     // this phase), so that the compiler may start the next row's loads
     // while this row's atomics are in flight
-    const int4 k4 = *reinterpret_cast<const int4*>(tk + r0);
-    const int gq[4] = {k4.x, k4.y, k4.z, k4.w};
+    int gq[4];
+    if (H == 2) {
+        const int4 k4 = *reinterpret_cast<const int4*>(tk + r0);
+        gq[0] = k4.x;
+        gq[1] = k4.y;
+        gq[2] = k4.z;
+        gq[3] = k4.w;
+    } else {
+        const int2 ka = *reinterpret_cast<const int2*>(tk + r0);
+        const int2 kc = *reinterpret_cast<const int2*>(tk + r0 + H);
+        gq[0] = ka.x;
+        gq[1] = ka.y;
+        gq[2] = kc.x;
+        gq[3] = kc.y;
+    }
     uint32_t vhi[4], vlo[4];
-    QuadWords<T>::load_ptr(tv + r0, vhi, vlo);
+    PairWords<T>::load(tv + r0, vhi[0], vlo[0], vhi[1], vlo[1]);
+    PairWords<T>::load(tv + r0 + H, vhi[2], vlo[2], vhi[3], vlo[3]);
     const uint32_t hi_off = sa.hi - sa.lo;
     unsigned okm = 0;  // bit q: row q added its digits
 #pragma unroll
@@ -278,7 +301,7 @@ __device__ __forceinline__ void consume_quad_fast(const SAddr& sa, const int32_t
             if (!(okm & (1u << q)) && !((unsigned)gq[q] < (unsigned)G && Lean<T>::is_zero(vhi[q], vlo[q]))) {
                 uint32_t idx;
                 asm volatile("atom.shared.add.u32 %0, [%1], 1;" : "=r"(idx) : "r"(scnt_addr) : "memory");
-                slist[idx] = (unsigned short)(r0 + q);
+                slist[idx] = (unsigned short)(r0 + (q & 1) + (q >> 1) * H);
             }
     }
 }

@@ -7,8 +7,10 @@
 
 #include <algorithm>
 #include <cstdint>
+#include <cstdlib>
 #include <map>
 #include <mutex>
+#include <vector>
 #include <tuple>
 
 #include "repro.h"
@@ -132,11 +134,26 @@ using namespace rp;
 
 namespace rp {
 
-// Coarse buckets of the adaptive entry point's key probe (at most).
+// Coarse buckets of the adaptive entry point's key probe (at most), and its
+// skew rule: an input whose fullest bucket holds more than kSkewRatio times
+// the mean is aggregated with kSkewItemsPerCta work items per CTA (the
+// partitioned path's default is 2; the tuner picked 4-8 on Zipf keys).
 constexpr long long kProbeBuckets = 4096;
+constexpr double kSkewRatio = 4.0;
+constexpr int kSkewItemsPerCta = 8;
 
-// Rows per staged chunk of repro_groupby_sum_host (two chunks in flight).
+// Rows per staged chunk of repro_groupby_sum_host (two chunks in flight);
+// REPRO_HOST_CHUNK_ROWS (2^20 to 2^27) overrides it.
 constexpr long long kHostChunkRows = 1ll << 24;
+
+static long long host_chunk_rows() {
+    static const long long v = [] {
+        const char* e = getenv("REPRO_HOST_CHUNK_ROWS");
+        const long long x = e ? atoll(e) : 0;
+        return x >= (1ll << 20) && x <= (1ll << 27) ? (x & ~255ll) : kHostChunkRows;
+    }();
+    return v;
+}
 
 // A library stream per device for host-to-device copies.
 static cudaStream_t copy_stream(cudaError_t& err) {
@@ -227,15 +244,22 @@ repro_status repro_groupby_sum_adaptive(const int32_t* keys, const void* values,
     cudaError_t e = cudaMemsetAsync(out + 2, 0, sizeof(int) * (size_t)nb, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(out, init, sizeof(init), cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = launch_key_probe(keys, n, num_groups, cshift, nb, out, s);
-    int range[2] = {0, 0};
-    if (e == cudaSuccess) e = cudaMemcpyAsync(range, out, sizeof(range), cudaMemcpyDeviceToHost, s);
+    std::vector<int> probe_h(2 + (size_t)nb);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(probe_h.data(), out, sizeof(int) * probe_h.size(), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return from_cuda(e);
-    if (range[0] < 0 || (long long)range[1] >= num_groups)  // bad keys: the plain path flags them
+    if (probe_h[0] < 0 || (long long)probe_h[1] >= num_groups)  // bad keys: the plain path flags them
         return (repro_status)groupby_dispatch(keys, values, n, dtype, L, num_groups, state, s);
     // depth from the groups the keys reach: none while one table holds them,
     // else the partition passes and fan-out for that many groups
-    const long long Gk = (long long)range[1] + 1;
+    const long long Gk = (long long)probe_h[1] + 1;
+    // skew: the fullest coarse bucket against the mean over the buckets the
+    // keys reach; a skewed input gets more, shorter work items per CTA so
+    // that a hot partition is spread over many CTAs
+    const int nbk = (int)(((Gk - 1) >> cshift) + 1);
+    int hot = 0;
+    for (int b = 0; b < nbk; ++b) hot = std::max(hot, probe_h[2 + b]);
+    const bool skewed = (double)hot * nbk > kSkewRatio * (double)n;
     if (fused_supported(dtype, L, Gk, keys, values, true) && fused_plan_config(dtype, L, (int)Gk, 0, cfg, true)) {
         Scratch scratch(fused_scratch_bytes(cfg, L, Gk, n), s);
         if (scratch.err != cudaSuccess) return from_cuda(scratch.err);
@@ -245,6 +269,7 @@ repro_status repro_groupby_sum_adaptive(const int32_t* keys, const void* values,
     }
     PartChoice pc;
     if (partitioned_supported(dtype, L, Gk, n, keys, values) && partition_choose(dtype, L, Gk, pc)) {
+        if (skewed && pc.ipc == 0) pc.ipc = kSkewItemsPerCta;  // a measured choice stands
         Scratch scratch(partitioned_scratch_bytes(pc, dtype, L, Gk, n), s);
         if (scratch.err != cudaSuccess) return from_cuda(scratch.err);
         if (depth_out) *depth_out = pc.shift1 > pc.shift ? 2 : 1;
@@ -331,7 +356,7 @@ repro_status repro_groupby_sum_host(const int32_t* keys, const void* values, int
     }
     cudaStream_t s = (cudaStream_t)stream;
     const size_t vs = dtype == REPRO_F64 ? 8 : 4;
-    const long long chunk = std::min<long long>(n, kHostChunkRows);
+    const long long chunk = std::min<long long>(n, host_chunk_rows());
     cudaError_t e = cudaSuccess;
     cudaStream_t cs = copy_stream(e);
     if (!cs) return from_cuda(e);

@@ -337,7 +337,7 @@ __global__ void __maxnreg__(96) k_fused_multi(MultiArgs a, int dtype) {
         sa.keys = smem_addr(tk_s);
         sa.vals = smem_addr(tv_s);
         for (int r = 4 * ctid; r < sm.rows_tma; r += 4 * NC)
-            consume_quad_fast<T, L, CC>(sa, tk_s, tv_s, sK, r, G, a.Gcap, copy, slist, smem_addr(scnt));
+            consume_quad_fast<T, L, CC, 2>(sa, tk_s, tv_s, sK, r, G, a.Gcap, copy, slist, smem_addr(scnt));
         for (int r = sm.rows_tma + ctid; r < sm.rows; r += NC)
             consume_row<T, L>(gk[r], gv[r], r, G, tab, copy, sK, sKp, sF, dlist, rlist, cnt, bad_key);
         named_bar_sync(1, NC);

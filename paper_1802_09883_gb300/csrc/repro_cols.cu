@@ -189,7 +189,7 @@ __global__ void __launch_bounds__(32 * (NCW + 1)) k_fused_cols(ColsArgs a) {
             sa.keys = smem_addr(tk);
             sa.vals = smem_addr(tv);
             for (int r = 4 * ctid; r < rows; r += 4 * NC)
-                consume_quad_fast<T, L, CC>(sa, tk, tv, sK, r, G, G, copy, slist, smem_addr(scnt));
+                consume_quad_fast<T, L, CC, 2>(sa, tk, tv, sK, r, G, G, copy, slist, smem_addr(scnt));
         } else {
             for (int r = ctid; r < rows; r += NC)
                 consume_row<T, L>(tk[r], tv[r], r, G, tab, copy, sK, sKp, sF, dlist, rlist, cnt, bad_key);

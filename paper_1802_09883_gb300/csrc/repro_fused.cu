@@ -171,13 +171,18 @@ __global__ void __launch_bounds__(32 * (NCW + 1), NCW == 8 ? 4 : (NCW == 16 ? 2 
             sa.vals = smem_addr(tv);
             if (SQ) {  // this thread's quads, squared where they lie (read only after the barrier by others)
                 T* w = svals + (size_t)s * R;
-                for (int r = 4 * ctid; r < R; r += 4 * NC)
+                for (int b = 128 * (ctid >> 5) + 2 * (ctid & 31); b < R; b += 128 * NCW)
 #pragma unroll
-                    for (int q = 0; q < 4; ++q) w[r + q] = w[r + q] * w[r + q];
+                    for (int q = 0; q < 4; ++q) {
+                        const int r = b + (q & 1) + (q >> 1) * 64;
+                        w[r] = w[r] * w[r];
+                    }
                 asm volatile("" ::: "memory");  // the stores stay ahead of the quads' shared loads
             }
-            for (int r = 4 * ctid; r < R; r += 4 * NC)
-                consume_quad_fast<T, L, CC>(sa, tk, tv, sK, r, G, G, copy, slist, smem_addr(scnt));
+            // each warp takes 128-row blocks (R is a multiple of 128 NCW),
+            // each lane rows 2 lane + {0, 1, 64, 65} of a block
+            for (int b = 128 * (ctid >> 5) + 2 * (ctid & 31); b < R; b += 128 * NCW)
+                consume_quad_fast<T, L, CC, 64>(sa, tk, tv, sK, b, G, G, copy, slist, smem_addr(scnt));
         } else {
             *abort_flag = 1;  // written before the barrier, read after it: uniform
             atomicOr(a.errors, REPRO_ERR_TIMEOUT);
