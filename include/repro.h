@@ -124,7 +124,12 @@ repro_status repro_state_init(void* state, repro_dtype dtype, int L, int64_t num
  * (Algorithm 2, transform; constant extractor so ties round to even);
  * exact accumulation (the carry-bit counts of Algorithm 2 become wide
  * integer bins); per-call partial states merged into `state` with
- * operator+=(repro) (Sec. V-B, Algorithm 4).
+ * operator+=(repro) (Sec. V-B, Algorithm 4).  Group counts beyond one
+ * shared-memory table are partitioned first (Algorithm 4's
+ * ParallelPartition, one or two passes); when the keys are skewed (the
+ * fullest partition above four times the mean, seen on the device) and
+ * there are more than 64 partitions, partitions are cut into shorter work
+ * items (8 per CTA instead of 2) unless a tuned choice says otherwise.
  */
 repro_status repro_groupby_sum(const int32_t* keys, const void* values, int64_t n,
                                repro_dtype dtype, int L, int64_t num_groups, void* state,
@@ -136,22 +141,24 @@ repro_status repro_groupby_sum(const int32_t* keys, const void* values, int64_t 
  * enough levels that the last one aggregates in cache, no more, and it
  * proposes choosing them adaptively, from the groups actually met, instead
  * of offline (Sec. V-C, "Tuning Buffer Size and Partitioning Depth").  Here
- * num_groups only bounds the keys; when it exceeds one shared-memory table,
- * a probe kernel first reads the keys once (4 bytes per row) for their
- * range, the stream is synchronised and the depth is picked for the groups
- * the keys reach, max(key) + 1: no partitioning while one table holds them
- * (a single pass over records [0, max(key)]), else one or two partition
- * passes and a fan-out sized for that many groups.  The probe also counts
- * rows per coarse key bucket; when the fullest bucket holds more than four
- * times the mean (skewed keys), the partitions are cut into more, shorter
- * work items (8 per CTA instead of 2), so that a hot partition is spread over
- * many CTAs; a tuned choice (repro_tune_groupby) takes precedence.  Same arguments
- * and the same result bits as repro_groupby_sum.  *depth_out (may be NULL)
- * receives the partition passes taken: 0, 1 or 2, or -1 when the call went
- * the plain way (keys or values not 16-byte aligned, bad keys, or a stream
- * under capture: then no probe runs and the depth is the built-in rule's).
+ * num_groups only bounds the keys.  When it exceeds one shared-memory table,
+ * the partitioned path planned for num_groups starts, and its first
+ * histogram pass (which reads every key anyway) also takes the keys' range;
+ * the stream is synchronised once, and if the groups the keys reach,
+ * max(key) + 1, call for another plan -- no partitioning while one table
+ * holds them (a single pass over records [0, max(key)]), else one or two
+ * partition passes sized for that many groups -- the call stops there and
+ * runs that plan instead; otherwise it goes on.  In both plans skewed keys
+ * (the fullest partition above four times the mean, seen on the device)
+ * cut their partitions into shorter work items when there are more than 64
+ * partitions and no tuned choice, as in repro_groupby_sum.  Same
+ * arguments and the same result bits as repro_groupby_sum.  *depth_out (may
+ * be NULL) receives the partition passes taken: 0, 1 or 2, or -1 when the
+ * call went the plain way without looking at the keys (keys or values not
+ * 16-byte aligned, a stream under capture, or the two-pass path).  Keys
+ * outside [0, num_groups) keep the plan for num_groups, which flags them.
  * Unlike repro_groupby_sum this call synchronises `stream` once when it
- * probes.
+ * reads the range.
  */
 repro_status repro_groupby_sum_adaptive(const int32_t* keys, const void* values, int64_t n, repro_dtype dtype, int L,
                                         int64_t num_groups, void* state, int* depth_out, void* stream);

@@ -134,14 +134,6 @@ using namespace rp;
 
 namespace rp {
 
-// Coarse buckets of the adaptive entry point's key probe (at most), and its
-// skew rule: an input whose fullest bucket holds more than kSkewRatio times
-// the mean is aggregated with kSkewItemsPerCta work items per CTA (the
-// partitioned path's default is 2; the tuner picked 4-8 on Zipf keys).
-constexpr long long kProbeBuckets = 4096;
-constexpr double kSkewRatio = 4.0;
-constexpr int kSkewItemsPerCta = 8;
-
 // Rows per staged chunk of repro_groupby_sum_host (two chunks in flight);
 // REPRO_HOST_CHUNK_ROWS (2^20 to 2^27) overrides it.
 constexpr long long kHostChunkRows = 1ll << 24;
@@ -230,53 +222,61 @@ repro_status repro_groupby_sum_adaptive(const int32_t* keys, const void* values,
         return (repro_status)groupby_dispatch(keys, values, n, dtype, L, num_groups, state, s);
     }
     cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    PartChoice pc;
     if (cudaStreamIsCapturing(s, &cap) != cudaSuccess || cap != cudaStreamCaptureStatusNone ||
-        (uintptr_t)keys % 16 || (uintptr_t)values % 16)
+        !partitioned_supported(dtype, L, num_groups, n, keys, values) ||
+        !partition_choose(dtype, L, num_groups, pc))
         return (repro_status)groupby_dispatch(keys, values, n, dtype, L, num_groups, state, s);
-    // the probe: key range and coarse bucket counts, read back once
-    int cshift = 0;
-    while ((num_groups - 1) >> cshift >= kProbeBuckets) ++cshift;
-    const int nb = (int)(((num_groups - 1) >> cshift) + 1);
-    Scratch probe(sizeof(int) * (2 + (size_t)nb), s);
-    if (probe.err != cudaSuccess) return from_cuda(probe.err);
-    int* out = (int*)probe.p;
+    // the partitioned path planned for num_groups reads the key range in its
+    // first histogram; it goes on when the groups the keys reach, max + 1,
+    // would take the same plan, else it stops there and the call is planned
+    // again for those groups
+    Scratch rng(2 * sizeof(int), s);
+    if (rng.err != cudaSuccess) return from_cuda(rng.err);
     const int init[2] = {INT32_MAX, INT32_MIN};
-    cudaError_t e = cudaMemsetAsync(out + 2, 0, sizeof(int) * (size_t)nb, s);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(out, init, sizeof(init), cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess) e = launch_key_probe(keys, n, num_groups, cshift, nb, out, s);
-    std::vector<int> probe_h(2 + (size_t)nb);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(probe_h.data(), out, sizeof(int) * probe_h.size(), cudaMemcpyDeviceToHost, s);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaError_t e = cudaMemcpyAsync(rng.p, init, sizeof(init), cudaMemcpyHostToDevice, s);
     if (e != cudaSuccess) return from_cuda(e);
-    if (probe_h[0] < 0 || (long long)probe_h[1] >= num_groups)  // bad keys: the plain path flags them
-        return (repro_status)groupby_dispatch(keys, values, n, dtype, L, num_groups, state, s);
-    // depth from the groups the keys reach: none while one table holds them,
-    // else the partition passes and fan-out for that many groups
-    const long long Gk = (long long)probe_h[1] + 1;
-    // skew: the fullest coarse bucket against the mean over the buckets the
-    // keys reach; a skewed input gets more, shorter work items per CTA so
-    // that a hot partition is spread over many CTAs
-    const int nbk = (int)(((Gk - 1) >> cshift) + 1);
-    int hot = 0;
-    for (int b = 0; b < nbk; ++b) hot = std::max(hot, probe_h[2 + b]);
-    const bool skewed = (double)hot * nbk > kSkewRatio * (double)n;
-    if (fused_supported(dtype, L, Gk, keys, values, true) && fused_plan_config(dtype, L, (int)Gk, 0, cfg, true)) {
+    long long Gk = num_groups;
+    bool single = false;
+    PartChoice pk;
+    PartProbe probe;
+    probe.dev = (int*)rng.p;
+    probe.keep = [&](int kmin, int kmax) {
+        if (kmin < 0 || (long long)kmax >= num_groups) return true;  // bad keys: this path flags them
+        Gk = (long long)kmax + 1;
+        FusedPlanConfig c;
+        if (fused_supported(dtype, L, Gk, keys, values, true) && fused_plan_config(dtype, L, (int)Gk, 0, c, true)) {
+            single = true;
+            return false;
+        }
+        if (!partition_choose(dtype, L, Gk, pk)) return true;
+        return pk.shift == pc.shift && (pk.shift1 > pk.shift) == (pc.shift1 > pc.shift);
+    };
+    {
+        Scratch scratch(partitioned_scratch_bytes(pc, dtype, L, num_groups, n), s);
+        if (scratch.err != cudaSuccess) return from_cuda(scratch.err);
+        e = launch_groupby_partitioned(keys, values, n, dtype, L, num_groups, pc, state, scratch.p, s, 0, &probe);
+        if (e != cudaSuccess) return from_cuda(e);
+        if (!probe.abandoned) {
+            if (depth_out) *depth_out = pc.shift1 > pc.shift ? 2 : 1;
+            return REPRO_OK;
+        }
+    }
+    // the keys reach Gk < num_groups groups: none, one or two passes for Gk
+    // (records [0, Gk) of the state; the header keeps num_groups)
+    if (single) {
+        if (!fused_plan_config(dtype, L, (int)Gk, 0, cfg, true))  // not expected: the probe just saw it fit
+            return (repro_status)groupby_dispatch(keys, values, n, dtype, L, num_groups, state, s);
         Scratch scratch(fused_scratch_bytes(cfg, L, Gk, n), s);
         if (scratch.err != cudaSuccess) return from_cuda(scratch.err);
         if (depth_out) *depth_out = 0;
         return from_cuda(launch_groupby_fused(keys, values, n, dtype, L, Gk, cfg, state, scratch.p, s, 0, false,
                                               num_groups));
     }
-    PartChoice pc;
-    if (partitioned_supported(dtype, L, Gk, n, keys, values) && partition_choose(dtype, L, Gk, pc)) {
-        if (skewed && pc.ipc == 0) pc.ipc = kSkewItemsPerCta;  // a measured choice stands
-        Scratch scratch(partitioned_scratch_bytes(pc, dtype, L, Gk, n), s);
-        if (scratch.err != cudaSuccess) return from_cuda(scratch.err);
-        if (depth_out) *depth_out = pc.shift1 > pc.shift ? 2 : 1;
-        return from_cuda(launch_groupby_partitioned(keys, values, n, dtype, L, Gk, pc, state, scratch.p, s,
-                                                    num_groups));
-    }
-    return (repro_status)groupby_dispatch(keys, values, n, dtype, L, num_groups, state, s);
+    Scratch scratch(partitioned_scratch_bytes(pk, dtype, L, Gk, n), s);
+    if (scratch.err != cudaSuccess) return from_cuda(scratch.err);
+    if (depth_out) *depth_out = pk.shift1 > pk.shift ? 2 : 1;
+    return from_cuda(launch_groupby_partitioned(keys, values, n, dtype, L, Gk, pk, state, scratch.p, s, num_groups));
 }
 
 repro_status repro_groupby_sum_cols(const uint8_t* key1, const uint8_t* key2, int card2, const void* const* cols,

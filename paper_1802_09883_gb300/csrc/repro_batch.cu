@@ -336,7 +336,12 @@ __global__ void __maxnreg__(96) k_fused_multi(MultiArgs a, int dtype) {
         const T* gv = static_cast<const T*>(sm.vals);
         sa.keys = smem_addr(tk_s);
         sa.vals = smem_addr(tv_s);
-        for (int r = 4 * ctid; r < sm.rows_tma; r += 4 * NC)
+        // whole 128-row blocks with a warp's loads contiguous (lane rows
+        // 2 lane + {0, 1, 64, 65}), then the item's last quads
+        const int full = sm.rows_tma & ~127;
+        for (int b = 128 * (ctid >> 5) + 2 * (ctid & 31); b < full; b += 128 * NCW)
+            consume_quad_fast<T, L, CC, 64>(sa, tk_s, tv_s, sK, b, G, a.Gcap, copy, slist, smem_addr(scnt));
+        for (int r = full + 4 * ctid; r < sm.rows_tma; r += 4 * NC)
             consume_quad_fast<T, L, CC, 2>(sa, tk_s, tv_s, sK, r, G, a.Gcap, copy, slist, smem_addr(scnt));
         for (int r = sm.rows_tma + ctid; r < sm.rows; r += NC)
             consume_row<T, L>(gk[r], gv[r], r, G, tab, copy, sK, sKp, sF, dlist, rlist, cnt, bad_key);

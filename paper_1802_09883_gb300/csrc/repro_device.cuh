@@ -242,13 +242,16 @@ struct Signed<double> {
             "subc.u32 %1, b, %4;\n\t}"
             : "=r"(sl), "=r"(sh)
             : "r"(vlo), "r"(mh), "r"(S));
-        // X = significand * 2^s, s = E + 79 - 40 kb in [27, 66]: shifted by 5
-        // first (the signed significand still fits 64 bits), then by
-        // s - 5 in [22, 61] = r within a word and q = 0 or 1 whole words
+        // X = significand * 2^s, s = E + 79 - 40 kb in [27, 66], has at least
+        // 27 zero bits at the bottom; the words hold X' = X / 2^8 (shift
+        // s - 8 in [19, 58]: by 5 first -- the signed significand still fits
+        // 64 bits -- then by s - 13 in [14, 53] = r within a word and q = 0
+        // or 1 whole words), so that X's 40-bit field [40, 80) is word 1
+        // plus the low byte of word 2
         const uint32_t sl5 = sl << 5, sh5 = __funnelshift_l(sl, sh, 5);
-        const int s5 = t + 22 - 40 * kb;
-        const int r = s5 & 31;
-        const bool q = s5 >= 32;
+        const int s13 = t + 14 - 40 * kb;
+        const int r = s13 & 31;
+        const bool q = s13 >= 32;
         const uint32_t v0 = sl5 << r;
         const uint32_t v1 = __funnelshift_l(sl5, sh5, r);
         const uint32_t v2 = __funnelshift_l(sh5, S, r);
@@ -256,25 +259,24 @@ struct Signed<double> {
         const uint32_t w1 = q ? v0 : v1;
         const uint32_t w2 = q ? v1 : v2;
         const uint32_t w3 = q ? v2 : S;
-        // 40-bit pieces: x0, x1 unsigned fields, x2 the signed part above
-        const uint32_t x0l = w0, x0h = w1 & 0xffu;
-        const uint32_t x1l = __funnelshift_r(w1, w2, 8), x1h = (w2 >> 8) & 0xffu;
-        const uint32_t x2l = __funnelshift_r(w2, w3, 16);
-        const int x2h = (int)w3 >> 16;
-        // carries at bits 40 and 80: [x + (2^39 - 1) + tie bit >= 2^40], the
-        // tie bit the parity above (bit 40) or, at bit 80, the parity of x2
-        // or any bit of x0; the low word's carry into the high word is
-        // [low word + tie bit > 0], folded into one add with carry-out
-        const uint32_t s1 = x1l & 1u;
-        const uint32_t z2 = x1l | x0l | x0h | (x2l & 1u);
-        const uint32_t c1 = (x0h + 0x7fu + (uint32_t)(((unsigned long long)(x0l | s1) + 0xffffffffull) >> 32)) >> 8;
+        // fields of X: x0 = w0 2^8 (bits [0, 40)), x1 = w1 + 2^32 (w2 & 0xff),
+        // x2 = (w3:w2) >> 8 (signed)
+        const uint32_t x1h = w2 & 0xffu;
+        const uint32_t x2l = __funnelshift_r(w2, w3, 8);
+        const int x2h = (int)w3 >> 8;
+        // carries at bits 40 and 80, round to nearest even: at 40,
+        // [x0 + 2^39 - 1 + (x1 & 1) >= 2^40] = [w0 + (w1 & 1) > 2^31] (x0's
+        // low byte is zero); at 80, [x1 + 2^39 - 1 + tie >= 2^40] with tie =
+        // [x0 != 0] | (x2 & 1), x1's low word folded into the carry-in
+        const uint32_t c1 = (uint32_t)(((unsigned long long)w0 + (w1 & 1u) + 0x7fffffffull) >> 32);
+        const uint32_t z2 = w1 | w0 | (w2 & 0x100u);
         const uint32_t c2 = (x1h + 0x7fu + (uint32_t)(((unsigned long long)z2 + 0xffffffffull) >> 32)) >> 8;
         lo[0] = x2l + c2;
         hi[0] = x2h + (int)(lo[0] < c2);
-        lo[1] = x1l + c1;
+        lo[1] = w1 + c1;
         hi[1] = (int)x1h + (int)(lo[1] < c1) - 256 * (int)c2;
-        lo[2] = x0l;
-        hi[2] = (int)x0h - 256 * (int)c1;
+        lo[2] = w0 << 8;
+        hi[2] = (int)(w0 >> 24) - 256 * (int)c1;
     }
 };
 

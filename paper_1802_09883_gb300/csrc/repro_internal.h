@@ -6,6 +6,7 @@
 
 #include <cstddef>
 #include <cstdint>
+#include <functional>
 #include <vector>
 
 namespace rp {
@@ -85,17 +86,24 @@ struct PartChoice {
 bool partition_choose(int dtype, int L, long long G, PartChoice& pc);
 bool partitioned_supported(int dtype, int L, long long G, long long n, const void* keys, const void* vals);
 size_t partitioned_scratch_bytes(const PartChoice& pc, int dtype, int L, long long G, long long n);
+// The key range read by the first partition pass's histogram, for a caller
+// that may drop the call when the keys reach far fewer groups than planned
+// for: dev points to {min, max} (preset to {INT32_MAX, INT32_MIN}); after the
+// histogram the stream is synchronised and keep(min, max) decides; when it
+// returns false the call returns at once with abandoned set (nothing has been
+// written to the state: only keys outside [0, G) would have flagged it, and
+// keep must return true for those).
+struct PartProbe {
+    int* dev = nullptr;
+    std::function<bool(int, int)> keep;
+    bool abandoned = false;
+};
+
 // G_hdr > 0: the state holds G_hdr >= G groups and every key is below G.
 cudaError_t launch_groupby_partitioned(const int32_t* keys, const void* vals, long long n, int dtype, int L,
                                        long long G, const PartChoice& pc, void* state, void* scratch, cudaStream_t s,
-                                       long long G_hdr = 0);
+                                       long long G_hdr = 0, PartProbe* probe = nullptr);
 
-// Key probe of the adaptive entry point: the smallest and largest key (over
-// all rows) and rows per coarse bucket key >> cshift (nb buckets), into
-// out = {min, max, counts[nb]} (the caller presets min / max and zeroes the
-// counts).  Keys outside [0, G) are not counted in the buckets.
-cudaError_t launch_key_probe(const int32_t* keys, long long n, long long G, int cshift, int nb, int* out,
-                             cudaStream_t s);
 
 // Several value columns over one key column in one pass (repro_cols.cu):
 // four columns (NV = 4), or one column and its square (NV = 2, square:

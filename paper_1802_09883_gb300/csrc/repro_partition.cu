@@ -58,6 +58,14 @@ constexpr long long kChunkRows = 32768;  // rows per unit of the fine pass
 // and raises again), and a partition longer than an item is split into
 // several (partial tables, merged afterwards).  The tuner measures 1-8.
 constexpr long long kItemsPerCta = 2;
+// Skewed keys (the fullest final partition above kSkewRatio times the mean,
+// decided on the device from the histogram's totals) with more than
+// kOneLevelParts partitions: kSkewItemsPerCta items per CTA instead, so that
+// a hot partition is cut into shorter items spread over many CTAs.  With
+// few partitions every partition is already cut into several items.  The
+// tuner measured 8 best on Zipf keys at 2^20 and 2^24 groups, 2 at 2^16.
+constexpr double kSkewRatio = 4.0;
+constexpr long long kSkewItemsPerCta = 8;
 
 // Geometry of one partition pass: a row with key k goes to bucket
 // (k >> shift) & bmask and is written with key k & kmask.
@@ -119,9 +127,10 @@ __global__ void __launch_bounds__(kPartThreads) k_part_hist(const int32_t* __res
                                                             PassGeom pg, int* __restrict__ counts,
                                                             unsigned* __restrict__ errors0,
                                                             unsigned long long* __restrict__ ftot, int fshift,
-                                                            int Ff) {
+                                                            int Ff, int* __restrict__ range) {
     extern __shared__ int s_hist[];  // [B] bucket counts, then [Ff] final-partition counts (ftot set)
     int* s_fin = s_hist + pg.B;
+    int kmin = 0x7fffffff, kmax = (int)0x80000000;  // the key range (range set)
     for (int unit = blockIdx.x;; unit += unit_step(units)) {
         long long beg, end;
         int seg;
@@ -140,6 +149,10 @@ __global__ void __launch_bounds__(kPartThreads) k_part_hist(const int32_t* __res
         const long long n4 = beg + ((end - beg) & ~3ll);
         const long long step = 4ll * blockDim.x;
         auto count1 = [&](int k) {
+            if (range) {
+                kmin = min(kmin, k);
+                kmax = max(kmax, k);
+            }
             if (!pg.check || (unsigned)k < (unsigned)Gk) {
                 atomicAdd(&s_hist[((unsigned)k >> pg.shift) & pg.bmask], 1);
                 if (ftot) atomicAdd(&s_fin[(unsigned)k >> fshift], 1);
@@ -172,6 +185,17 @@ __global__ void __launch_bounds__(kPartThreads) k_part_hist(const int32_t* __res
                 if (s_fin[p]) atomicAdd(&ftot[p], (unsigned long long)s_fin[p]);
         __syncthreads();
         if (!units.chunks) break;
+    }
+    if (range) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            kmin = min(kmin, __shfl_xor_sync(0xffffffffu, kmin, o));
+            kmax = max(kmax, __shfl_xor_sync(0xffffffffu, kmax, o));
+        }
+        if ((threadIdx.x & 31) == 0) {
+            atomicMin(&range[0], kmin);
+            atomicMax(&range[1], kmax);
+        }
     }
 }
 
@@ -651,11 +675,31 @@ __global__ void __launch_bounds__(1024) k_part_plan(const long long* __restrict_
                                                     const int* win, int win_hint, const PartTask* __restrict__ tt,
                                                     int B, MTask* __restrict__ tasks, MItem* __restrict__ items,
                                                     int* nitems, MergeBlk* __restrict__ blks, int* nblks,
-                                                    long long G_hdr) {
+                                                    long long G_hdr, long long tpi_skew) {
     __shared__ long long s_it[1024], s_pt[1024], s_bk[1024];
     const size_t rec = 8 + 16 * (size_t)L;
     const int per = (pg.F + blockDim.x - 1) / blockDim.x;
     const int p0 = threadIdx.x * per, p1 = min(pg.F, p0 + per);
+    if (tpi_skew > 0) {  // skewed keys: the fullest partition above kSkewRatio x the mean
+        long long mx = 0, sum = 0;
+        for (int p = p0; p < p1; ++p) {
+            mx = max(mx, pcount[p]);
+            sum += pcount[p];
+        }
+        s_it[threadIdx.x] = mx;
+        s_pt[threadIdx.x] = sum;
+        __syncthreads();
+        for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+            if ((int)threadIdx.x < o) {
+                s_it[threadIdx.x] = max(s_it[threadIdx.x], s_it[threadIdx.x + o]);
+                s_pt[threadIdx.x] += s_pt[threadIdx.x + o];
+            }
+            __syncthreads();
+        }
+        const bool skewed = (double)s_it[0] * pg.F > kSkewRatio * (double)s_pt[0];
+        __syncthreads();
+        if (skewed) tpi = tpi_skew;
+    }
     long long it = 0, pt = 0, bk = 0;
     for (int p = p0; p < p1; ++p) {
         const long long cnt = pcount[p];
@@ -742,6 +786,7 @@ struct PartPlan {
     FusedPlanConfig cfg;
     int ctas;            // CTAs of the multi-task kernel
     long long tpi;       // tiles per work item
+    long long tpi_skew;  // tiles per work item if the keys are skewed (0: no rule)
     long long max_items, max_blks, max_part_recs;
     int windows;         // 1: compute every group's window before aggregating
     long long max_wchunks;
@@ -802,13 +847,18 @@ bool make_part_plan(const PartChoice& pc, int L, long long G, long long n, PartP
     const long long R = pc.cfg.R;
     const long long total_tiles = (n + R - 1) / R + F;
     const long long ipc = pc.ipc > 0 ? pc.ipc : kItemsPerCta;
-    pp.tpi = std::max(8ll, (total_tiles + ipc * pp.ctas - 1) / (ipc * pp.ctas));
-    pp.tpi = std::min(pp.tpi, (1ll << 23) / R);
-    pp.max_items = total_tiles / pp.tpi + F + 1;
-    const long long max_split = std::min(F, total_tiles / pp.tpi + 1);
+    auto tiles_per_item = [&](long long k) {
+        return std::min(std::max(8ll, (total_tiles + k * pp.ctas - 1) / (k * pp.ctas)), (1ll << 23) / R);
+    };
+    pp.tpi = tiles_per_item(ipc);
+    // a measured choice stands; the rule's skew split only with many partitions
+    pp.tpi_skew = pc.ipc == 0 && F > kOneLevelParts ? tiles_per_item(kSkewItemsPerCta) : 0;
+    const long long tpi_min = pp.tpi_skew > 0 ? std::min(pp.tpi, pp.tpi_skew) : pp.tpi;  // sizes the lists
+    pp.max_items = total_tiles / tpi_min + F + 1;
+    const long long max_split = std::min(F, total_tiles / tpi_min + 1);
     pp.max_blks = max_split * ((Gp + 31) / 32);
     // only partitions of at least 2 tpi tiles are split into several items
-    pp.max_part_recs = (total_tiles / pp.tpi + 1 + max_split) * (long long)Gp;
+    pp.max_part_recs = (total_tiles / tpi_min + 1 + max_split) * (long long)Gp;
     pp.windows = n < kWindowRowsPerGroup * G ? 1 : 0;
     pp.max_wchunks = (n + kWindowChunkRows - 1) / kWindowChunkRows + F;
     if (pp.F > 8 * 1024) return false;  // k_seg_chunks covers 8 partitions per thread
@@ -849,8 +899,8 @@ PartScratch part_scratch_layout(const PartPlan& pp, long long n, int dtype, int 
         take(s.pstart1, (size_t)pp.F1 * 8);
         take(s.pcount1, (size_t)pp.F1 * 8);
         take(s.chunks, (size_t)pp.max_chunks * sizeof(PartChunk));
-        take(s.cursor, (size_t)pp.Fs * 4);
     }
+    take(s.cursor, (size_t)pp.Fs * 4);
     take(s.ptot, (size_t)pp.Fs * 8);
     take(s.pstart, (size_t)pp.Fs * 8);
     take(s.pcount, (size_t)pp.Fs * 8);
@@ -879,13 +929,20 @@ cudaError_t launch_scatter(const int32_t* keys, const void* vals, const Units& u
 }
 
 cudaError_t launch_hist(const int32_t* keys, const Units& u, const PassGeom& pg, int grid, int* counts,
-                        unsigned* errors, unsigned long long* ftot, int fshift, int Ff, cudaStream_t s) {
+                        unsigned* errors, unsigned long long* ftot, int fshift, int Ff, cudaStream_t s,
+                        PartProbe* probe = nullptr) {
     const size_t smem = ((size_t)pg.B + (ftot ? (size_t)Ff : 0)) * 4;
     cudaError_t e = cudaFuncSetAttribute(k_part_hist, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k_part_hist<<<grid, kPartThreads, smem, s>>>(keys, u, pg, counts, errors, ftot, fshift, Ff);
+    k_part_hist<<<grid, kPartThreads, smem, s>>>(keys, u, pg, counts, errors, ftot, fshift, Ff,
+                                                 probe ? probe->dev : nullptr);
     count_launches(1);
-    return cudaGetLastError();
+    if ((e = cudaGetLastError()) != cudaSuccess || !probe) return e;
+    int r[2] = {0, 0};  // the key range: read back once, then the caller's decision
+    if ((e = cudaMemcpyAsync(r, probe->dev, sizeof(r), cudaMemcpyDeviceToHost, s)) != cudaSuccess) return e;
+    if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;
+    probe->abandoned = !probe->keep(r[0], r[1]);
+    return cudaSuccess;
 }
 
 cudaError_t launch_scatter_t(int dtype, const int32_t* keys, const void* vals, const Units& u, const PassGeom& pg,
@@ -902,9 +959,10 @@ cudaError_t launch_scatter_t(int dtype, const int32_t* keys, const void* vals, c
 cudaError_t partition_pass(const int32_t* keys, const void* vals, int dtype, const Units& u, const PassGeom& pg,
                            const ScanGeom& sg, int grid, int* counts, int* offsets, long long* ptot,
                            long long* pstart, long long* pcount, int32_t* okeys, void* ovals, unsigned* errors,
-                           cudaStream_t s, unsigned long long* ftot = nullptr, int fshift = 0, int Ff = 0) {
-    cudaError_t e = launch_hist(keys, u, pg, grid, counts, errors, ftot, fshift, Ff, s);
-    if (e != cudaSuccess) return e;
+                           cudaStream_t s, unsigned long long* ftot = nullptr, int fshift = 0, int Ff = 0,
+                           PartProbe* probe = nullptr) {
+    cudaError_t e = launch_hist(keys, u, pg, grid, counts, errors, ftot, fshift, Ff, s, probe);
+    if (e != cudaSuccess || (probe && probe->abandoned)) return e;
     const int sgrid = std::max(1, std::min(1024, (sg.F + 7) / 8));
     k_scan_totals<<<sgrid, 256, 0, s>>>(counts, sg, ptot);
     k_scan_starts<<<1, 1024, 0, s>>>(ptot, sg.F, pstart, pcount, nullptr);
@@ -975,7 +1033,7 @@ size_t partitioned_scratch_bytes(const PartChoice& pc, int dtype, int L, long lo
 
 cudaError_t launch_groupby_partitioned(const int32_t* keys, const void* vals, long long n, int dtype, int L,
                                        long long G, const PartChoice& pc, void* state, void* scratch,
-                                       cudaStream_t s, long long G_hdr) {
+                                       cudaStream_t s, long long G_hdr, PartProbe* probe) {
     if (G_hdr <= 0) G_hdr = G;
     PartPlan pp;
     if (!make_part_plan(pc, L, G, n, pp) || !fused_config_fits(dtype, L, pp.Gp, kMetaSmemBytes, pc.cfg))
@@ -991,10 +1049,32 @@ cudaError_t launch_groupby_partitioned(const int32_t* keys, const void* vals, lo
     cudaError_t e;
     const Units whole{pp.chunk, n, nullptr, nullptr, nullptr};
     prof_begin(PROF_PARTITION, s);
-    if (pp.levels == 1) {
+    if (pp.levels == 1 && pp.F <= kOneLevelParts) {
         const ScanGeom sg{pp.Fs, pp.Fs, 1, pp.C, pp.C, nullptr, nullptr};
         e = partition_pass(keys, vals, dtype, whole, pp.p1, sg, pp.C, (int*)(b + ly.counts1), (int*)(b + ly.offsets1),
-                           (long long*)(b + ly.ptot), pstart, pcount, okeys, ovals, errors, s);
+                           (long long*)(b + ly.ptot), pstart, pcount, okeys, ovals, errors, s, nullptr, 0, 0, probe);
+    } else if (pp.levels == 1) {
+        // a wide single pass: runs of a few rows per partition per tile, so
+        // every tile reserves its runs from the partition's shared cursor
+        // (runs of all CTAs then fill each partition front to back and its
+        // lines complete in L2) rather than from per-CTA regions (about
+        // F x 2 x SMs partly written runs open at once; measured at 2^28
+        // rows, 1024 partitions: 5.66 -> 2.91 ms, 512: 3.35 -> 2.16 ms)
+        const ScanGeom sg{pp.Fs, pp.Fs, 1, pp.C, pp.C, nullptr, nullptr};
+        int* counts = (int*)(b + ly.counts1);
+        long long* ptot = (long long*)(b + ly.ptot);
+        int* cursor = (int*)(b + ly.cursor);
+        e = launch_hist(keys, whole, pp.p1, pp.C, counts, errors, nullptr, 0, 0, s, probe);
+        if (e != cudaSuccess || (probe && probe->abandoned)) {
+            prof_end(PROF_PARTITION, s);
+            return e;
+        }
+        const int sgrid = std::max(1, std::min(1024, (sg.F + 7) / 8));
+        k_scan_totals<<<sgrid, 256, 0, s>>>(counts, sg, ptot);
+        k_scan_starts<<<1, 1024, 0, s>>>(ptot, sg.F, pstart, pcount, cursor);
+        count_launches(2);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        e = launch_scatter_t(dtype, keys, vals, whole, pp.p1, pp.C, nullptr, cursor, okeys, ovals, errors, s);
     } else {
         int32_t* akeys = (int32_t*)(b + ly.akeys);
         void* avals = b + ly.avals;
@@ -1006,8 +1086,11 @@ cudaError_t launch_groupby_partitioned(const int32_t* keys, const void* vals, lo
         if ((e = cudaMemsetAsync(ptot, 0, (size_t)pp.Fs * 8, s)) != cudaSuccess) return e;
         e = partition_pass(keys, vals, dtype, whole, pp.p1, sg1, pp.C, (int*)(b + ly.counts1), (int*)(b + ly.offsets1),
                            (long long*)(b + ly.ptot1), pstart1, pcount1, akeys, avals, errors, s,
-                           reinterpret_cast<unsigned long long*>(ptot), pp.p2.shift, pp.Fs);
-        if (e != cudaSuccess) return e;
+                           reinterpret_cast<unsigned long long*>(ptot), pp.p2.shift, pp.Fs, probe);
+        if (e != cudaSuccess || (probe && probe->abandoned)) {  // abandoned: the scans never ran
+            prof_end(PROF_PARTITION, s);
+            return e;
+        }
         PartChunk* chunks = (PartChunk*)(b + ly.chunks);
         k_seg_chunks<<<1, 1024, 0, s>>>(pstart1, pcount1, pp.F1, kChunkRows, chunks, nullptr, nullptr, ints + 3);
         count_launches(1);
@@ -1024,7 +1107,7 @@ cudaError_t launch_groupby_partitioned(const int32_t* keys, const void* vals, lo
         count_launches(1);
     }
     prof_end(PROF_PARTITION, s);
-    if (e != cudaSuccess) return e;
+    if (e != cudaSuccess || (probe && probe->abandoned)) return e;
     // every group's window: exact from a window pass when groups are sparse,
     // else a lower bound the task's items raise as they end (later items of
     // a split partition then start near their groups' windows)
@@ -1049,7 +1132,8 @@ cudaError_t launch_groupby_partitioned(const int32_t* keys, const void* vals, lo
     k_part_plan<<<1, 1024, 0, s>>>(pstart, pcount, pg, (int)G, pp.cfg.R, pp.tpi, okeys, ovals,
                                    dtype == REPRO_F64 ? 8 : 4, (unsigned char*)state, L, win, win_hint, nullptr, 0,
                                    (MTask*)(b + ly.tasks),
-                                   (MItem*)(b + ly.items), ints, (MergeBlk*)(b + ly.blks), ints + 1, G_hdr);
+                                   (MItem*)(b + ly.items), ints, (MergeBlk*)(b + ly.blks), ints + 1, G_hdr,
+                                   pp.tpi_skew);
     count_launches(1);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     e = launch_multi(dtype, L, pp.cfg, pp.Gp, b + ly.tasks, b + ly.items, (int)pp.max_items, ints, ints + 2,
@@ -1223,7 +1307,7 @@ cudaError_t BatchPartition::launch(void* scratch, cudaStream_t s) const {
     k_part_plan<<<1, 1024, 0, s>>>(pstart, pcount, geo, 0, P.pc.cfg.R, P.tpi, okeys, ovals,
                                    P.dtype == REPRO_F64 ? 8 : 4, nullptr, P.L, nullptr, 0,
                                    (const PartTask*)(b + P.ly.ptask), P.B, (MTask*)(b + P.ly.tasks),
-                                   (MItem*)(b + P.ly.items), ints, (MergeBlk*)(b + P.ly.blks), ints + 1, 0);
+                                   (MItem*)(b + P.ly.items), ints, (MergeBlk*)(b + P.ly.blks), ints + 1, 0, 0);
     count_launches(1);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     e = launch_multi(P.dtype, P.L, P.pc.cfg, P.Gp, b + P.ly.tasks, b + P.ly.items, (int)P.max_items, ints, ints + 2,
@@ -1236,56 +1320,4 @@ cudaError_t BatchPartition::launch(void* scratch, cudaStream_t s) const {
 }
 
 // ------------------------------------------------------------------
-// Key probe (the adaptive entry point's look at the data before it picks a
-// depth): one read of the keys with 16-byte loads, the smallest and largest
-// key, and rows per coarse bucket key >> cshift of the valid keys.
-
-__global__ void __launch_bounds__(512) k_key_probe(const int32_t* __restrict__ keys, long long n, long long G,
-                                                   int cshift, int nb, int* __restrict__ out) {
-    extern __shared__ int s_cnt[];
-    for (int b = threadIdx.x; b < nb; b += blockDim.x) s_cnt[b] = 0;
-    __syncthreads();
-    int kmin = 0x7fffffff, kmax = (int)0x80000000;
-    auto one = [&](int k) {
-        kmin = min(kmin, k);
-        kmax = max(kmax, k);
-        if ((unsigned)k < (unsigned long long)G) atomicAdd(&s_cnt[(unsigned)k >> cshift], 1);
-    };
-    const long long n4 = n & ~3ll;
-    const long long stride = 4ll * gridDim.x * blockDim.x;
-    for (long long i = 4ll * (blockIdx.x * (long long)blockDim.x + threadIdx.x); i < n4; i += stride) {
-        const int4 k = *reinterpret_cast<const int4*>(keys + i);
-        one(k.x);
-        one(k.y);
-        one(k.z);
-        one(k.w);
-    }
-    if (blockIdx.x == 0)
-        for (long long i = n4 + threadIdx.x; i < n; i += blockDim.x) one(keys[i]);
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        kmin = min(kmin, __shfl_xor_sync(0xffffffffu, kmin, o));
-        kmax = max(kmax, __shfl_xor_sync(0xffffffffu, kmax, o));
-    }
-    if ((threadIdx.x & 31) == 0) {
-        atomicMin(&out[0], kmin);
-        atomicMax(&out[1], kmax);
-    }
-    __syncthreads();
-    for (int b = threadIdx.x; b < nb; b += blockDim.x)
-        if (s_cnt[b]) atomicAdd(&out[2 + b], s_cnt[b]);
-}
-
-cudaError_t launch_key_probe(const int32_t* keys, long long n, long long G, int cshift, int nb, int* out,
-                             cudaStream_t s) {
-    const size_t smem = (size_t)nb * 4;
-    cudaError_t e = cudaFuncSetAttribute(k_key_probe, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    const long long work = (n / 4 + 511) / 512;
-    const int grid = (int)std::max(1ll, std::min<long long>(work, (long long)device_info().sms * 4));
-    k_key_probe<<<grid, 512, smem, s>>>(keys, n, G, cshift, nb, out);
-    count_launches(1);
-    return cudaGetLastError();
-}
-
 }  // namespace rp

@@ -83,11 +83,14 @@ def test_full_key_range_keeps_the_rule_depth(dist):
 
 
 def test_bad_keys_and_unaligned_columns_go_the_plain_way():
+    """A key outside [0, G) keeps the plan for the declared count (which
+    flags it, as repro_groupby_sum does); unaligned columns skip the range
+    read altogether."""
     G, L = 1 << 20, 3
     keys, vals = _rows(100_003, 2000, 11)
     keys[77] = G + 3
     depth, a, b = _both(keys, vals, G, L)
-    assert depth == -1
+    assert depth in (1, 2)
     with pytest.raises(R.ReproError):
         a.check()
     assert torch.equal(a.tensor, b.tensor)
