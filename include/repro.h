@@ -144,11 +144,16 @@ repro_status repro_groupby_sum(const int32_t* keys, const void* values, int64_t 
  * num_groups only bounds the keys.  When it exceeds one shared-memory table,
  * the partitioned path planned for num_groups starts, and its first
  * histogram pass (which reads every key anyway) also takes the keys' range;
- * the stream is synchronised once, and if the groups the keys reach,
+ * the stream is synchronised once (range and partition row counts read
+ * back), and if the groups the keys reach,
  * max(key) + 1, call for another plan -- no partitioning while one table
  * holds them (a single pass over records [0, max(key)]), else one or two
- * partition passes sized for that many groups -- the call stops there and
- * runs that plan instead; otherwise it goes on.  In both plans skewed keys
+ * partition passes sized for that many groups; when the keys are skewed
+ * (the fullest partition above four times the mean) and no tuned choice
+ * applies, one pass into partitions small enough for lane-private table
+ * copies where at most 2048 partitions cover the groups, else one wide pass
+ * instead of two where that covers them -- the call stops there and runs
+ * that plan instead; otherwise it goes on.  In both plans skewed keys
  * (the fullest partition above four times the mean, seen on the device)
  * cut their partitions into shorter work items when there are more than 64
  * partitions and no tuned choice, as in repro_groupby_sum.  Same

@@ -134,6 +134,10 @@ using namespace rp;
 
 namespace rp {
 
+// The adaptive entry point's skew test: the fullest partition above this
+// many times the mean row count of the partitions the keys reach.
+constexpr double kAdaptiveSkewRatio = 4.0;
+
 // Rows per staged chunk of repro_groupby_sum_host (two chunks in flight);
 // REPRO_HOST_CHUNK_ROWS (2^20 to 2^27) overrides it.
 constexpr long long kHostChunkRows = 1ll << 24;
@@ -227,10 +231,10 @@ repro_status repro_groupby_sum_adaptive(const int32_t* keys, const void* values,
         !partitioned_supported(dtype, L, num_groups, n, keys, values) ||
         !partition_choose(dtype, L, num_groups, pc))
         return (repro_status)groupby_dispatch(keys, values, n, dtype, L, num_groups, state, s);
-    // the partitioned path planned for num_groups reads the key range in its
-    // first histogram; it goes on when the groups the keys reach, max + 1,
-    // would take the same plan, else it stops there and the call is planned
-    // again for those groups
+    // the partitioned path planned for num_groups reads the key range and the
+    // partitions' row counts in its first pass; it goes on when the groups
+    // the keys reach, max + 1, and their skew call for the same plan, else it
+    // stops there and the call is planned again
     Scratch rng(2 * sizeof(int), s);
     if (rng.err != cudaSuccess) return from_cuda(rng.err);
     const int init[2] = {INT32_MAX, INT32_MIN};
@@ -241,7 +245,7 @@ repro_status repro_groupby_sum_adaptive(const int32_t* keys, const void* values,
     PartChoice pk;
     PartProbe probe;
     probe.dev = (int*)rng.p;
-    probe.keep = [&](int kmin, int kmax) {
+    probe.keep = [&](int kmin, int kmax, const std::vector<long long>& tot) {
         if (kmin < 0 || (long long)kmax >= num_groups) return true;  // bad keys: this path flags them
         Gk = (long long)kmax + 1;
         FusedPlanConfig c;
@@ -250,7 +254,38 @@ repro_status repro_groupby_sum_adaptive(const int32_t* keys, const void* values,
             return false;
         }
         if (!partition_choose(dtype, L, Gk, pk)) return true;
-        return pk.shift == pc.shift && (pk.shift1 > pk.shift) == (pc.shift1 > pc.shift);
+        // skewed keys (the fullest partition the keys reach above
+        // kAdaptiveSkewRatio x their mean), unless the choice was measured:
+        // one pass into partitions small enough for lane-private table
+        // copies (a hot key's rows then never meet on one word within a
+        // warp), where at most 2048 partitions cover the groups; else one
+        // wide pass instead of two.  Both are what the tuner measured best
+        // on Zipf keys (2^16 groups: 2^7 or 2^6 groups per partition; 2^20:
+        // one pass into 1024 partitions)
+        const long long Fk = std::min<long long>((long long)tot.size(), ((Gk - 1) >> pc.shift) + 1);
+        long long hot = 0;
+        for (long long p = 0; p < Fk; ++p) hot = std::max(hot, tot[(size_t)p]);
+        const bool skewed = (double)hot * (double)Fk > kAdaptiveSkewRatio * (double)n;
+        if (skewed && !pk.measured) {
+            PartChoice t;
+            bool found = false;
+            for (int sh = pk.shift; sh >= 6 && !found; --sh)
+                if (partition_with(dtype, L, Gk, sh, 1, t) && t.cfg.copies == 32) {
+                    pk = t;
+                    found = true;
+                }
+            // else one pass where at most 1024 partitions cover the groups
+            // (wider single passes scatter slower: 2.91 ms into 1024, more
+            // into 2048), at the rule's width or twice it
+            if (!found && (pk.shift1 > pk.shift || ((Gk - 1) >> pk.shift) + 1 > 1024))
+                for (int sh = pk.shift; sh <= pk.shift + 1 && !found; ++sh)
+                    if (((Gk - 1) >> sh) + 1 <= 1024 && partition_with(dtype, L, Gk, sh, 1, t)) {
+                        pk = t;
+                        found = true;
+                    }
+        }
+        return pk.shift == pc.shift && (pk.shift1 > pk.shift) == (pc.shift1 > pc.shift) &&
+               pk.cfg.copies == pc.cfg.copies;
     };
     {
         Scratch scratch(partitioned_scratch_bytes(pc, dtype, L, num_groups, n), s);
@@ -262,8 +297,8 @@ repro_status repro_groupby_sum_adaptive(const int32_t* keys, const void* values,
             return REPRO_OK;
         }
     }
-    // the keys reach Gk < num_groups groups: none, one or two passes for Gk
-    // (records [0, Gk) of the state; the header keeps num_groups)
+    // another plan for the Gk <= num_groups groups the keys reach: none, one
+    // or two passes (records [0, Gk) of the state; the header keeps num_groups)
     if (single) {
         if (!fused_plan_config(dtype, L, (int)Gk, 0, cfg, true))  // not expected: the probe just saw it fit
             return (repro_status)groupby_dispatch(keys, values, n, dtype, L, num_groups, state, s);

@@ -243,18 +243,16 @@ struct Signed<double> {
             : "=r"(sl), "=r"(sh)
             : "r"(vlo), "r"(mh), "r"(S));
         // X = significand * 2^s, s = E + 79 - 40 kb in [27, 66], has at least
-        // 27 zero bits at the bottom; the words hold X' = X / 2^8 (shift
-        // s - 8 in [19, 58]: by 5 first -- the signed significand still fits
-        // 64 bits -- then by s - 13 in [14, 53] = r within a word and q = 0
-        // or 1 whole words), so that X's 40-bit field [40, 80) is word 1
-        // plus the low byte of word 2
-        const uint32_t sl5 = sl << 5, sh5 = __funnelshift_l(sl, sh, 5);
-        const int s13 = t + 14 - 40 * kb;
-        const int r = s13 & 31;
-        const bool q = s13 >= 32;
-        const uint32_t v0 = sl5 << r;
-        const uint32_t v1 = __funnelshift_l(sl5, sh5, r);
-        const uint32_t v2 = __funnelshift_l(sh5, S, r);
+        // 27 zero bits at the bottom; the words hold X' = X / 2^8, the signed
+        // significand shifted by s - 8 in [19, 58] = r within a word and q =
+        // 0 or 1 whole words (X' < 2^111 in magnitude), so that X's 40-bit
+        // field [40, 80) is word 1 plus the low byte of word 2
+        const int s8 = t + 19 - 40 * kb;
+        const int r = s8 & 31;
+        const bool q = s8 >= 32;
+        const uint32_t v0 = sl << r;
+        const uint32_t v1 = __funnelshift_l(sl, sh, r);
+        const uint32_t v2 = __funnelshift_l(sh, S, r);
         const uint32_t w0 = q ? 0u : v0;
         const uint32_t w1 = q ? v0 : v1;
         const uint32_t w2 = q ? v1 : v2;

@@ -82,20 +82,25 @@ struct PartChoice {
     int shift1 = 0;
     FusedPlanConfig cfg{};
     int ipc = 0;
+    bool measured = false;  // from the tuner (forced or cached), not the rule
 };
 bool partition_choose(int dtype, int L, long long G, PartChoice& pc);
+// A choice of width 2^shift with `levels` partition passes and the rule's
+// aggregation configuration; false where that width or depth is not usable.
+bool partition_with(int dtype, int L, long long G, int shift, int levels, PartChoice& pc);
 bool partitioned_supported(int dtype, int L, long long G, long long n, const void* keys, const void* vals);
 size_t partitioned_scratch_bytes(const PartChoice& pc, int dtype, int L, long long G, long long n);
-// The key range read by the first partition pass's histogram, for a caller
-// that may drop the call when the keys reach far fewer groups than planned
-// for: dev points to {min, max} (preset to {INT32_MAX, INT32_MIN}); after the
-// histogram the stream is synchronised and keep(min, max) decides; when it
-// returns false the call returns at once with abandoned set (nothing has been
-// written to the state: only keys outside [0, G) would have flagged it, and
-// keep must return true for those).
+// The key range and the final partitions' row counts read by the first
+// partition pass's histogram, for a caller that may drop the call when
+// another plan suits the keys better: dev points to {min, max} (preset to
+// {INT32_MAX, INT32_MIN}); once the histogram and the partition totals are
+// known the stream is synchronised and keep(min, max, totals) decides; when
+// it returns false the call returns at once with abandoned set (nothing has
+// been written to the state: only keys outside [0, G) would have flagged
+// it, and keep must return true for those).
 struct PartProbe {
     int* dev = nullptr;
-    std::function<bool(int, int)> keep;
+    std::function<bool(int, int, const std::vector<long long>&)> keep;
     bool abandoned = false;
 };
 

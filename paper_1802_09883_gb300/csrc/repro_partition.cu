@@ -5,12 +5,13 @@
 // owning a disjoint slice of the caller's state (Algorithm 4's private
 // tables; the slices make the merge into the shared table a plain write).
 //
-// Up to 64 partitions the rows are partitioned in one pass (a measured
-// choice may take one pass up to 2048).  Beyond that a single pass would
-// write runs of only a few rows per partition per tile (scattered stores),
-// so the rows are partitioned twice, as the paper's multi-pass radix
-// partitioning does for large fan-outs: a coarse pass by the high key bits,
-// then, inside every coarse partition, a fine pass by the next bits.  A pass:
+// Up to 512 partitions the rows are partitioned in one pass (a measured
+// choice may take one pass up to 2048; beyond 64 partitions each tile
+// reserves its runs from the partitions' shared cursors).  Beyond that a
+// single pass writes runs of only a few rows per partition per tile, so the
+// rows are partitioned twice, as the paper's multi-pass radix partitioning
+// does for large fan-outs: a coarse pass by the high key bits, then, inside
+// every coarse partition, a fine pass by the next bits.  A pass:
 //
 //   k_part_hist     per unit (a CTA's chunk of rows), rows per bucket (and
 //                   bad keys); before two passes also every row's final
@@ -49,7 +50,8 @@ constexpr int kPartThreads = 512;
 constexpr int kScatterRows = 8;          // rows per thread per scatter tile
 constexpr uint64_t kCopyWaitNs = 2000000000ull;  // a scatter tile's copy is given up after 2 s
 constexpr int kMaxParts = 8192;          // final partitions
-constexpr int kOneLevelParts = 64;       // beyond this the rule takes two passes
+constexpr int kOneLevelParts = 64;       // beyond this a single pass reserves runs from shared cursors
+constexpr int kOneLevelRuleParts = 512;  // beyond this the rule takes two passes
 constexpr int kOneLevelMaxParts = 2048;  // one pass at most this wide
 constexpr long long kChunkRows = 32768;  // rows per unit of the fine pass
 // Work items per CTA the aggregation aims at by default: items come from a
@@ -937,11 +939,20 @@ cudaError_t launch_hist(const int32_t* keys, const Units& u, const PassGeom& pg,
     k_part_hist<<<grid, kPartThreads, smem, s>>>(keys, u, pg, counts, errors, ftot, fshift, Ff,
                                                  probe ? probe->dev : nullptr);
     count_launches(1);
-    if ((e = cudaGetLastError()) != cudaSuccess || !probe) return e;
-    int r[2] = {0, 0};  // the key range: read back once, then the caller's decision
-    if ((e = cudaMemcpyAsync(r, probe->dev, sizeof(r), cudaMemcpyDeviceToHost, s)) != cudaSuccess) return e;
-    if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;
-    probe->abandoned = !probe->keep(r[0], r[1]);
+    return cudaGetLastError();
+}
+
+// The probe's look at the data: the key range and the F final partitions'
+// row counts (totals: F x 8 bytes on the device), read back once with a
+// synchronisation, then the caller's decision.
+cudaError_t probe_read(PartProbe* probe, const long long* totals, int F, cudaStream_t s) {
+    int r[2] = {0, 0};
+    std::vector<long long> t((size_t)F);
+    cudaError_t e = cudaMemcpyAsync(r, probe->dev, sizeof(r), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(t.data(), totals, sizeof(long long) * (size_t)F, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return e;
+    probe->abandoned = !probe->keep(r[0], r[1], t);
     return cudaSuccess;
 }
 
@@ -962,12 +973,18 @@ cudaError_t partition_pass(const int32_t* keys, const void* vals, int dtype, con
                            cudaStream_t s, unsigned long long* ftot = nullptr, int fshift = 0, int Ff = 0,
                            PartProbe* probe = nullptr) {
     cudaError_t e = launch_hist(keys, u, pg, grid, counts, errors, ftot, fshift, Ff, s, probe);
-    if (e != cudaSuccess || (probe && probe->abandoned)) return e;
+    if (e != cudaSuccess) return e;
     const int sgrid = std::max(1, std::min(1024, (sg.F + 7) / 8));
     k_scan_totals<<<sgrid, 256, 0, s>>>(counts, sg, ptot);
+    count_launches(1);
+    if (probe) {  // the final partitions' totals: this pass's, or those the histogram counted (ftot)
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        e = ftot ? probe_read(probe, reinterpret_cast<const long long*>(ftot), Ff, s) : probe_read(probe, ptot, sg.F, s);
+        if (e != cudaSuccess || probe->abandoned) return e;
+    }
     k_scan_starts<<<1, 1024, 0, s>>>(ptot, sg.F, pstart, pcount, nullptr);
     k_scan_offsets<<<sgrid, 256, 0, s>>>(counts, sg, pstart, offsets);
-    count_launches(4);
+    count_launches(3);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     return launch_scatter_t(dtype, keys, vals, u, pg, grid, offsets, nullptr, okeys, ovals, errors, s);
 }
@@ -979,9 +996,11 @@ bool partition_choose(int dtype, int L, long long G, PartChoice& pc) {
     int forced = tune_forced_shift();
     int shift = 0, levels = 0;
     pc.ipc = 0;
+    pc.measured = false;
     if (forced && shift_usable(dtype, L, G, forced, pc.cfg)) {
         shift = forced;
         levels = tune_forced_levels();
+        pc.measured = true;
     } else {
         int tuned = 0, tuned_levels = 0, tuned_ipc = 0;
         FusedPlanConfig tuned_cfg{};
@@ -991,6 +1010,7 @@ bool partition_choose(int dtype, int L, long long G, PartChoice& pc) {
             levels = tuned_levels;
             if (tuned_cfg.S && fused_config_fits(dtype, L, 1 << tuned, kMetaSmemBytes, tuned_cfg)) pc.cfg = tuned_cfg;
             pc.ipc = tuned_ipc;
+            pc.measured = true;
         } else {
             // rule: the widest power-of-two slice whose table keeps two CTAs
             // per SM (then one), with at most kMaxParts partitions
@@ -1006,14 +1026,26 @@ bool partition_choose(int dtype, int L, long long G, PartChoice& pc) {
     }
     if (!shift) return false;
     pc.shift = shift;
-    // rule: one pass up to kOneLevelParts partitions, else two with about
-    // sqrt(F) buckets per coarse partition; a measured choice may take one
-    // pass up to kOneLevelMaxParts (a wider scatter, one pass fewer over the
-    // rows) or two passes beyond kOneLevelParts
+    // rule: one pass up to kOneLevelRuleParts partitions (measured at 2^28
+    // rows: one pass into 512 partitions 2.16 ms, two passes 2.43 ms; 1024
+    // partitions 2.91 ms, two passes 2.43 ms), else two with about sqrt(F)
+    // buckets per coarse partition; a measured choice may take one pass up
+    // to kOneLevelMaxParts or two passes beyond kOneLevelParts
     const long long F = (G + (1ll << shift) - 1) >> shift;
     if (levels == 1 && F > kOneLevelMaxParts) levels = 0;
     if (levels == 2 && F <= kOneLevelParts) levels = 0;
-    if (levels == 0) levels = F > kOneLevelParts ? 2 : 1;
+    if (levels == 0) levels = F > kOneLevelRuleParts ? 2 : 1;
+    pc.shift1 = levels == 2 ? shift + (ceil_log2(F) + 1) / 2 : 0;
+    return true;
+}
+
+bool partition_with(int dtype, int L, long long G, int shift, int levels, PartChoice& pc) {
+    pc = PartChoice{};
+    if (!shift_usable(dtype, L, G, shift, pc.cfg)) return false;
+    const long long F = (G + (1ll << shift) - 1) >> shift;
+    if ((levels == 1 && F > kOneLevelMaxParts) || (levels == 2 && F <= kOneLevelParts) || levels < 1 || levels > 2)
+        return false;
+    pc.shift = shift;
     pc.shift1 = levels == 2 ? shift + (ceil_log2(F) + 1) / 2 : 0;
     return true;
 }
@@ -1064,15 +1096,18 @@ cudaError_t launch_groupby_partitioned(const int32_t* keys, const void* vals, lo
         int* counts = (int*)(b + ly.counts1);
         long long* ptot = (long long*)(b + ly.ptot);
         int* cursor = (int*)(b + ly.cursor);
-        e = launch_hist(keys, whole, pp.p1, pp.C, counts, errors, nullptr, 0, 0, s, probe);
-        if (e != cudaSuccess || (probe && probe->abandoned)) {
+        if ((e = launch_hist(keys, whole, pp.p1, pp.C, counts, errors, nullptr, 0, 0, s, probe)) != cudaSuccess)
+            return e;
+        const int sgrid = std::max(1, std::min(1024, (sg.F + 7) / 8));
+        k_scan_totals<<<sgrid, 256, 0, s>>>(counts, sg, ptot);
+        count_launches(1);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        if (probe && ((e = probe_read(probe, ptot, sg.F, s)) != cudaSuccess || probe->abandoned)) {
             prof_end(PROF_PARTITION, s);
             return e;
         }
-        const int sgrid = std::max(1, std::min(1024, (sg.F + 7) / 8));
-        k_scan_totals<<<sgrid, 256, 0, s>>>(counts, sg, ptot);
         k_scan_starts<<<1, 1024, 0, s>>>(ptot, sg.F, pstart, pcount, cursor);
-        count_launches(2);
+        count_launches(1);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         e = launch_scatter_t(dtype, keys, vals, whole, pp.p1, pp.C, nullptr, cursor, okeys, ovals, errors, s);
     } else {

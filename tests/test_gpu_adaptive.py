@@ -65,15 +65,20 @@ def test_medium_key_range_takes_one_pass_instead_of_two():
     assert torch.equal(a.tensor, b.tensor)
 
 
-@pytest.mark.parametrize("dist", ["zipf", "uniform"])
-def test_full_key_range_keeps_the_rule_depth(dist):
-    """Keys over all 2^20 groups: the rule's depth; Zipf keys are skewed
-    (the probe's fullest bucket far above the mean), so their partitions go
-    in shorter work items -- the same bytes either way."""
-    G, L = 1 << 20, 3
+@pytest.mark.parametrize("G,dist,want", [(1 << 20, "zipf", 1), (1 << 20, "uniform", 2),
+                                         (1 << 16, "zipf", 1), (1 << 16, "uniform", 1)])
+def test_full_key_range_keeps_the_rule_depth(G, dist, want):
+    """Keys over all groups: uniform keys keep the rule's plan (two passes
+    over 1024 partitions at 2^20 groups, one over 64 at 2^16); Zipf keys are
+    skewed (the fullest partition far above the mean), so the call goes
+    over to one pass -- into 2^7-group partitions with lane-private table
+    copies at 2^16, into the rule's 1024 at 2^20 -- the same bytes either
+    way, and the oracle's."""
+    L = 3
+    R.tune_clear()  # the rule's choices, not a measured one
     w = WL.sweep_cell(G, dist, L, n=1 << 22, seed=9, device=DEV)
     depth, a, b = _both(w.keys, w.values, G, L)
-    assert depth in (1, 2)
+    assert depth == want
     assert torch.equal(a.tensor, b.tensor)
     ost = O.init(np.float64, L, G)
     O.groupby_sum(ost, w.keys.cpu().numpy(), w.values.cpu().numpy(), threads=4)
