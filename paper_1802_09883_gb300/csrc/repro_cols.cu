@@ -1,10 +1,13 @@
-// repro_cols.cu -- several value columns over one key stream in one pass.
+// repro_cols.cu -- a value column and its square over one key stream in one
+// pass.
 //
 // k_fused_cols is the single-pass kernel of repro_fused.cu for NV value
-// columns that share one key column (SUM(c0), ..., SUM(c_NV-1) GROUP BY key,
-// the few-group multi-column aggregate of the paper's TPC-H Q1 experiment,
-// Sec. VI), or for one column and its square (the sums of x and x*x behind
-// VARIANCE / STDDEV, Sec. I).  The producer warp stages a tile of keys and
+// columns that share one key column; it is built for one column and its
+// square (the sums of x and x*x behind VARIANCE / STDDEV, Sec. I).  (Built
+// for four plain columns -- the few-group multi-column aggregate of the
+// paper's TPC-H Q1 experiment, Sec. VI -- it measured slower than one
+// single pass per column: 1.09 vs 0.96 ms for four float columns over 4
+// groups.)  The producer warp stages a tile of keys and
 // of every column; the consumers walk the tile once per column, each column
 // with its own table, windows and raise list (Algorithm 2 per column, exact
 // integer bins), so per tile the keys, the TMA traffic and the tile
@@ -292,11 +295,9 @@ const void* cols_kernel_L(int L, int C) {
     }
 }
 
-// The kernels built: four plain columns, and x with x*x.
-const void* cols_kernel_of(int dtype, int L, bool square, int C) {
-    if (dtype == REPRO_F64)
-        return square ? cols_kernel_L<double, 2, true>(L, C) : cols_kernel_L<double, 4, false>(L, C);
-    return square ? cols_kernel_L<float, 2, true>(L, C) : cols_kernel_L<float, 4, false>(L, C);
+// The kernels built: x with x*x.
+const void* cols_kernel_of(int dtype, int L, int C) {
+    return dtype == REPRO_F64 ? cols_kernel_L<double, 2, true>(L, C) : cols_kernel_L<float, 2, true>(L, C);
 }
 
 size_t cols_smem(int dtype, int L, int G, int NV, const FusedPlanConfig& c) {
@@ -351,9 +352,8 @@ void launch_L(int L, const ColsArgs& a, int ctas, size_t smem, cudaStream_t s) {
 }
 
 template <typename T>
-void launch_any(int L, bool sq, const ColsArgs& a, int ctas, size_t smem, cudaStream_t s) {
-    if (sq) launch_L<T, 2, true>(L, a, ctas, smem, s);
-    else launch_L<T, 4, false>(L, a, ctas, smem, s);
+void launch_any(int L, const ColsArgs& a, int ctas, size_t smem, cudaStream_t s) {
+    launch_L<T, 2, true>(L, a, ctas, smem, s);
 }
 
 }  // namespace
@@ -365,7 +365,7 @@ void launch_any(int L, bool sq, const ColsArgs& a, int ctas, size_t smem, cudaSt
 constexpr int kColsMinCtasPerSm = 3;
 
 bool cols_supported(int dtype, int L, long long G, int NV, const int32_t* keys, const void* const* vals) {
-    if (NV != 2 && NV != 4) return false;  // NV = 2: a column and its square
+    if (NV != 2) return false;  // a column and its square only
     if ((uintptr_t)keys % 16) return false;
     for (int c = 0; c < NV; ++c)
         if ((uintptr_t)vals[c] % 16) return false;
@@ -381,16 +381,16 @@ size_t cols_scratch_bytes(int dtype, int L, long long G, int NV, long long n) {
 
 cudaError_t launch_groupby_cols(const int32_t* keys, const void* const* vals, int NV, bool square, long long n,
                                 int dtype, int L, long long G, void* const* states, void* scratch, cudaStream_t s) {
-    const int nv = square ? 2 : NV;
-    if (nv != (square ? 2 : 4)) return cudaErrorInvalidValue;
+    if (!square || NV != 2) return cudaErrorInvalidValue;
+    const int nv = 2;
     FusedPlanConfig cfg;
     if (!cols_config(dtype, L, G, nv, cfg)) return cudaErrorInvalidValue;
     const size_t smem = cols_smem(dtype, L, (int)G, nv, cfg);
-    const int resident = resident_ctas(cols_kernel_of(dtype, L, square, cfg.copies), 32 * 9, smem);
+    const int resident = resident_ctas(cols_kernel_of(dtype, L, cfg.copies), 32 * 9, smem);
     if (resident < 1) return cudaErrorInvalidConfiguration;
     ColsArgs a{};
     a.keys = keys;
-    for (int c = 0; c < (square ? 1 : nv); ++c) a.vals[c] = vals[c];
+    a.vals[0] = vals[0];
     a.n = n;
     a.G = (int)G;
     a.R = cfg.R;
@@ -403,8 +403,8 @@ cudaError_t launch_groupby_cols(const int32_t* keys, const void* const* vals, in
     a.partials = (unsigned char*)scratch;
     for (int c = 0; c < nv; ++c) a.errors[c] = &reinterpret_cast<repro_state_header*>(states[c])->errors;
     prof_begin(PROF_FUSED, s);
-    if (dtype == REPRO_F64) launch_any<double>(L, square, a, ctas, smem, s);
-    else launch_any<float>(L, square, a, ctas, smem, s);
+    if (dtype == REPRO_F64) launch_any<double>(L, a, ctas, smem, s);
+    else launch_any<float>(L, a, ctas, smem, s);
     prof_end(PROF_FUSED, s);
     count_launches(1);
     cudaError_t e = cudaGetLastError();

@@ -110,10 +110,9 @@ cudaError_t launch_groupby_partitioned(const int32_t* keys, const void* vals, lo
                                        long long G_hdr = 0, PartProbe* probe = nullptr);
 
 
-// Several value columns over one key column in one pass (repro_cols.cu):
-// four columns (NV = 4), or one column and its square (NV = 2, square:
-// vals[0] only, two states).  Supported only where the tables leave three
-// CTAs per SM.
+// A value column and its square over one key column in one pass
+// (repro_cols.cu): NV = 2 and square only (vals[0], two states).  Supported
+// only where the two tables leave three CTAs per SM.
 bool cols_supported(int dtype, int L, long long G, int NV, const int32_t* keys, const void* const* vals);
 size_t cols_scratch_bytes(int dtype, int L, long long G, int NV, long long n);
 cudaError_t launch_groupby_cols(const int32_t* keys, const void* const* vals, int NV, bool square, long long n,
