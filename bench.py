@@ -364,6 +364,26 @@ def time_fp_modes(R, keys, values, G, steps, stream):
     return res
 
 
+def verify_state(keys_np, vals_np, G, L, state_bytes, got, threads=0):
+    """One state and its results against the C oracle on the same rows, bit
+    for bit: every group's K, flags and 128-bit bins and every result."""
+    import numpy as np
+
+    import paper_1802_09883_gb300 as R
+    from oracle import oracle as O
+
+    nth = threads if threads and threads > 0 else (os.cpu_count() or 1)
+    ref = O.init(vals_np.dtype.type, L, G)
+    bad = O.groupby_sum(ref, keys_np, vals_np, threads=nth)
+    K, fl, lo, hi = R.parse_state(state_bytes, L, G)
+    oK, ofl, olo, ohi = O.to_bins(ref)
+    iv = np.int64 if vals_np.dtype == np.float64 else np.int32
+    state_ok = bool(np.array_equal(K, oK) and np.array_equal(fl, ofl) and np.array_equal(lo, olo)
+                    and np.array_equal(hi, ohi))
+    res_ok = bool(np.array_equal(np.asarray(got).view(iv), O.finalize(ref).view(iv)))
+    return state_ok and res_ok and bad == 0
+
+
 def verify_step(w, state_bytes, got, threads=0):
     """The last timed step's state and results against the CPU oracle.
 
@@ -544,6 +564,17 @@ def run_multicol(args, local_rank):
     clocks.stop()
     launches = lib.repro_launch_count() - l0
     prof = _prof_stop(lib)
+    for st in states:
+        st.check()
+    verify = None
+    if not args.no_verify:  # untimed: every column's state and results against the oracle
+        t0 = time.perf_counter()
+        torch.cuda.synchronize()
+        gh = gid.cpu().numpy()
+        oks = [verify_state(gh, c.cpu().numpy(), G, L, st.tensor.cpu().numpy(), o.cpu().numpy(),
+                            args.oracle_threads) for c, st, o in zip(colsl, states, outs)]
+        verify = {"mode": "full state, every column", "groups": G, "rows": n, "columns": len(oks),
+                  "bit_exact": all(oks), "oracle": "C oracle", "seconds": round(time.perf_counter() - t0, 2)}
     # conventional GroupBy on the same rows (group ids precomputed, untimed)
     fp_outs = [torch.empty(G, dtype=dt, device=dev) for _ in colsl]
     fp = R.groupby_sum_fp64 if dt == torch.float64 else R.groupby_sum_fp32
@@ -613,6 +644,9 @@ def run_multicol(args, local_rank):
                 "e2e": {"value": n / (e2e_ms / 1e3), "unit": "rows/s", "h2d_bytes_per_step": n * (2 + 4 * esz),
                         "d2h_bytes_per_step": 4 * G * esz, "ms_per_step": e2e_ms},
                 "gpu_launches": int(launches), "clocks": clocks.summary(), "tuned": tuned})
+    if verify is not None:
+        res["verify"] = verify
+        res["bit_exact"] = verify["bit_exact"]
     return res
 
 
@@ -816,6 +850,17 @@ def run_scalar(args, local_rank):
     ub_ms = _time(ub_step, max(1, args.steps // 2), stream)
     torch.cuda.synchronize()
     same = torch.equal(ub.tensor, st.tensor)
+    st.check()
+    verify = None
+    if not args.no_verify:  # untimed: the state and result against the oracle on all values
+        import numpy as np
+
+        t0 = time.perf_counter()
+        vh = vals.cpu().numpy()
+        ok = verify_state(np.zeros(vh.size, np.int32), vh, 1, args.L, st.tensor.cpu().numpy(), out.cpu().numpy(),
+                          args.oracle_threads)
+        verify = {"mode": "full state", "groups": 1, "rows": n, "bit_exact": ok, "oracle": "C oracle",
+                  "seconds": round(time.perf_counter() - t0, 2)}
     peaks = load_peaks()
     fused = prof.get("fused")
     roof = None
@@ -833,6 +878,9 @@ def run_scalar(args, local_rank):
                 "unbuffered_dropin": {"ms_per_step": ub_ms, "over_buffered_time": ub_ms / ms,
                                       "over_fp64_time": ub_ms / base_ms, "same_state_bytes": bool(same)},
                 "e2e": None, "gpu_launches": int(launches), "clocks": clocks.summary(), "tuned": tuned})
+    if verify is not None:
+        res["verify"] = verify
+        res["bit_exact"] = verify["bit_exact"]
     return res
 
 
@@ -888,6 +936,25 @@ def run_stats(args, local_rank):
                 "fp64_baseline": {"kind": "two groupby_sum_fp64 (x, x*x precomputed)", "ms_per_step": fp_ms,
                                   "repro_over_fp64_time": ms / fp_ms},
                 "e2e": None, "gpu_launches": int(launches), "clocks": clocks.summary()})
+    st.check()
+    if not args.no_verify:  # untimed: every statistic of every group against the oracle, bit for bit
+        import numpy as np
+
+        from oracle import stats as OS
+
+        t0 = time.perf_counter()
+        torch.cuda.synchronize()
+        nth = args.oracle_threads if args.oracle_threads > 0 else (os.cpu_count() or 1)
+        ref = OS.groupby_stats(w.keys.cpu().numpy(), w.values.cpu().numpy(), G, args.L, threads=nth)
+        ok = True
+        for name, want in ref.items():
+            got = outs[name].cpu().numpy()
+            iv = np.int64 if got.dtype.itemsize == 8 else np.int32
+            ok = ok and bool(np.array_equal(got.view(iv), np.asarray(want).astype(got.dtype).view(iv)))
+        res["verify"] = {"mode": "every statistic of every group", "groups": G, "rows": n, "bit_exact": ok,
+                         "oracle": f"C oracle ({nth} host threads) and oracle/stats.py",
+                         "seconds": round(time.perf_counter() - t0, 2)}
+        res["bit_exact"] = ok
     return res
 
 
