@@ -275,8 +275,8 @@ repro_status repro_groupby_sum_adaptive(const int32_t* keys, const void* values,
                     found = true;
                 }
             // else one pass where at most 1024 partitions cover the groups
-            // (wider single passes scatter slower: 2.91 ms into 1024, more
-            // into 2048), at the rule's width or twice it
+            // (a single pass into 2048 scatters slower than into 1024), at
+            // the rule's width or twice it
             if (!found && (pk.shift1 > pk.shift || ((Gk - 1) >> pk.shift) + 1 > 1024))
                 for (int sh = pk.shift; sh <= pk.shift + 1 && !found; ++sh)
                     if (((Gk - 1) >> sh) + 1 <= 1024 && partition_with(dtype, L, Gk, sh, 1, t)) {

@@ -5,9 +5,10 @@
 // owning a disjoint slice of the caller's state (Algorithm 4's private
 // tables; the slices make the merge into the shared table a plain write).
 //
-// Up to 512 partitions the rows are partitioned in one pass (a measured
+// Up to 1024 partitions the rows are partitioned in one pass (a measured
 // choice may take one pass up to 2048; beyond 64 partitions each tile
-// reserves its runs from the partitions' shared cursors).  Beyond that a
+// reserves its runs from the partitions' shared cursors, and beyond 256 the
+// tiles are twice as long).  Beyond that a
 // single pass writes runs of only a few rows per partition per tile, so the
 // rows are partitioned twice, as the paper's multi-pass radix partitioning
 // does for large fan-outs: a coarse pass by the high key bits, then, inside
@@ -48,10 +49,11 @@ namespace {
 
 constexpr int kPartThreads = 512;
 constexpr int kScatterRows = 8;          // rows per thread per scatter tile
+constexpr int kWideTileBuckets = 256;    // wider passes through shared cursors: tiles of 2 kScatterRows
 constexpr uint64_t kCopyWaitNs = 2000000000ull;  // a scatter tile's copy is given up after 2 s
 constexpr int kMaxParts = 8192;          // final partitions
 constexpr int kOneLevelParts = 64;       // beyond this a single pass reserves runs from shared cursors
-constexpr int kOneLevelRuleParts = 512;  // beyond this the rule takes two passes
+constexpr int kOneLevelRuleParts = 1024;  // beyond this the rule takes two passes
 constexpr int kOneLevelMaxParts = 2048;  // one pass at most this wide
 constexpr long long kChunkRows = 32768;  // rows per unit of the fine pass
 // Work items per CTA the aggregation aims at by default: items come from a
@@ -368,7 +370,7 @@ __device__ int block_exclusive_scan(int* a, int n, int* warp_tot) {
 // staging buffer while this one is ranked, sorted and written, so reads stay
 // in flight through the whole tile (unit starts are 4-row aligned, so every
 // copy starts 16-byte aligned; a tile's last rows % 4 are read directly).
-template <typename T>
+template <typename T, int RPT>
 __global__ void __launch_bounds__(kPartThreads) k_part_scatter(const int32_t* __restrict__ keys0,
                                                                const T* __restrict__ vals0, Units units,
                                                                PassGeom pg, const int* __restrict__ offsets,
@@ -376,8 +378,7 @@ __global__ void __launch_bounds__(kPartThreads) k_part_scatter(const int32_t* __
                                                                int32_t* __restrict__ okeys, T* __restrict__ ovals,
                                                                unsigned* errors0) {
     extern __shared__ __align__(16) unsigned char s_raw[];
-    constexpr int RPT = kScatterRows;  // rows per thread per tile
-    constexpr int TILE = RPT * kPartThreads;
+    constexpr int TILE = RPT * kPartThreads;  // RPT rows per thread per tile
     T* s_vals = reinterpret_cast<T*>(s_raw);              // [TILE] rows sorted by bucket
     T* s_in_vals = s_vals + TILE;                         // [TILE] staging (TMA)
     int* s_keys = reinterpret_cast<int*>(s_in_vals + TILE);  // [TILE] keys, sorted by bucket
@@ -917,17 +918,33 @@ PartScratch part_scratch_layout(const PartPlan& pp, long long n, int dtype, int 
     return s;
 }
 
+template <typename T, int RPT>
+cudaError_t launch_scatter_rpt(const int32_t* keys, const void* vals, const Units& u, const PassGeom& pg, int grid,
+                               const int* offsets, int* cursor, int32_t* okeys, void* ovals, unsigned* errors,
+                               cudaStream_t s) {
+    // sorted rows + staging rows, the mbarrier, three per-bucket arrays, scan scratch
+    const size_t smem = 2 * (size_t)RPT * kPartThreads * (sizeof(T) + 4) + 8 + 3 * (size_t)pg.B * 4 + 33 * 4;
+    cudaError_t e =
+        cudaFuncSetAttribute(k_part_scatter<T, RPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_part_scatter<T, RPT><<<grid, kPartThreads, smem, s>>>(keys, (const T*)vals, u, pg, offsets, cursor, okeys,
+                                                            (T*)ovals, errors);
+    return cudaGetLastError();
+}
+
+// A pass wider than kWideTileBuckets through shared cursors takes tiles
+// twice as long (one CTA per SM instead of two), so that each tile's runs,
+// and each global cursor atomic, cover twice the rows (measured at 2^28
+// rows: 1024 partitions 2.92 -> 2.18 ms, 512: 2.18 -> 1.65 ms; at 128
+// partitions the shorter tiles stay faster, 1.39 vs 1.54 ms).
 template <typename T>
 cudaError_t launch_scatter(const int32_t* keys, const void* vals, const Units& u, const PassGeom& pg, int grid,
                            const int* offsets, int* cursor, int32_t* okeys, void* ovals, unsigned* errors,
                            cudaStream_t s) {
-    // sorted rows + staging rows, the mbarrier, three per-bucket arrays, scan scratch
-    const size_t smem = 2 * (size_t)kScatterRows * kPartThreads * (sizeof(T) + 4) + 8 + 3 * (size_t)pg.B * 4 + 33 * 4;
-    cudaError_t e = cudaFuncSetAttribute(k_part_scatter<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    k_part_scatter<T><<<grid, kPartThreads, smem, s>>>(keys, (const T*)vals, u, pg, offsets, cursor, okeys,
-                                                       (T*)ovals, errors);
-    return cudaGetLastError();
+    if (!offsets && pg.B > kWideTileBuckets)
+        return launch_scatter_rpt<T, 2 * kScatterRows>(keys, vals, u, pg, grid, offsets, cursor, okeys, ovals,
+                                                       errors, s);
+    return launch_scatter_rpt<T, kScatterRows>(keys, vals, u, pg, grid, offsets, cursor, okeys, ovals, errors, s);
 }
 
 cudaError_t launch_hist(const int32_t* keys, const Units& u, const PassGeom& pg, int grid, int* counts,
@@ -1027,10 +1044,10 @@ bool partition_choose(int dtype, int L, long long G, PartChoice& pc) {
     if (!shift) return false;
     pc.shift = shift;
     // rule: one pass up to kOneLevelRuleParts partitions (measured at 2^28
-    // rows: one pass into 512 partitions 2.16 ms, two passes 2.43 ms; 1024
-    // partitions 2.91 ms, two passes 2.43 ms), else two with about sqrt(F)
-    // buckets per coarse partition; a measured choice may take one pass up
-    // to kOneLevelMaxParts or two passes beyond kOneLevelParts
+    // rows, 2^20 groups: one pass into 1024 partitions 2.18 ms, two passes
+    // 2.45 ms), else two with about sqrt(F) buckets per coarse partition; a
+    // measured choice may take one pass up to kOneLevelMaxParts or two
+    // passes beyond kOneLevelParts
     const long long F = (G + (1ll << shift) - 1) >> shift;
     if (levels == 1 && F > kOneLevelMaxParts) levels = 0;
     if (levels == 2 && F <= kOneLevelParts) levels = 0;

@@ -65,16 +65,17 @@ def test_medium_key_range_takes_one_pass_instead_of_two():
     assert torch.equal(a.tensor, b.tensor)
 
 
-@pytest.mark.parametrize("G,dist,want", [(1 << 20, "zipf", 1), (1 << 20, "uniform", 2),
-                                         (1 << 16, "zipf", 1), (1 << 16, "uniform", 1)])
-def test_full_key_range_keeps_the_rule_depth(G, dist, want):
-    """Keys over all groups: uniform keys keep the rule's plan (two passes
-    over 1024 partitions at 2^20 groups, one over 64 at 2^16); Zipf keys are
-    skewed (the fullest partition far above the mean), so the call goes
-    over to one pass -- into 2^7-group partitions with lane-private table
-    copies at 2^16, into the rule's 1024 at 2^20 -- the same bytes either
-    way, and the oracle's."""
-    L = 3
+@pytest.mark.parametrize("G,L,dist,want", [(1 << 20, 3, "zipf", 1), (1 << 20, 3, "uniform", 1),
+                                           (1 << 20, 4, "uniform", 2), (1 << 20, 4, "zipf", 1),
+                                           (1 << 16, 3, "zipf", 1), (1 << 16, 3, "uniform", 1)])
+def test_full_key_range_keeps_the_rule_depth(G, L, dist, want):
+    """Keys over all groups: uniform keys keep the rule's plan (one pass
+    into 1024 partitions at 2^20 groups and L = 3, two passes over 2048 at
+    L = 4, one over 64 at 2^16); Zipf keys are skewed (the fullest partition
+    far above the mean), so the call goes over to one pass -- into 2^7-group
+    partitions with lane-private table copies at 2^16, into 1024 partitions
+    instead of two passes at 2^20 and L = 4 -- the same bytes either way,
+    and the oracle's."""
     R.tune_clear()  # the rule's choices, not a measured one
     w = WL.sweep_cell(G, dist, L, n=1 << 22, seed=9, device=DEV)
     depth, a, b = _both(w.keys, w.values, G, L)
