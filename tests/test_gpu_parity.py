@@ -336,15 +336,19 @@ def test_fused_variants_in_subprocess(env):
 
 # ------------------------------------------------- partitioned large-G path
 
-@pytest.mark.parametrize("G,dist,L,n", [
-    (1 << 16, "zipf", 3, 1 << 22), (1 << 16, "uniform", 2, 1 << 22),  # one partition pass
-    (5000, "zipf", 3, 1 << 22),
-    (1 << 20, "uniform", 4, 1 << 22), (300_000, "uniform", 3, 1 << 22),  # two passes
-    (3_000_000, "zipf", 2, 1 << 21),  # two passes, coarse partitions of uneven size
-    (1 << 24, "uniform", 4, 1 << 20),  # 8192 final partitions (most groups empty)
+@pytest.mark.parametrize("G,dist,L,n,dtype", [
+    (1 << 16, "zipf", 3, 1 << 22, torch.float64), (1 << 16, "uniform", 2, 1 << 22, torch.float64),  # one pass
+    (5000, "zipf", 3, 1 << 22, torch.float64),
+    (1 << 20, "uniform", 3, 1 << 22, torch.float64),  # one wide pass: 1024 partitions, long tiles
+    (1 << 20, "zipf", 3, 1 << 22, torch.float32),
+    (300_000, "uniform", 3, 1 << 22, torch.float32),  # one pass, 293 partitions
+    (300_000, "uniform", 4, 1 << 22, torch.float64),  # one pass, 586 partitions of 512 groups
+    (1 << 20, "uniform", 4, 1 << 22, torch.float64),  # two passes: 2048 partitions
+    (3_000_000, "zipf", 2, 1 << 21, torch.float64),  # two passes, coarse partitions of uneven size
+    (1 << 24, "uniform", 4, 1 << 20, torch.float64),  # 8192 final partitions (most groups empty)
 ])
-def test_partitioned_path_matches_oracle(G, dist, L, n):
-    w = WL.sweep_cell(G, dist, L, n=n, seed=G + L, device=DEV)
+def test_partitioned_path_matches_oracle(G, dist, L, n, dtype):
+    w = WL.sweep_cell(G, dist, L, n=n, seed=G + L, device=DEV, dtype=dtype)
     st, out = run_gpu(w.keys, w.values, w.G, w.L)
     assert st.check() == 0
     ost, _ = oracle_state(_np(w.keys), _np(w.values), w.G, w.L, threads=8 if G <= (1 << 20) else 1)
